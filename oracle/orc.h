@@ -1,0 +1,127 @@
+/*
+ * CPU oracle for the continuous-time loop-cluster update (test infrastructure).
+ *
+ * This directory is TEST INFRASTRUCTURE.  Only the tests, the smoke entry point
+ * and the benchmark's CPU-baseline leg may load it.  It shares no code with the
+ * CUDA library: it is a plain, slow, obviously-correct restatement of the method
+ * in fp64 / exact integer arithmetic.
+ *
+ * Two forms of one Monte Carlo step of the S=1/2 (Q=2S=1) or S=1 (Q=2, subspin)
+ * antiferromagnetic Heisenberg chain, H = J sum_j S_j . S_{j+1}  (Eq. 1, Sec. 2):
+ *
+ *   orc_serial_update  -- the paper's sequential 8-step scan (Sec. 2, the
+ *                         enumerated MC step): global exponential gaps, a
+ *                         uniformly drawn bond per gap, union-find by weight with
+ *                         path compression.  Its random stream is its own; it is
+ *                         compared with everything else only statistically.
+ *
+ *   orc_keyed_update   -- the same Markov chain written per bond and per time
+ *                         window with Philox keys (a reading of the insertion
+ *                         step: superposition of per-bond Poisson processes of
+ *                         rate J/2, Sec. 2 rule ii).  Clusters are found by
+ *                         walking the loops of the segment graph (no
+ *                         union-find).  Given the same state, seed and sweep it
+ *                         defines every integer output of the update exactly.
+ */
+#ifndef ORC_H
+#define ORC_H
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Poisson thresholds per window: K <= ORC_KMAX-1 candidates per cell. */
+#define ORC_KMAX 48
+/* Mean number of candidate graphs per full window: window width w = 16/J. */
+#define ORC_CELL_MEAN 8.0
+/* Windows per time block in the canonical cell order. */
+#define ORC_TW 4
+
+/* Philox tags (high byte of counter word 0). */
+#define ORC_TAG_INSERT 1u
+#define ORC_TAG_FLIP 2u
+#define ORC_TAG_FREE 3u
+#define ORC_TAG_PERM 4u
+#define ORC_TAG_SERIAL 9u
+
+typedef struct {
+  int64_t L;      /* original sites (even, >= 2) */
+  int Q;          /* 2S subspins per site: 1 or 2 */
+  double J;       /* coupling, > 0 */
+  double beta;    /* inverse temperature, > 0 */
+  uint64_t seed;  /* Philox key */
+} orc_params;
+
+/* One update's measurements. Integer sums are exact. */
+typedef struct {
+  int64_t n;            /* graph vertices (old off-diagonal + new diagonal) */
+  int64_t n_off_old;    /* off-diagonal operators before the update */
+  int64_t n_off_new;    /* off-diagonal operators after the update */
+  int64_t n_free;       /* loops that carry no vertex (empty cut cycles) */
+  int64_t n_clusters;   /* loops in total */
+  int64_t n_seg;        /* world-line fragments (pieces between vertices) */
+  int32_t F;            /* fixed-point exponent of the per-loop sums */
+  int32_t pad;
+  uint64_t sw2_lo, sw2_hi;  /* sum over loops of Wq^2 (128-bit) */
+  uint64_t sf2_lo, sf2_hi;  /* sum over loops of Cq^2 + Sq^2 (128-bit) */
+  double energy;        /* E/L = (Q^2 J/4) - n/(beta L) */
+  double chi_s;         /* sum_c W_c^2 / (4 beta L) */
+  double chi_q;         /* sum_c |sum e^{ikx} len|^2 / (4 beta L), k = 2 pi/L */
+} orc_record;
+
+/* Derived chain geometry (both forms use it). */
+int64_t orc_nsub(const orc_params *p);
+int64_t orc_nbond(const orc_params *p);
+int64_t orc_nwin(const orc_params *p);
+int64_t orc_ncell(const orc_params *p);
+int64_t orc_cell_index(const orc_params *p, int64_t b, int64_t j);
+int orc_fixed_exponent(const orc_params *p);
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Poisson(mu) thresholds: T[k] = floor(2^64 * P(K <= k)), saturated. */
+void orc_poisson_thresholds(double mu, uint64_t T[ORC_KMAX]);
+
+/* Neel start: s0[(i,a)] = i & 1, no operators. op_ptr has ncell+1 entries. */
+void orc_neel(const orc_params *p, uint8_t *s0, int64_t *op_ptr);
+
+/*
+ * Keyed update.  Inputs: s0 [nsub], op_ptr [ncell+1] (canonical cell order),
+ * op_tau [op_ptr[ncell]] sorted within each cell.  Outputs: s0_out, op_ptr_out,
+ * op_tau_out (capacity op_cap).  Optional debug outputs (may be NULL):
+ *   vtx_tau[n], vtx_flag[n] (1 = off-diagonal before the update),
+ *   vtx_bond[n], vtx_pl[n], vtx_pr[n] (node of the piece below the vertex on its
+ *   left / right subsite), vtx_root[n] (canonical id of the loop through the
+ *   vertex's upper legs), cap_vtx the capacity of these arrays.
+ * Returns 0, or -1 (capacity) / -2 (invalid configuration).
+ */
+int orc_keyed_update(const orc_params *p, uint32_t sweep, const uint8_t *s0,
+                     const int64_t *op_ptr, const double *op_tau, uint8_t *s0_out,
+                     int64_t *op_ptr_out, double *op_tau_out, int64_t op_cap,
+                     orc_record *rec, int64_t cap_vtx, double *vtx_tau, uint8_t *vtx_flag,
+                     int64_t *vtx_bond, int64_t *vtx_pl, int64_t *vtx_pr, int64_t *vtx_root);
+
+/* Run n keyed updates in place (state arrays must have room: op_cap). */
+int orc_keyed_run(const orc_params *p, uint32_t sweep0, int64_t n_updates, uint8_t *s0,
+                  int64_t *op_ptr, double *op_tau, int64_t op_cap, orc_record *recs);
+
+/*
+ * Serial (paper-literal) update on a time-ordered operator list.
+ * ops_tau[n_ops], ops_bond[n_ops] sorted by tau; outputs replace them
+ * (capacity op_cap).  Random numbers: Philox keyed by seed, counter stream
+ * (i, sweep, ORC_TAG_SERIAL).
+ */
+int orc_serial_update(const orc_params *p, uint32_t sweep, uint8_t *s0, int64_t *n_ops,
+                      double *ops_tau, int64_t *ops_bond, int64_t op_cap, orc_record *rec);
+
+int orc_serial_run(const orc_params *p, uint32_t sweep0, int64_t n_updates, uint8_t *s0,
+                   int64_t *n_ops, double *ops_tau, int64_t *ops_bond, int64_t op_cap,
+                   orc_record *recs);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
