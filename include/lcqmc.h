@@ -1,0 +1,238 @@
+/*
+ * lcqmc -- continuous-time loop-cluster quantum Monte Carlo update of the
+ * antiferromagnetic Heisenberg chain on one GB300 GPU (sm_103a), C ABI.
+ *
+ * Method: Todo, Matsuo, Shitara, "Parallel loop cluster quantum Monte Carlo
+ * simulation of quantum magnets based on global union-find graph algorithm"
+ * (arXiv:1810.07485).  The model is H = J sum_j S_j . S_{j+1} with periodic
+ * boundaries (Eq. 1, Sec. 2); one update is the continuous-time loop step of
+ * Sec. 2 (labeling, cluster identification, flip, rewrite, measurement) with the
+ * cluster identification done by a lock-free union-find (Sec. 3.2).  S = 1 is
+ * handled by the subspin representation of Sec. 5 (two S=1/2 subspins per site,
+ * four sub-bonds per bond).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: LCQMC_OK (0) on success, LCQMC_PENDING (1) where stated,
+ *     a negative LCQMC_E_* code on failure.  lcqmc_last_error() returns a
+ *     thread-local message describing the last failure of the calling thread.
+ *   - Host pointers are plain host memory owned by the caller; the library
+ *     copies from / into them before returning.  The library owns every device
+ *     buffer it allocates; handles own their state until destroyed.
+ *   - A chain handle or batch handle must not be used from two threads at
+ *     once.  Server calls are thread-safe.
+ *   - Work is ordered on the handle's CUDA stream; lcqmc_update only enqueues,
+ *     lcqmc_sync / lcqmc_measure wait for it.
+ *   - The world-line state is the spin configuration at tau=0 plus the
+ *     imaginary times of the off-diagonal operators (Sec. 2, world lines).  Its
+ *     exchange format groups operators by cell = (bond, time window):
+ *       bond b of the subspin lattice joins subsite (i*Q + a) and
+ *       (((i+1) mod L)*Q + a') with b = i*Q*Q + a*Q + a', Q = 2S;
+ *       window j covers [j*w, (j+1)*w) with w = 16/J, the last one ends at beta;
+ *       cells are ordered in blocks of LCQMC_TW windows, bond-major inside a
+ *       block: cell(b, j) = (j/TW)*nbond*TW + b*tw + (j mod TW), tw = the
+ *       block's window count.
+ *     op_ptr has ncell+1 entries (CSR offsets), op_tau the times, ascending
+ *     inside each cell.
+ */
+#ifndef LCQMC_H
+#define LCQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LCQMC_OK 0
+#define LCQMC_PENDING 1
+#define LCQMC_E_INVAL (-1)          /* bad argument: L < 2 or odd, beta <= 0, J <= 0, 2S not 1 or 2 */
+#define LCQMC_E_NOMEM (-2)          /* device or host allocation failed */
+#define LCQMC_E_TOO_LARGE (-3)      /* footprint above the budget / the server's HBM budget */
+#define LCQMC_E_ID_OVERFLOW (-4)    /* more than 2^31-1 graph vertices or cells in one chain */
+#define LCQMC_E_DEVICE_TIMEOUT (-5) /* a bounded device wait (union-find retry) ran out */
+#define LCQMC_E_CUDA (-6)           /* a CUDA runtime call failed */
+#define LCQMC_E_STATE (-7)          /* imported configuration is not a valid world-line state */
+#define LCQMC_E_NOT_FOUND (-8)      /* unknown server ticket */
+#define LCQMC_E_CANCELLED (-9)      /* request was cancelled or rejected at admission */
+#define LCQMC_E_CAPACITY (-10)      /* caller-provided output buffer too small */
+
+#define LCQMC_TW 4 /* windows per time block of the cell order */
+
+typedef struct lcqmc_chain *lcqmc_handle;
+typedef struct lcqmc_batch *lcqmc_batch_t;
+typedef struct lcqmc_server *lcqmc_server_t;
+
+/* Running averages since create / the last reset (caller-owned). Index k of
+ * sum/sumsq: 0 E/L, 1 chi_s, 2 chi(pi+2pi/L), 3 n (graph vertices),
+ * 4 n_off (off-diagonal operators after the update), 5 world-line fragments,
+ * 6 loops, 7 vertices+edges of the cluster graph (fragments + 2n). */
+typedef struct {
+  int64_t n_updates;
+  double sum[8];
+  double sumsq[8];
+  double xi; /* (L/2pi) sqrt(<chi_s>/<chi(pi+2pi/L)> - 1), ratio of means */
+} lcqmc_obs;
+
+/* One update's measurements.  The sums of squared loop lengths are exact
+ * 128-bit integers in units of 2^-2F (F = 60 - ceil(log2(Q L beta))): every
+ * fragment length is rounded once to a multiple of 2^-F, then summed per loop
+ * exactly.  energy = Q^2 J/4 - n/(beta L); chi_s = sw2 2^-2F/(4 beta L);
+ * chi_q = sf2 2^-2F/(4 beta L) with q = pi + 2 pi / L. */
+typedef struct {
+  int64_t n, n_off_old, n_off_new, n_free, n_clusters, n_seg;
+  int32_t F, pad;
+  uint64_t sw2_lo, sw2_hi, sf2_lo, sf2_hi;
+  double energy, chi_s, chi_q;
+} lcqmc_record;
+
+typedef struct {
+  int64_t L, nsub, nbond, nwin, ncell;
+  int32_t Q, F;
+  double J, beta, w;
+  uint64_t seed;
+  uint32_t sweep; /* updates completed (the Philox sweep counter) */
+  uint32_t pad;
+} lcqmc_geometry;
+
+/* Device memory allocator supplied by the caller (e.g. a framework's caching
+ * allocator).  alloc returns device memory of at least `bytes` or NULL; free
+ * releases it.  ctx is passed through. */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *ctx);
+  void (*free)(void *ptr, void *ctx);
+  void *ctx;
+} lcqmc_allocator;
+
+/* --- single chain (Sec. 2 MC step on one chain) ----------------------------- */
+
+/* Creates a chain of L sites (even, >= 2), spin S (0.5 or 1.0, checked exactly),
+ * coupling J > 0, inverse temperature beta > 0, Philox seed.  Starts from the
+ * Neel state with no operators, sweep 0, on device 0's default stream. */
+int lcqmc_create(int64_t L, double S, double J, double beta, uint64_t seed, lcqmc_handle *out);
+
+/* As lcqmc_create with a CUDA stream (cudaStream_t as void*, NULL = legacy
+ * default) and an optional allocator (NULL = cudaMalloc/cudaFree). */
+int lcqmc_create_ex(int64_t L, double S, double J, double beta, uint64_t seed, void *cuda_stream,
+                    const lcqmc_allocator *alloc, lcqmc_handle *out);
+
+/* Enqueues n loop updates on the chain's stream.  Returns at once. */
+int lcqmc_update(lcqmc_handle h, int64_t n);
+
+/* Waits for enqueued updates.  Grows device buffers and replays updates that
+ * ran out of room (results are unchanged: the random numbers are keyed by the
+ * sweep counter).  Returns LCQMC_E_DEVICE_TIMEOUT if a device wait ran out. */
+int lcqmc_sync(lcqmc_handle h);
+
+/* Syncs, then fills *out with averages since create or the last reset. */
+int lcqmc_measure(lcqmc_handle h, lcqmc_obs *out);
+int lcqmc_reset_obs(lcqmc_handle h);
+
+/* Syncs, then copies up to max per-update records (oldest first) that were
+ * produced since the previous call into out; *count receives the number.  The
+ * device keeps the last 4096 records; older ones are dropped (count them with
+ * lcqmc_obs.n_updates). */
+int lcqmc_get_records(lcqmc_handle h, lcqmc_record *out, int64_t max, int64_t *count);
+
+int lcqmc_get_geometry(lcqmc_handle h, lcqmc_geometry *out);
+
+/* Syncs, then copies the state: s0[nsub] (0/1), op_ptr[ncell+1], op_tau[n_off].
+ * op_tau may be NULL to query *n_off only; LCQMC_E_CAPACITY if op_cap < n_off. */
+int lcqmc_export_config(lcqmc_handle h, uint8_t *s0, int32_t *op_ptr, double *op_tau,
+                        int64_t op_cap, int64_t *n_off);
+
+/* Replaces the state with the given one and sets the sweep counter.  Checks
+ * that op_ptr is a non-decreasing CSR, every time lies in its cell's window,
+ * times are ascending inside a cell, and every operator acts on antiparallel
+ * spins (Sec. 2 world-line constraint); LCQMC_E_STATE otherwise. */
+int lcqmc_import_config(lcqmc_handle h, const uint8_t *s0, const int32_t *op_ptr,
+                        const double *op_tau, int64_t n_off, uint32_t sweep);
+
+/* Debug: keep the graph of the most recent update for lcqmc_export_graph. */
+int lcqmc_set_keep_graph(lcqmc_handle h, int keep);
+
+/* Debug: after an update with keep_graph set, copies per-vertex arrays of that
+ * update (chain-local vertex ids): tau, flag (1 = operator was off-diagonal
+ * before the update), pl / pr (node of the fragment below the vertex on its
+ * left / right subsite), root (smallest node id of its loop).  n_cap entries
+ * each; *n receives the vertex count.  Any pointer may be NULL. */
+int lcqmc_export_graph(lcqmc_handle h, double *tau, uint8_t *flag, int32_t *pl, int32_t *pr,
+                       int32_t *root, int64_t n_cap, int64_t *n);
+
+/* Debug: vertex offsets of every cell (ncell+1 entries, chain-local ids, in
+ * the cell order above) of the most recent update: the vertices of cell c are
+ * ids vptr[c] .. vptr[c+1]-1 of lcqmc_export_graph. */
+int lcqmc_export_cells(lcqmc_handle h, int32_t *vptr, int64_t cap);
+
+/* Checkpoint = geometry + seed + sweep + state.  lcqmc_checkpoint with
+ * buf == NULL sets *len to the size needed.  Restoring continues the same
+ * Markov chain bit for bit. */
+int lcqmc_checkpoint(lcqmc_handle h, void *buf, size_t *len);
+int lcqmc_restore(lcqmc_handle h, const void *buf, size_t len);
+
+/* Per-phase device time (ms) accumulated over updates while enabled, in the
+ * order of the cost table of Sec. 4.3: 0 random numbers and insertion,
+ * 1 scans, 2 linking and union-find, 3 loop ids (compression, coins),
+ * 4 loop properties and flags, 5 operator rewrite, 6 spin rewrite and record. */
+#define LCQMC_NPHASE 7
+int lcqmc_set_phase_timing(lcqmc_handle h, int enable);
+int lcqmc_get_phase_times(lcqmc_handle h, double *ms, int nphase);
+
+/* Raw CUDA stream of the handle (cudaStream_t as void*). */
+void *lcqmc_stream(lcqmc_handle h);
+
+int lcqmc_destroy(lcqmc_handle h);
+
+/* --- batched form: many independent chains in one launch per phase ------- */
+
+typedef struct {
+  int64_t L;
+  double S, J, beta;
+  uint64_t seed;
+} lcqmc_chain_spec;
+
+/* Creates a batch of independent chains (Sec. 3: independent Markov chains),
+ * updated together: every phase of an update is one kernel launch over all
+ * chains' cells, and n updates are replayed from one captured CUDA graph. */
+int lcqmc_batch_create(int64_t nchains, const lcqmc_chain_spec *specs, void *cuda_stream,
+                       lcqmc_batch_t *out);
+int lcqmc_batch_update(lcqmc_batch_t b, int64_t n);
+int lcqmc_batch_sync(lcqmc_batch_t b);
+int lcqmc_batch_measure(lcqmc_batch_t b, int64_t chain, lcqmc_obs *out);
+int lcqmc_batch_get_records(lcqmc_batch_t b, int64_t chain, lcqmc_record *out, int64_t max,
+                            int64_t *count);
+int lcqmc_batch_destroy(lcqmc_batch_t b);
+
+/* --- served form: continuous batching of simulation requests -------------- */
+
+typedef struct {
+  int64_t L;
+  double S, J, beta;
+  uint64_t seed;
+  int64_t n_updates; /* updates to run, then read out */
+} lcqmc_request;
+
+typedef struct {
+  int32_t status; /* LCQMC_OK, LCQMC_PENDING, or LCQMC_E_* */
+  int32_t pad;
+  lcqmc_obs obs;
+  double t_submit, t_admit, t_done; /* seconds on the server's clock */
+  int64_t vertices_edges;           /* total V+E processed for this request */
+} lcqmc_result;
+
+/* A server keeps up to max_slots chains resident on the device within
+ * hbm_budget bytes, admits queued requests as slots and memory free up, and
+ * advances all resident chains together in ticks of updates. */
+int lcqmc_server_create(size_t hbm_budget, int max_slots, lcqmc_server_t *out);
+int lcqmc_submit(lcqmc_server_t s, const lcqmc_request *req, uint64_t *ticket);
+int lcqmc_poll(lcqmc_server_t s, uint64_t ticket, lcqmc_result *out);
+int lcqmc_cancel(lcqmc_server_t s, uint64_t ticket);
+int lcqmc_server_destroy(lcqmc_server_t s);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char *lcqmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -99,6 +99,143 @@ static int poisson_sample(const uint64_t T[ORC_KMAX], uint64_t U) {
   return K;
 }
 
+/*
+ * Labeling of one cell (bond b, window j): the old operators of the cell are
+ * horizontal graphs (rule i); candidates of a Poisson process of rate J/2 are
+ * kept where the bond's spins are antiparallel (rules ii, iii).  ev_l / ev_r
+ * are the old operators touching the bond's left / right subsite, sorted by
+ * (tau, bond).  Writes the cell's vertices in (tau, old-first, draw) order and
+ * returns their number.
+ */
+static int64_t label_cell(const orc_params *p, uint32_t sweep, int64_t b, int64_t j,
+                          const uint8_t *s0, const ev_t *ev_l, int64_t n_l, const ev_t *ev_r,
+                          int64_t n_r, const int64_t *op_ptr, const double *op_tau,
+                          const uint64_t *T_full, const uint64_t *T_last, double *out_tau,
+                          uint8_t *out_flag) {
+  const int64_t NW = orc_nwin(p);
+  const double beta = p->beta, w = 16.0 / p->J;
+  const uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
+  int64_t ul, ur;
+  bond_ends(p, b, &ul, &ur);
+  const int64_t c = orc_cell_index(p, b, j);
+  double t0 = (double)j * w;
+  double t_end = (j == NW - 1) ? beta : (double)(j + 1) * w;
+  double d = t_end - t0;
+  const uint64_t *T = (j == NW - 1) ? T_last : T_full;
+  cand_t cand[ORC_KMAX];
+  /* Draws: call 0 gives K and candidate 0; call m >= 1 gives 2m-1, 2m. */
+  uint32_t ctr[4] = {(ORC_TAG_INSERT << 24) | 0u, (uint32_t)b, (uint32_t)j, sweep};
+  uint32_t out[4];
+  orc_philox4x32_10(ctr, key, out);
+  uint64_t U = (uint64_t)out[0] | ((uint64_t)out[1] << 32);
+  int K = poisson_sample(T, U);
+  int nk = 0;
+  for (int k = 0; k < K; ++k) {
+    uint64_t bits;
+    if (k == 0) {
+      bits = (uint64_t)out[2] | ((uint64_t)out[3] << 32);
+    } else {
+      uint32_t m = (uint32_t)((k + 1) / 2);
+      uint32_t c2[4] = {(ORC_TAG_INSERT << 24) | m, (uint32_t)b, (uint32_t)j, sweep};
+      uint32_t o2[4];
+      orc_philox4x32_10(c2, key, o2);
+      bits = (k & 1) ? ((uint64_t)o2[0] | ((uint64_t)o2[1] << 32))
+                     : ((uint64_t)o2[2] | ((uint64_t)o2[3] << 32));
+    }
+    uint64_t u53 = bits >> 11;
+    double tau = fma(d, ldexp((double)u53, -53), t0);
+    if (!(tau < t_end)) continue;
+    /* Rule ii/iii: keep iff the bond's spins are antiparallel at tau. */
+    int64_t pl = count_before(ev_l, n_l, tau, b);
+    int64_t pr = count_before(ev_r, n_r, tau, b);
+    int sl = s0[ul] ^ (int)(pl & 1), sr = s0[ur] ^ (int)(pr & 1);
+    if (sl == sr) continue;
+    cand[nk].u53 = u53;
+    cand[nk].k = k;
+    cand[nk].tau = tau;
+    ++nk;
+  }
+  qsort(cand, (size_t)nk, sizeof(cand_t), cand_cmp);
+  /* Merge with the cell's old operators; an old one goes first at equal tau. */
+  int64_t q = op_ptr[c], qe = op_ptr[c + 1], r = 0;
+  int ki = 0;
+  while (q < qe || ki < nk) {
+    if (q < qe && (ki >= nk || op_tau[q] <= cand[ki].tau)) {
+      out_tau[r] = op_tau[q++];
+      out_flag[r] = 1;
+    } else {
+      out_tau[r] = cand[ki++].tau;
+      out_flag[r] = 0;
+    }
+    ++r;
+  }
+  return r;
+}
+
+static int64_t gather_events(const orc_params *p, int64_t u, const int64_t *op_ptr,
+                             const double *op_tau, ev_t **out) {
+  /* Old operators on the bonds touching subsite u, sorted by (tau, bond). */
+  const int64_t NW = orc_nwin(p), Q = p->Q, i = u / Q, a = u % Q;
+  int64_t cnt = 0, cap = 1024;
+  ev_t *e = (ev_t *)malloc(sizeof(ev_t) * (size_t)cap);
+  for (int64_t k = 0; k < 2 * Q; ++k) {
+    /* bonds (i, a, k) with u at the left end, bonds (i-1, k-Q, a) at the right */
+    int64_t b = (k < Q) ? i * Q * Q + a * Q + k : ((i - 1 + p->L) % p->L) * Q * Q + (k - Q) * Q + a;
+    for (int64_t j = 0; j < NW; ++j) {
+      int64_t c = orc_cell_index(p, b, j);
+      for (int64_t q = op_ptr[c]; q < op_ptr[c + 1]; ++q) {
+        if (cnt == cap) {
+          cap *= 2;
+          e = (ev_t *)realloc(e, sizeof(ev_t) * (size_t)cap);
+        }
+        e[cnt].tau = op_tau[q];
+        e[cnt].bond = b;
+        ++cnt;
+      }
+    }
+  }
+  qsort(e, (size_t)cnt, sizeof(ev_t), ev_cmp);
+  *out = e;
+  return cnt;
+}
+
+int orc_keyed_cell(const orc_params *p, uint32_t sweep, const uint8_t *s0, const int64_t *op_ptr,
+                   const double *op_tau, int64_t b, int64_t j, double *out_tau, uint8_t *out_flag,
+                   int64_t cap, int64_t *n_out) {
+  const int64_t NW = orc_nwin(p);
+  const double w = 16.0 / p->J;
+  uint64_t T_full[ORC_KMAX], T_last[ORC_KMAX];
+  orc_poisson_thresholds(ORC_CELL_MEAN, T_full);
+  {
+    double t0 = (double)(NW - 1) * w;
+    double d = p->beta - t0;
+    orc_poisson_thresholds(d > 0.0 ? p->J * d * 0.5 : 0.0, T_last);
+  }
+  int64_t ul, ur;
+  bond_ends(p, b, &ul, &ur);
+  ev_t *el, *er;
+  int64_t nl = gather_events(p, ul, op_ptr, op_tau, &el);
+  int64_t nr = gather_events(p, ur, op_ptr, op_tau, &er);
+  const int64_t c = orc_cell_index(p, b, j);
+  const int64_t nold = op_ptr[c + 1] - op_ptr[c];
+  double *t = (double *)malloc(sizeof(double) * (size_t)(nold + ORC_KMAX + 1));
+  uint8_t *f = (uint8_t *)malloc((size_t)(nold + ORC_KMAX + 1));
+  int64_t m = label_cell(p, sweep, b, j, s0, el, nl, er, nr, op_ptr, op_tau, T_full, T_last, t, f);
+  int rc = 0;
+  if (m > cap) {
+    rc = -1;
+  } else {
+    memcpy(out_tau, t, sizeof(double) * (size_t)m);
+    memcpy(out_flag, f, (size_t)m);
+  }
+  *n_out = m;
+  free(t);
+  free(f);
+  free(el);
+  free(er);
+  return rc;
+}
+
 typedef unsigned __int128 u128;
 
 int orc_keyed_update(const orc_params *p, uint32_t sweep, const uint8_t *s0,
@@ -110,7 +247,6 @@ int orc_keyed_update(const orc_params *p, uint32_t sweep, const uint8_t *s0,
   const int64_t L = p->L, Q = p->Q, NS = orc_nsub(p), NB = orc_nbond(p);
   const int64_t NW = orc_nwin(p), NC = orc_ncell(p);
   const double beta = p->beta, w = 16.0 / p->J;
-  const uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
   int rc = 0;
 
   /* Windows: [j w, (j+1) w) and the last one [(NW-1) w, beta). */
@@ -157,7 +293,11 @@ int orc_keyed_update(const orc_params *p, uint32_t sweep, const uint8_t *s0,
   /* 1. Labeling: build each cell's vertex list in canonical cell order. */
   int64_t vcap = n_old + 1024, n = 0;
   vtx_t *vtx = (vtx_t *)malloc(sizeof(vtx_t) * (size_t)vcap);
-  cand_t cand[ORC_KMAX];
+  int64_t max_cell = 0;
+  for (int64_t c = 0; c < NC; ++c)
+    if (op_ptr[c + 1] - op_ptr[c] > max_cell) max_cell = op_ptr[c + 1] - op_ptr[c];
+  double *cell_tau = (double *)malloc(sizeof(double) * (size_t)(max_cell + ORC_KMAX));
+  uint8_t *cell_flag = (uint8_t *)malloc((size_t)(max_cell + ORC_KMAX));
   int64_t nblk = (NW + ORC_TW - 1) / ORC_TW;
   int64_t c_expect = 0;
   for (int64_t blk = 0; blk < nblk; ++blk) {
@@ -171,63 +311,20 @@ int orc_keyed_update(const orc_params *p, uint32_t sweep, const uint8_t *s0,
         int64_t c = orc_cell_index(p, b, j);
         if (c != c_expect) { rc = -3; goto done; }
         ++c_expect;
-        double t0 = (double)j * w;
-        double t_end = (j == NW - 1) ? beta : (double)(j + 1) * w;
-        double d = t_end - t0;
-        const uint64_t *T = (j == NW - 1) ? T_last : T_full;
-        /* Draws: call 0 gives K and candidate 0; call m >= 1 gives 2m-1, 2m. */
-        uint32_t ctr[4] = {(ORC_TAG_INSERT << 24) | 0u, (uint32_t)b, (uint32_t)j, sweep};
-        uint32_t out[4];
-        orc_philox4x32_10(ctr, key, out);
-        uint64_t U = (uint64_t)out[0] | ((uint64_t)out[1] << 32);
-        int K = poisson_sample(T, U);
-        int nk = 0;
-        for (int k = 0; k < K; ++k) {
-          uint64_t bits;
-          if (k == 0) {
-            bits = (uint64_t)out[2] | ((uint64_t)out[3] << 32);
-          } else {
-            uint32_t m = (uint32_t)((k + 1) / 2);
-            uint32_t c2[4] = {(ORC_TAG_INSERT << 24) | m, (uint32_t)b, (uint32_t)j, sweep};
-            uint32_t o2[4];
-            orc_philox4x32_10(c2, key, o2);
-            bits = (k & 1) ? ((uint64_t)o2[0] | ((uint64_t)o2[1] << 32))
-                           : ((uint64_t)o2[2] | ((uint64_t)o2[3] << 32));
-          }
-          uint64_t u53 = bits >> 11;
-          double tau = fma(d, ldexp((double)u53, -53), t0);
-          if (!(tau < t_end)) continue;
-          /* Rule ii/iii: keep iff the bond's spins are antiparallel at tau. */
-          int64_t pl = count_before(ev + ev_cnt[ul], ev_cnt[ul + 1] - ev_cnt[ul], tau, b);
-          int64_t pr = count_before(ev + ev_cnt[ur], ev_cnt[ur + 1] - ev_cnt[ur], tau, b);
-          int sl = s0[ul] ^ (int)(pl & 1), sr = s0[ur] ^ (int)(pr & 1);
-          if (sl == sr) continue;
-          cand[nk].u53 = u53;
-          cand[nk].k = k;
-          cand[nk].tau = tau;
-          ++nk;
+        int64_t m = label_cell(p, sweep, b, j, s0, ev + ev_cnt[ul], ev_cnt[ul + 1] - ev_cnt[ul],
+                               ev + ev_cnt[ur], ev_cnt[ur + 1] - ev_cnt[ur], op_ptr, op_tau, T_full,
+                               T_last, cell_tau, cell_flag);
+        if (n + m > vcap) {
+          while (n + m > vcap) vcap *= 2;
+          vtx = (vtx_t *)realloc(vtx, sizeof(vtx_t) * (size_t)vcap);
         }
-        qsort(cand, (size_t)nk, sizeof(cand_t), cand_cmp);
-        /* Merge with the cell's old operators; an old one goes first at equal tau. */
-        int64_t q = op_ptr[c], qe = op_ptr[c + 1];
-        int ki = 0;
-        while (q < qe || ki < nk) {
-          if (n + 1 > vcap) {
-            vcap = vcap * 2;
-            vtx = (vtx_t *)realloc(vtx, sizeof(vtx_t) * (size_t)vcap);
-          }
-          vtx_t v;
-          v.bond = b;
-          v.cell = c;
-          v.id = n;
-          if (q < qe && (ki >= nk || op_tau[q] <= cand[ki].tau)) {
-            v.tau = op_tau[q++];
-            v.flag = 1;
-          } else {
-            v.tau = cand[ki++].tau;
-            v.flag = 0;
-          }
-          vtx[n++] = v;
+        for (int64_t r = 0; r < m; ++r) {
+          vtx[n].tau = cell_tau[r];
+          vtx[n].flag = cell_flag[r];
+          vtx[n].bond = b;
+          vtx[n].cell = c;
+          vtx[n].id = n;
+          ++n;
         }
       }
     }
@@ -505,6 +602,8 @@ done2:
   free(pos_l);
   free(pos_r);
 done:
+  free(cell_tau);
+  free(cell_flag);
   free(ev_cnt);
   free(ev);
   free(ev_fill);

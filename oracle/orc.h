@@ -104,6 +104,13 @@ int orc_keyed_update(const orc_params *p, uint32_t sweep, const uint8_t *s0,
                      orc_record *rec, int64_t cap_vtx, double *vtx_tau, uint8_t *vtx_flag,
                      int64_t *vtx_bond, int64_t *vtx_pl, int64_t *vtx_pr, int64_t *vtx_root);
 
+/* Labeling step of one cell (bond b, window j) of the keyed update: writes the
+ * cell's vertices (tau, flag) in vertex-id order; *n_out their number.
+ * Returns -1 if cap is too small. */
+int orc_keyed_cell(const orc_params *p, uint32_t sweep, const uint8_t *s0, const int64_t *op_ptr,
+                   const double *op_tau, int64_t b, int64_t j, double *out_tau, uint8_t *out_flag,
+                   int64_t cap, int64_t *n_out);
+
 /* Run n keyed updates in place (state arrays must have room: op_cap). */
 int orc_keyed_run(const orc_params *p, uint32_t sweep0, int64_t n_updates, uint8_t *s0,
                   int64_t *op_ptr, double *op_tau, int64_t op_cap, orc_record *recs);

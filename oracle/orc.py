@@ -205,3 +205,24 @@ def serial_run(p, sweep0, n_updates, s0=None, ops=None):
 
 def u128(lo, hi):
     return (int(hi) << 64) | int(lo)
+
+
+def keyed_cell(p, sweep, st, b, j):
+    """Labeling of one cell of the keyed update from state st: (tau, flag)."""
+    L = lib()
+    if not hasattr(L, "_cell_sig"):
+        L.orc_keyed_cell.argtypes = [ctypes.POINTER(Params), ctypes.c_uint32, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                     ctypes.POINTER(ctypes.c_int64)]
+        L.orc_keyed_cell.restype = ctypes.c_int
+        L._cell_sig = True
+    cap = 4096
+    tau = np.zeros(cap)
+    flag = np.zeros(cap, np.uint8)
+    n = ctypes.c_int64()
+    rc = L.orc_keyed_cell(ctypes.byref(p), ctypes.c_uint32(sweep), _ptr(st.s0), _ptr(st.op_ptr),
+                          _ptr(st.op_tau), int(b), int(j), _ptr(tau), _ptr(flag), cap, ctypes.byref(n))
+    if rc != 0:
+        raise RuntimeError("orc_keyed_cell failed")
+    return tau[: n.value].copy(), flag[: n.value].copy()

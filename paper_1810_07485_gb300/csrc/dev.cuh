@@ -1,0 +1,182 @@
+// Device-side definitions of the loop-cluster update: chain descriptor,
+// batch scratch layout, Philox4x32-10, the canonical cell order and small
+// bit / 128-bit helpers.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/lcqmc.h"
+
+namespace lcq {
+
+constexpr int KMAX = 48;          // Poisson count table length (K <= KMAX-1)
+constexpr int TW = LCQMC_TW;      // windows per time block of the cell order
+constexpr int TILE = 128;         // cells per tile (one thread block)
+constexpr int SMEM_CAP = 2048;    // vertices a tile can accumulate in shared memory
+constexpr int OPEN_SLOTS = 128;   // shared hash slots for loops that leave a tile
+constexpr int MAX_COIN_GROUPS = 64;
+constexpr int SITE_BLOCK = 128;   // original sites per block
+constexpr int BOND_BLOCK = 128;   // bonds per block
+constexpr double CELL_MEAN = 8.0; // mean candidate graphs per full window (w = 16/J)
+constexpr uint32_t TAG_INSERT = 1u, TAG_FLIP = 2u, TAG_FREE = 3u, TAG_PERM = 4u;
+constexpr int UF_MAX_ITERS = 1 << 22;  // bound of every union-find retry / find walk
+
+// Status bits (device word; any set bit makes every later kernel of the update
+// return at entry, so the persistent state is left untouched).
+enum : int {
+  ST_VTX_OVERFLOW = 1,
+  ST_OP_OVERFLOW = 2,
+  ST_TIMEOUT = 4,
+  ST_INTERNAL = 8,
+  ST_BADSTATE = 16,
+  ST_ID_OVERFLOW = 32,
+};
+
+// Vertex flag bits.
+enum : uint8_t { VF_OLD = 1, VF_WRAP_L = 2, VF_WRAP_R = 4, VF_NEW = 8 };
+
+struct DevChain {
+  // geometry
+  int32_t L, Q, nsub, nbond, nwin, nblk, ncell, ntile, nsiteblk, F, ring_cap, pad0;
+  double beta, J, w;
+  uint64_t seed;
+  // tables
+  const uint64_t *T_last;
+  const double *cosx, *sinx;
+  // persistent state, double-buffered (index cur is current)
+  uint8_t *s0[2];
+  int32_t *op_ptr[2];
+  double *op_tau[2];
+  int64_t op_cap;
+  // offsets into batch scratch
+  int64_t cell_off;  // vptr: ncell+1 entries
+  int64_t tile0;     // first tile of the chain in the tile arrays
+  int64_t site0;     // first site block
+  int64_t bpar_off;  // bond parity table: (nblk+1) * nbond bytes
+  int64_t sub_off;   // per-subsite arrays: nsub entries
+  // dynamic, written by the kernels
+  int32_t cur;
+  uint32_t sweep;
+  int64_t vtx_base;  // first vertex of the chain in the vertex arrays (multiple of 128)
+  int64_t n;         // graph vertices of the current update
+  int64_t n_off_new; // off-diagonal operators after the current update
+  // measurements
+  lcqmc_record *ring;
+  int64_t n_rec;
+  int64_t n_updates;
+  double sum[8], sumsq[8];
+};
+
+struct Scratch {
+  int32_t *vptr;
+  int64_t *tile_sum, *tile_pref, *tile_sum2, *tile_pref2, *tile_roots;
+  unsigned long long *tile_sw2, *tile_sf2;   // 2 words (lo, hi) per tile
+  int64_t *site_free;
+  unsigned long long *site_sw2, *site_sf2;   // 2 words per site block
+  uint8_t *bpar;
+  int32_t *cut_node, *cut_cell, *free_min;
+  int8_t *cut_cross, *free_len;
+  double *vtau;
+  uint8_t *vflag;
+  int32_t *pl, *pr, *parent;
+  unsigned long long *accW, *accC, *accS;
+  uint32_t *openmark, *openroot, *flipbits;
+  int64_t vcap;
+  int *status;
+  int64_t *need;  // [0] vertex capacity needed by the last update
+};
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) -----------------
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+    uint32_t lo0 = m0 * c0, hi0 = __umulhi(m0, c0);
+    uint32_t lo1 = m1 * c2, hi1 = __umulhi(m1, c2);
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+__device__ __forceinline__ int coin_from(const U4 &o, uint32_t idx) {
+  uint32_t bit = idx & 127u;
+  uint32_t word = (bit < 32) ? o.x : (bit < 64) ? o.y : (bit < 96) ? o.z : o.w;
+  return (int)((word >> (bit & 31u)) & 1u);
+}
+
+// One fair coin per index, 128 indices per Philox block.
+__device__ __forceinline__ int coin(const DevChain &C, uint32_t tag, uint32_t idx) {
+  U4 o = philox(tag << 24, idx >> 7, 0u, C.sweep, (uint32_t)C.seed, (uint32_t)(C.seed >> 32));
+  return coin_from(o, idx);
+}
+
+// ---- cell order ----------------------------------------------------------
+__device__ __forceinline__ int cell_of(const DevChain &C, int b, int j) {
+  int blk = j / TW, jj = j - blk * TW;
+  int tw = min(TW, C.nwin - blk * TW);
+  return blk * C.nbond * TW + b * tw + jj;
+}
+
+__device__ __forceinline__ void cell_bj(const DevChain &C, int c, int &b, int &j) {
+  int per = C.nbond * TW;
+  int blk = c / per;
+  int r = c - blk * per;
+  int tw = min(TW, C.nwin - blk * TW);
+  b = r / tw;
+  j = blk * TW + (r - b * tw);
+}
+
+// ---- lattice of subspins: bond b = i*Q*Q + a*Q + a2 joins (i,a) and (i+1,a2)
+template <int Q>
+__device__ __forceinline__ int left_sub(int b) {
+  return (b / (Q * Q)) * Q + (b / Q) % Q;
+}
+template <int Q>
+__device__ __forceinline__ int right_sub(int b, int L) {
+  int i = b / (Q * Q) + 1;
+  if (i == L) i = 0;
+  return i * Q + b % Q;
+}
+// k-th bond touching subsite u: k < Q as its left end, k >= Q as its right end.
+template <int Q>
+__device__ __forceinline__ int inc_bond(int u, int k, int L) {
+  int i = u / Q, a = u - (u / Q) * Q;
+  if (k < Q) return i * Q * Q + a * Q + k;
+  int im = (i == 0) ? L - 1 : i - 1;
+  return im * Q * Q + (k - Q) * Q + a;
+}
+
+// ---- bits ------------------------------------------------------------------
+__device__ __forceinline__ int get_bit(const uint32_t *bits, int64_t word0, int32_t i) {
+  return (int)((__ldcg(bits + word0 + (i >> 5)) >> (i & 31)) & 1u);
+}
+__device__ __forceinline__ void set_bit(uint32_t *bits, int64_t word0, int32_t i) {
+  atomicOr(bits + word0 + (i >> 5), 1u << (i & 31));
+}
+
+// ---- exact fixed-point helpers ---------------------------------------------
+// len * 2^F rounded to nearest (ties to even), as llrint(ldexp(len, F)).
+__device__ __forceinline__ long long fixq(double len, double scale) {
+  return __double2ll_rn(__dmul_rn(len, scale));
+}
+
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ u128 sq_abs(long long v) {
+  unsigned long long a = (unsigned long long)(v < 0 ? -v : v);
+  return (u128)a * (u128)a;
+}
+
+}  // namespace lcq

@@ -1,0 +1,812 @@
+// Host engine of the loop-cluster update: per-chain state, batch scratch, the
+// per-update launch sequence (captured once as a CUDA graph), capacity growth
+// with replay, and state import / export.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+
+namespace lcq {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+const char *last_error() { return g_err.c_str(); }
+
+#define CK(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      set_error(std::string("CUDA error: ") + cudaGetErrorString(e_) + " at " #call); \
+      return LCQMC_E_CUDA;                                                           \
+    }                                                                                \
+  } while (0)
+
+// ---- method tables (host) ------------------------------------------------------
+// Poisson(mu) thresholds T[k] = floor(2^64 P(K <= k)), from the recurrence
+// P(0) = e^{-mu}, P(k) = P(k-1) mu / k; saturated at 2^64 - 1.
+static void poisson_table(double mu, uint64_t *T) {
+  double pk = std::exp(-mu), cdf = 0.0;
+  for (int k = 0; k < KMAX; ++k) {
+    if (k > 0) pk = pk * mu / (double)k;
+    cdf += pk;
+    const double x = std::ldexp(cdf, 64);
+    T[k] = (x >= 18446744073709551616.0) ? UINT64_MAX : (uint64_t)x;
+  }
+}
+
+static int fixed_exponent(const ChainSpec &c) {
+  const double total = (double)c.Q * (double)c.L * c.beta;
+  int e;
+  const double m = std::frexp(total, &e);
+  const int cl = (m == 0.5) ? e - 1 : e;
+  return std::min(62, std::max(0, 60 - cl));
+}
+
+int validate_spec(int64_t L, double S, double J, double beta, ChainSpec &out) {
+  const double twoS = 2.0 * S;
+  if (!(L >= 2) || (L & 1)) {
+    set_error("L must be even and >= 2 (odd L frustrates the periodic antiferromagnet)");
+    return LCQMC_E_INVAL;
+  }
+  if (!(twoS == 1.0 || twoS == 2.0)) {
+    set_error("2S must be 1 or 2");
+    return LCQMC_E_INVAL;
+  }
+  if (!(J > 0.0) || !std::isfinite(J) || !(beta > 0.0) || !std::isfinite(beta)) {
+    set_error("J and beta must be positive and finite");
+    return LCQMC_E_INVAL;
+  }
+  out.L = L;
+  out.Q = (int)twoS;
+  out.J = J;
+  out.beta = beta;
+  const double w = 16.0 / J;
+  const double nw = std::ceil(beta / w);
+  const double ncell = nw * (double)L * out.Q * out.Q;
+  if (!(ncell < 2147483000.0) || (double)L * out.Q > 1.0e9) {
+    set_error("too many cells (bond x time window) for 32-bit indices");
+    return LCQMC_E_ID_OVERFLOW;
+  }
+  return LCQMC_OK;
+}
+
+static int64_t vertex_estimate(const ChainSpec &c) {
+  const double m = 0.8 * c.Q * c.Q * c.J * c.beta * (double)c.L;
+  return (int64_t)(m + 16.0 * std::sqrt(m) + 256.0);
+}
+static int64_t op_estimate(const ChainSpec &c) {
+  const double m = 0.45 * c.Q * c.Q * c.J * c.beta * (double)c.L;
+  return (int64_t)(m + 16.0 * std::sqrt(m) + 256.0);
+}
+
+struct Geo {
+  int64_t nsub, nbond, nwin, nblk, ncell, ntile, nsiteblk, nbondblk;
+  double w;
+};
+static Geo geo_of(const ChainSpec &c) {
+  Geo g;
+  g.nsub = c.L * c.Q;
+  g.nbond = c.L * c.Q * c.Q;
+  g.w = 16.0 / c.J;
+  g.nwin = std::max<int64_t>(1, (int64_t)std::ceil(c.beta / g.w));
+  g.nblk = (g.nwin + TW - 1) / TW;
+  g.ncell = g.nbond * g.nwin;
+  g.ntile = (g.ncell + TILE - 1) / TILE;
+  g.nsiteblk = (c.L + SITE_BLOCK - 1) / SITE_BLOCK;
+  g.nbondblk = (g.nbond + BOND_BLOCK - 1) / BOND_BLOCK;
+  return g;
+}
+
+size_t Engine::estimate_footprint(const std::vector<ChainSpec> &specs, int ring_cap) {
+  size_t bytes = 0;
+  int64_t vc = 4096;
+  for (const auto &c : specs) {
+    Geo g = geo_of(c);
+    bytes += 2 * (g.nsub + 2 * 4 * (g.ncell + 1) + 8 * op_estimate(c));
+    bytes += 8 * KMAX + 16 * c.L + sizeof(lcqmc_record) * ring_cap;
+    bytes += 4 * (g.ncell + 1) + 64 * g.ntile + 48 * g.nsiteblk + (g.nblk + 1) * g.nbond +
+             14 * g.nsub + sizeof(DevChain) + 8 * (g.ntile + g.nsiteblk + g.nbondblk);
+    vc += (vertex_estimate(c) + 127) / 128 * 128;
+  }
+  bytes += (size_t)vc * (8 + 1 + 12 + 24) + 3 * (size_t)(vc / 32 + 1) * 4;
+  return bytes;
+}
+
+// ---- allocation ------------------------------------------------------------------------
+void *Engine::dalloc(size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void *p = nullptr;
+  if (has_alloc_) {
+    p = alloc_.alloc(bytes, alloc_.ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  return p;
+}
+void Engine::dfree(void *p) {
+  if (!p) return;
+  if (has_alloc_)
+    alloc_.free(p, alloc_.ctx);
+  else
+    cudaFree(p);
+}
+
+#define DALLOC(ptr, type, count)                                                    \
+  do {                                                                              \
+    ptr = (type *)dalloc(sizeof(type) * (size_t)(count));                           \
+    if (!ptr) {                                                                     \
+      set_error("device allocation of " + std::to_string(sizeof(type) * (size_t)(count)) + \
+                " bytes failed");                                                   \
+      return LCQMC_E_NOMEM;                                                         \
+    }                                                                               \
+  } while (0)
+
+void Engine::free_vertex() {
+  dfree(s_.vtau);
+  dfree(s_.vflag);
+  dfree(s_.pl);
+  dfree(s_.pr);
+  dfree(s_.parent);
+  dfree(s_.accW);
+  dfree(s_.accC);
+  dfree(s_.accS);
+  dfree(s_.openmark);
+  dfree(s_.openroot);
+  dfree(s_.flipbits);
+  s_.vtau = nullptr;
+  s_.vflag = nullptr;
+  s_.pl = s_.pr = s_.parent = nullptr;
+  s_.accW = s_.accC = s_.accS = nullptr;
+  s_.openmark = s_.openroot = s_.flipbits = nullptr;
+  vertex_bytes_ = 0;
+}
+
+int Engine::alloc_vertex(int64_t vcap) {
+  free_vertex();
+  vcap = (vcap + 127) / 128 * 128;
+  DALLOC(s_.vtau, double, vcap);
+  DALLOC(s_.vflag, uint8_t, vcap);
+  DALLOC(s_.pl, int32_t, vcap);
+  DALLOC(s_.pr, int32_t, vcap);
+  DALLOC(s_.parent, int32_t, vcap);
+  DALLOC(s_.accW, unsigned long long, vcap);
+  DALLOC(s_.accC, unsigned long long, vcap);
+  DALLOC(s_.accS, unsigned long long, vcap);
+  const int64_t nw = vcap / 32 + 1;
+  DALLOC(s_.openmark, uint32_t, nw);
+  DALLOC(s_.openroot, uint32_t, nw);
+  DALLOC(s_.flipbits, uint32_t, nw);
+  CK(cudaMemsetAsync(s_.accW, 0, sizeof(unsigned long long) * vcap, st_));
+  CK(cudaMemsetAsync(s_.accC, 0, sizeof(unsigned long long) * vcap, st_));
+  CK(cudaMemsetAsync(s_.accS, 0, sizeof(unsigned long long) * vcap, st_));
+  s_.vcap = vcap;
+  vcap_ = vcap;
+  vertex_bytes_ = (size_t)vcap * (8 + 1 + 12 + 24) + 3 * (size_t)nw * 4;
+  L_.s = s_;
+  if (gexec_) {
+    cudaGraphExecDestroy(gexec_);
+    gexec_ = nullptr;
+  }
+  return LCQMC_OK;
+}
+
+Engine::~Engine() {
+  if (st_) cudaStreamSynchronize(st_);
+  if (gexec_) cudaGraphExecDestroy(gexec_);
+  for (auto e : ev_) cudaEventDestroy(e);
+  free_vertex();
+  for (auto &b : buf_) {
+    for (int k = 0; k < 2; ++k) {
+      dfree(b.s0[k]);
+      dfree(b.op_ptr[k]);
+      dfree(b.op_tau[k]);
+    }
+    dfree(b.T_last);
+    dfree(b.cosx);
+    dfree(b.sinx);
+    dfree(b.ring);
+  }
+  dfree(dch_);
+  dfree(tile_tab_);
+  dfree(site_tab_);
+  dfree(bond_tab_);
+  dfree(s_.vptr);
+  dfree(s_.tile_sum);
+  dfree(s_.tile_pref);
+  dfree(s_.tile_sum2);
+  dfree(s_.tile_pref2);
+  dfree(s_.tile_roots);
+  dfree(s_.tile_sw2);
+  dfree(s_.tile_sf2);
+  dfree(s_.site_free);
+  dfree(s_.site_sw2);
+  dfree(s_.site_sf2);
+  dfree(s_.bpar);
+  dfree(s_.cut_node);
+  dfree(s_.cut_cell);
+  dfree(s_.free_min);
+  dfree(s_.cut_cross);
+  dfree(s_.free_len);
+  dfree(s_.status);
+  dfree(s_.need);
+  if (own_stream_ && st_) cudaStreamDestroy(st_);
+}
+
+int Engine::init(const std::vector<ChainSpec> &specs, void *stream, const lcqmc_allocator *alloc,
+                 int ring_cap) {
+  if (specs.empty()) {
+    set_error("empty batch");
+    return LCQMC_E_INVAL;
+  }
+  CK(cudaGetDevice(&device_));
+  if (init_kernel_attributes() != 0) {
+    set_error("cudaFuncSetAttribute failed");
+    return LCQMC_E_CUDA;
+  }
+  if (alloc && alloc->alloc && alloc->free) {
+    alloc_ = *alloc;
+    has_alloc_ = true;
+  }
+  if (stream) {
+    st_ = (cudaStream_t)stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&st_, cudaStreamNonBlocking));
+    own_stream_ = true;
+  }
+  ring_cap_ = ring_cap;
+  // Order chains: Q=1 group first (tables), but keep the caller's chain index.
+  spec_ = specs;
+  const int nc = (int)specs.size();
+  hch.assign(nc, DevChain{});
+  buf_.assign(nc, ChainBuf{});
+  rec_read_.assign(nc, 0);
+  std::vector<int2> ttab, stab, btab;
+  int64_t cell_off = 0, bpar_off = 0, sub_off = 0, vest = 4096;
+  for (int q = 0; q < 2; ++q) {
+    L_.tile0[q] = (int64_t)ttab.size();
+    L_.site0[q] = (int64_t)stab.size();
+    L_.bond0[q] = (int64_t)btab.size();
+    for (int c = 0; c < nc; ++c) {
+      if (specs[c].Q != q + 1) continue;
+      const Geo g = geo_of(specs[c]);
+      DevChain &d = hch[c];
+      d.L = (int32_t)specs[c].L;
+      d.Q = specs[c].Q;
+      d.nsub = (int32_t)g.nsub;
+      d.nbond = (int32_t)g.nbond;
+      d.nwin = (int32_t)g.nwin;
+      d.nblk = (int32_t)g.nblk;
+      d.ncell = (int32_t)g.ncell;
+      d.ntile = (int32_t)g.ntile;
+      d.nsiteblk = (int32_t)g.nsiteblk;
+      d.F = fixed_exponent(specs[c]);
+      d.ring_cap = ring_cap;
+      d.beta = specs[c].beta;
+      d.J = specs[c].J;
+      d.w = g.w;
+      d.seed = specs[c].seed;
+      d.cell_off = cell_off;
+      d.tile0 = (int64_t)ttab.size();
+      d.site0 = (int64_t)stab.size();
+      d.bpar_off = bpar_off;
+      d.sub_off = sub_off;
+      d.op_cap = op_estimate(specs[c]);
+      cell_off += g.ncell + 1;
+      bpar_off += (g.nblk + 1) * g.nbond;
+      sub_off += g.nsub;
+      for (int64_t t = 0; t < g.ntile; ++t) ttab.push_back(make_int2(c, (int)t));
+      for (int64_t t = 0; t < g.nsiteblk; ++t) stab.push_back(make_int2(c, (int)t));
+      for (int64_t t = 0; t < g.nbondblk; ++t) btab.push_back(make_int2(c, (int)t));
+      vest += (vertex_estimate(specs[c]) + 127) / 128 * 128;
+    }
+    L_.ntile[q] = (int64_t)ttab.size() - L_.tile0[q];
+    L_.nsiteblk[q] = (int64_t)stab.size() - L_.site0[q];
+    L_.nbondblk[q] = (int64_t)btab.size() - L_.bond0[q];
+  }
+  ncell_tot_ = cell_off;
+  bpar_tot_ = bpar_off;
+  nsub_tot_ = sub_off;
+  ntile_tot_ = (int64_t)ttab.size();
+  nsiteblk_tot_ = (int64_t)stab.size();
+  nbondblk_tot_ = (int64_t)btab.size();
+
+  // Per-chain persistent buffers and tables; Neel start, no operators.
+  std::vector<uint64_t> T(KMAX);
+  for (int c = 0; c < nc; ++c) {
+    DevChain &d = hch[c];
+    ChainBuf &b = buf_[c];
+    for (int k = 0; k < 2; ++k) {
+      DALLOC(b.s0[k], uint8_t, d.nsub);
+      DALLOC(b.op_ptr[k], int32_t, (int64_t)d.ncell + 1);
+      DALLOC(b.op_tau[k], double, d.op_cap);
+      d.s0[k] = b.s0[k];
+      d.op_ptr[k] = b.op_ptr[k];
+      d.op_tau[k] = b.op_tau[k];
+    }
+    std::vector<uint8_t> s0(d.nsub);
+    for (int u = 0; u < d.nsub; ++u) s0[u] = (uint8_t)((u / d.Q) & 1);
+    CK(cudaMemcpyAsync(b.s0[0], s0.data(), d.nsub, cudaMemcpyHostToDevice, st_));
+    CK(cudaMemsetAsync(b.op_ptr[0], 0, sizeof(int32_t) * ((size_t)d.ncell + 1), st_));
+    const double t0 = (double)(d.nwin - 1) * d.w;
+    const double dl = d.beta - t0;
+    poisson_table(dl > 0.0 ? d.J * dl * 0.5 : 0.0, T.data());
+    DALLOC(b.T_last, uint64_t, KMAX);
+    CK(cudaMemcpyAsync(b.T_last, T.data(), 8 * KMAX, cudaMemcpyHostToDevice, st_));
+    std::vector<double> cs(d.L), sn(d.L);
+    for (int x = 0; x < d.L; ++x) {
+      const double ang = (2.0 * M_PI * (double)x) / (double)d.L;
+      cs[x] = std::cos(ang);
+      sn[x] = std::sin(ang);
+    }
+    DALLOC(b.cosx, double, d.L);
+    DALLOC(b.sinx, double, d.L);
+    CK(cudaMemcpyAsync(b.cosx, cs.data(), 8 * (size_t)d.L, cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync(b.sinx, sn.data(), 8 * (size_t)d.L, cudaMemcpyHostToDevice, st_));
+    DALLOC(b.ring, lcqmc_record, ring_cap);
+    d.T_last = b.T_last;
+    d.cosx = b.cosx;
+    d.sinx = b.sinx;
+    d.ring = b.ring;
+    op_bytes_ += 2 * (8 * (size_t)d.op_cap);
+    CK(cudaStreamSynchronize(st_));  // host vectors above go out of scope
+  }
+  poisson_table(CELL_MEAN, T.data());
+  set_full_table(T.data(), st_);
+
+  DALLOC(dch_, DevChain, nc);
+  DALLOC(tile_tab_, int2, std::max<int64_t>(1, ntile_tot_));
+  DALLOC(site_tab_, int2, std::max<int64_t>(1, nsiteblk_tot_));
+  DALLOC(bond_tab_, int2, std::max<int64_t>(1, nbondblk_tot_));
+  CK(cudaMemcpyAsync(dch_, hch.data(), sizeof(DevChain) * nc, cudaMemcpyHostToDevice, st_));
+  CK(cudaMemcpyAsync(tile_tab_, ttab.data(), sizeof(int2) * ttab.size(), cudaMemcpyHostToDevice, st_));
+  CK(cudaMemcpyAsync(site_tab_, stab.data(), sizeof(int2) * stab.size(), cudaMemcpyHostToDevice, st_));
+  CK(cudaMemcpyAsync(bond_tab_, btab.data(), sizeof(int2) * btab.size(), cudaMemcpyHostToDevice, st_));
+
+  const int64_t nt = std::max<int64_t>(1, ntile_tot_), ns = std::max<int64_t>(1, nsiteblk_tot_);
+  DALLOC(s_.vptr, int32_t, ncell_tot_);
+  DALLOC(s_.tile_sum, int64_t, nt);
+  DALLOC(s_.tile_pref, int64_t, nt);
+  DALLOC(s_.tile_sum2, int64_t, nt);
+  DALLOC(s_.tile_pref2, int64_t, nt);
+  DALLOC(s_.tile_roots, int64_t, nt);
+  DALLOC(s_.tile_sw2, unsigned long long, 2 * nt);
+  DALLOC(s_.tile_sf2, unsigned long long, 2 * nt);
+  DALLOC(s_.site_free, int64_t, ns);
+  DALLOC(s_.site_sw2, unsigned long long, 2 * ns);
+  DALLOC(s_.site_sf2, unsigned long long, 2 * ns);
+  DALLOC(s_.bpar, uint8_t, bpar_tot_);
+  DALLOC(s_.cut_node, int32_t, nsub_tot_);
+  DALLOC(s_.cut_cell, int32_t, nsub_tot_);
+  DALLOC(s_.free_min, int32_t, nsub_tot_);
+  DALLOC(s_.cut_cross, int8_t, nsub_tot_);
+  DALLOC(s_.free_len, int8_t, nsub_tot_);
+  DALLOC(s_.status, int, 1);
+  DALLOC(s_.need, int64_t, 4);
+  CK(cudaMemsetAsync(s_.status, 0, sizeof(int), st_));
+  fixed_bytes_ = 4 * (size_t)ncell_tot_ + 64 * (size_t)nt + 48 * (size_t)ns + bpar_tot_ +
+                 14 * (size_t)nsub_tot_ + sizeof(DevChain) * nc;
+  for (auto &d : hch)
+    fixed_bytes_ += 2 * ((size_t)d.nsub + 4 * ((size_t)d.ncell + 1)) + 8 * KMAX + 16 * (size_t)d.L +
+                    sizeof(lcqmc_record) * ring_cap;
+
+  L_.ch = dch_;
+  L_.nchains = nc;
+  L_.tile_tab = tile_tab_;
+  L_.site_tab = site_tab_;
+  L_.bond_tab = bond_tab_;
+  L_.s = s_;
+  int rc = alloc_vertex(vest);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(st_));
+  return LCQMC_OK;
+}
+
+// ---- update sequence ---------------------------------------------------------------------
+int Engine::enqueue_one(bool timed, int slot) {
+  const int64_t nw = vcap_ / 32 + 1;
+  auto mark = [&](int k) {
+    if (timed) cudaEventRecord(ev_[slot * (LCQMC_NPHASE + 1) + k], st_);
+  };
+  mark(0);
+  launch_bond_parity(L_, st_);
+  launch_insert(L_, 0, st_);
+  mark(1);
+  launch_scan(L_, 0, st_);
+  launch_chain_bases(L_, st_);
+  CK(cudaMemsetAsync(s_.openmark, 0, 4 * nw, st_));
+  CK(cudaMemsetAsync(s_.openroot, 0, 4 * nw, st_));
+  CK(cudaMemsetAsync(s_.flipbits, 0, 4 * nw, st_));
+  launch_insert(L_, 1, st_);
+  launch_cut(L_, st_);
+  mark(2);
+  launch_link(L_, st_);
+  mark(3);
+  launch_compress(L_, st_);
+  mark(4);
+  launch_est(L_, st_);
+  mark(5);
+  launch_scan(L_, 1, st_);
+  launch_compact(L_, st_);
+  mark(6);
+  launch_sites(L_, st_);
+  launch_final(L_, st_);
+  mark(7);
+  CK(cudaGetLastError());
+  return LCQMC_OK;
+}
+
+int Engine::capture() {
+  if (gexec_) return LCQMC_OK;
+  cudaGraph_t g;
+  CK(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_one(false, 0);
+  cudaError_t e = cudaStreamEndCapture(st_, &g);
+  if (rc) return rc;
+  CK(e);
+  CK(cudaGraphInstantiate(&gexec_, g, 0));
+  cudaGraphDestroy(g);
+  return LCQMC_OK;
+}
+
+int Engine::update(int64_t n) {
+  if (n < 0) {
+    set_error("negative update count");
+    return LCQMC_E_INVAL;
+  }
+  if (n == 0) return LCQMC_OK;
+  if (pending_ == 0) pending_sweep0_ = hch[0].sweep;
+  if (timing_) {
+    const int per = LCQMC_NPHASE + 1;
+    while ((int)ev_.size() < (ev_used_ + (int)n) * per) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      ev_.push_back(e);
+    }
+    for (int64_t i = 0; i < n; ++i) {
+      int rc = enqueue_one(true, ev_used_++);
+      if (rc) return rc;
+    }
+  } else {
+    int rc = capture();
+    if (rc) return rc;
+    for (int64_t i = 0; i < n; ++i) CK(cudaGraphLaunch(gexec_, st_));
+  }
+  pending_ += n;
+  return LCQMC_OK;
+}
+
+int Engine::pull_chains() {
+  CK(cudaMemcpyAsync(hch.data(), dch_, sizeof(DevChain) * hch.size(), cudaMemcpyDeviceToHost, st_));
+  CK(cudaStreamSynchronize(st_));
+  return LCQMC_OK;
+}
+
+int Engine::push_chains() {
+  CK(cudaMemcpyAsync(dch_, hch.data(), sizeof(DevChain) * hch.size(), cudaMemcpyHostToDevice, st_));
+  CK(cudaStreamSynchronize(st_));
+  return LCQMC_OK;
+}
+
+int Engine::grow_ops(int64_t c, int64_t need) {
+  DevChain &d = hch[c];
+  ChainBuf &b = buf_[c];
+  const int64_t cap = need + need / 4 + 1024;
+  const int64_t nold = 0;
+  (void)nold;
+  for (int k = 0; k < 2; ++k) {
+    double *p;
+    DALLOC(p, double, cap);
+    if (k == d.cur) {
+      int32_t n_off = 0;
+      CK(cudaMemcpyAsync(&n_off, b.op_ptr[k] + d.ncell, 4, cudaMemcpyDeviceToHost, st_));
+      CK(cudaStreamSynchronize(st_));
+      if (n_off > 0)
+        CK(cudaMemcpyAsync(p, b.op_tau[k], 8 * (size_t)n_off, cudaMemcpyDeviceToDevice, st_));
+    }
+    CK(cudaStreamSynchronize(st_));
+    dfree(b.op_tau[k]);
+    b.op_tau[k] = p;
+    d.op_tau[k] = p;
+  }
+  op_bytes_ += 2 * 8 * (size_t)(cap - d.op_cap);
+  d.op_cap = cap;
+  return LCQMC_OK;
+}
+
+int Engine::sync() {
+  for (int guard = 0; guard < 64; ++guard) {
+    CK(cudaStreamSynchronize(st_));
+    int status = 0;
+    CK(cudaMemcpy(&status, s_.status, sizeof(int), cudaMemcpyDeviceToHost));
+    int rc = pull_chains();
+    if (rc) return rc;
+    if (timing_ && ev_used_ > 0) {
+      for (int u = 0; u < ev_used_; ++u)
+        for (int k = 0; k < LCQMC_NPHASE; ++k) {
+          float ms = 0.f;
+          if (cudaEventElapsedTime(&ms, ev_[u * (LCQMC_NPHASE + 1) + k],
+                                   ev_[u * (LCQMC_NPHASE + 1) + k + 1]) == cudaSuccess)
+            phase_ms_[k] += ms;
+        }
+      ev_used_ = 0;
+    }
+    if (status == 0) {
+      pending_ = 0;
+      return LCQMC_OK;
+    }
+    const int64_t done = (int64_t)(uint32_t)(hch[0].sweep - pending_sweep0_);
+    const int64_t remaining = pending_ - done;
+    if (status & (ST_TIMEOUT | ST_INTERNAL | ST_BADSTATE | ST_ID_OVERFLOW)) {
+      CK(cudaMemsetAsync(s_.status, 0, sizeof(int), st_));
+      pending_ = 0;
+      if (status & ST_TIMEOUT) {
+        set_error("a bounded union-find wait ran out on the device");
+        return LCQMC_E_DEVICE_TIMEOUT;
+      }
+      if (status & ST_ID_OVERFLOW) {
+        set_error("more than 2^31 graph vertices in one chain");
+        return LCQMC_E_ID_OVERFLOW;
+      }
+      if (status & ST_BADSTATE) {
+        set_error("configuration violates the world-line constraint at tau=0");
+        return LCQMC_E_STATE;
+      }
+      set_error("internal consistency check failed on the device");
+      return LCQMC_E_CUDA;
+    }
+    if (status & ST_VTX_OVERFLOW) {
+      int64_t need = 0;
+      CK(cudaMemcpy(&need, s_.need, 8, cudaMemcpyDeviceToHost));
+      rc = alloc_vertex(need + need / 8 + 4096);
+      if (rc) return rc;
+    }
+    if (status & ST_OP_OVERFLOW) {
+      for (int64_t c = 0; c < (int64_t)hch.size(); ++c)
+        if (hch[c].n_off_new > hch[c].op_cap) {
+          rc = grow_ops(c, hch[c].n_off_new);
+          if (rc) return rc;
+        }
+      rc = push_chains();
+      if (rc) return rc;
+      if (gexec_) {
+        cudaGraphExecDestroy(gexec_);
+        gexec_ = nullptr;
+      }
+    }
+    CK(cudaMemsetAsync(s_.status, 0, sizeof(int), st_));
+    pending_ = 0;
+    if (remaining > 0) {
+      rc = update(remaining);
+      if (rc) return rc;
+    }
+  }
+  set_error("capacity growth did not converge");
+  return LCQMC_E_NOMEM;
+}
+
+// ---- measurements ------------------------------------------------------------------------
+int Engine::measure(int64_t c, lcqmc_obs *out) {
+  int rc = sync();
+  if (rc) return rc;
+  const DevChain &d = hch[c];
+  std::memset(out, 0, sizeof(*out));
+  out->n_updates = d.n_updates;
+  for (int k = 0; k < 8; ++k) {
+    out->sum[k] = d.sum[k];
+    out->sumsq[k] = d.sumsq[k];
+  }
+  if (d.n_updates > 0 && d.sum[2] > 0) {
+    const double r = d.sum[1] / d.sum[2] - 1.0;
+    out->xi = r > 0 ? (double)d.L / (2.0 * M_PI) * std::sqrt(r) : 0.0;
+  }
+  return LCQMC_OK;
+}
+
+int Engine::reset_obs(int64_t c) {
+  int rc = sync();
+  if (rc) return rc;
+  DevChain &d = hch[c];
+  d.n_updates = 0;
+  for (int k = 0; k < 8; ++k) d.sum[k] = d.sumsq[k] = 0.0;
+  return push_chains();
+}
+
+int Engine::records(int64_t c, lcqmc_record *out, int64_t max, int64_t *count) {
+  int rc = sync();
+  if (rc) return rc;
+  const DevChain &d = hch[c];
+  int64_t &rd = rec_read_[c];
+  if (d.n_rec - rd > d.ring_cap) rd = d.n_rec - d.ring_cap;
+  int64_t avail = d.n_rec - rd;
+  const int64_t m = std::min<int64_t>(avail, std::max<int64_t>(0, max));
+  for (int64_t i = 0; i < m; ++i) {
+    const int64_t slot = (rd + i) % d.ring_cap;
+    CK(cudaMemcpyAsync(out + i, buf_[c].ring + slot, sizeof(lcqmc_record), cudaMemcpyDeviceToHost, st_));
+  }
+  CK(cudaStreamSynchronize(st_));
+  rd += m;
+  *count = m;
+  return LCQMC_OK;
+}
+
+int Engine::geometry(int64_t c, lcqmc_geometry *out) {
+  int rc = sync();
+  if (rc) return rc;
+  const DevChain &d = hch[c];
+  out->L = d.L;
+  out->nsub = d.nsub;
+  out->nbond = d.nbond;
+  out->nwin = d.nwin;
+  out->ncell = d.ncell;
+  out->Q = d.Q;
+  out->F = d.F;
+  out->J = d.J;
+  out->beta = d.beta;
+  out->w = d.w;
+  out->seed = d.seed;
+  out->sweep = d.sweep;
+  out->pad = 0;
+  return LCQMC_OK;
+}
+
+int Engine::export_config(int64_t c, uint8_t *s0, int32_t *op_ptr, double *op_tau, int64_t op_cap,
+                          int64_t *n_off) {
+  int rc = sync();
+  if (rc) return rc;
+  const DevChain &d = hch[c];
+  const ChainBuf &b = buf_[c];
+  int32_t n = 0;
+  CK(cudaMemcpy(&n, b.op_ptr[d.cur] + d.ncell, 4, cudaMemcpyDeviceToHost));
+  if (n_off) *n_off = n;
+  if (s0) CK(cudaMemcpy(s0, b.s0[d.cur], d.nsub, cudaMemcpyDeviceToHost));
+  if (op_ptr) CK(cudaMemcpy(op_ptr, b.op_ptr[d.cur], 4 * ((size_t)d.ncell + 1), cudaMemcpyDeviceToHost));
+  if (op_tau) {
+    if (op_cap < n) {
+      set_error("op_tau buffer too small");
+      return LCQMC_E_CAPACITY;
+    }
+    if (n > 0) CK(cudaMemcpy(op_tau, b.op_tau[d.cur], 8 * (size_t)n, cudaMemcpyDeviceToHost));
+  }
+  return LCQMC_OK;
+}
+
+// World-line validity of an imported state (Sec. 2): every operator in its
+// cell's window, ascending within the cell, acting on antiparallel spins; the
+// spins at tau = beta equal those at tau = 0 (up to a subspin permutation of
+// each site for S = 1).
+static int check_state(const DevChain &d, const uint8_t *s0, const int32_t *op_ptr,
+                       const double *op_tau, int64_t n_off) {
+  if (op_ptr[0] != 0 || op_ptr[d.ncell] != n_off) return LCQMC_E_STATE;
+  for (int u = 0; u < d.nsub; ++u)
+    if (s0[u] > 1) return LCQMC_E_STATE;
+  struct Ev {
+    double tau;
+    int bond;
+  };
+  std::vector<Ev> ev;
+  ev.reserve(n_off);
+  for (int b = 0; b < d.nbond; ++b)
+    for (int j = 0; j < d.nwin; ++j) {
+      const int blk = j / TW, jj = j - blk * TW, tw = std::min(TW, d.nwin - blk * TW);
+      const int c = blk * d.nbond * TW + b * tw + jj;
+      if (op_ptr[c + 1] < op_ptr[c]) return LCQMC_E_STATE;
+      const double t0 = (double)j * d.w;
+      const double t_end = (j == d.nwin - 1) ? d.beta : (double)(j + 1) * d.w;
+      for (int q = op_ptr[c]; q < op_ptr[c + 1]; ++q) {
+        if (!(op_tau[q] >= t0 && op_tau[q] < t_end)) return LCQMC_E_STATE;
+        if (q > op_ptr[c] && op_tau[q] < op_tau[q - 1]) return LCQMC_E_STATE;
+        ev.push_back(Ev{op_tau[q], b});
+      }
+    }
+  std::sort(ev.begin(), ev.end(), [](const Ev &a, const Ev &b) {
+    return a.tau < b.tau || (a.tau == b.tau && a.bond < b.bond);
+  });
+  std::vector<uint8_t> s(s0, s0 + d.nsub);
+  const int Q = d.Q;
+  for (const Ev &e : ev) {
+    const int i = e.bond / (Q * Q), a = (e.bond / Q) % Q, a2 = e.bond % Q;
+    const int ul = i * Q + a, ur = ((i + 1) % d.L) * Q + a2;
+    if (s[ul] == s[ur]) return LCQMC_E_STATE;
+    s[ul] ^= 1;
+    s[ur] ^= 1;
+  }
+  for (int i = 0; i < d.L; ++i) {
+    int top = 0, bot = 0;
+    for (int a = 0; a < Q; ++a) {
+      top += s[i * Q + a];
+      bot += s0[i * Q + a];
+    }
+    if (top != bot) return LCQMC_E_STATE;
+  }
+  return LCQMC_OK;
+}
+
+int Engine::import_config(int64_t c, const uint8_t *s0, const int32_t *op_ptr, const double *op_tau,
+                          int64_t n_off, uint32_t sweep) {
+  int rc = sync();
+  if (rc) return rc;
+  DevChain &d = hch[c];
+  if (n_off < 0 || (n_off > 0 && !op_tau) || !s0 || !op_ptr) {
+    set_error("bad arguments to import_config");
+    return LCQMC_E_INVAL;
+  }
+  rc = check_state(d, s0, op_ptr, op_tau, n_off);
+  if (rc) {
+    set_error("imported configuration is not a valid world-line state");
+    return rc;
+  }
+  if (n_off > d.op_cap) {
+    rc = grow_ops(c, n_off);
+    if (rc) return rc;
+    if (gexec_) {
+      cudaGraphExecDestroy(gexec_);
+      gexec_ = nullptr;
+    }
+  }
+  const ChainBuf &b = buf_[c];
+  CK(cudaMemcpy(b.s0[d.cur], s0, d.nsub, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(b.op_ptr[d.cur], op_ptr, 4 * ((size_t)d.ncell + 1), cudaMemcpyHostToDevice));
+  if (n_off > 0) CK(cudaMemcpy(b.op_tau[d.cur], op_tau, 8 * (size_t)n_off, cudaMemcpyHostToDevice));
+  d.sweep = sweep;
+  return push_chains();
+}
+
+int Engine::export_graph(int64_t c, double *tau, uint8_t *flag, int32_t *pl, int32_t *pr,
+                         int32_t *root, int64_t n_cap, int64_t *n) {
+  int rc = sync();
+  if (rc) return rc;
+  const DevChain &d = hch[c];
+  const int64_t nv = d.n;
+  if (n) *n = nv;
+  if (!tau && !flag && !pl && !pr && !root) return LCQMC_OK;
+  if (n_cap < nv) {
+    set_error("graph buffers too small");
+    return LCQMC_E_CAPACITY;
+  }
+  const int64_t vb = d.vtx_base;
+  if (tau) CK(cudaMemcpy(tau, s_.vtau + vb, 8 * nv, cudaMemcpyDeviceToHost));
+  if (flag) {
+    CK(cudaMemcpy(flag, s_.vflag + vb, nv, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < nv; ++i) flag[i] &= VF_OLD;
+  }
+  if (pl) CK(cudaMemcpy(pl, s_.pl + vb, 4 * nv, cudaMemcpyDeviceToHost));
+  if (pr) CK(cudaMemcpy(pr, s_.pr + vb, 4 * nv, cudaMemcpyDeviceToHost));
+  if (root) CK(cudaMemcpy(root, s_.parent + vb, 4 * nv, cudaMemcpyDeviceToHost));
+  return LCQMC_OK;
+}
+
+int Engine::export_cells(int64_t c, int32_t *vptr, int64_t cap) {
+  int rc = sync();
+  if (rc) return rc;
+  const DevChain &d = hch[c];
+  if (!vptr || cap < (int64_t)d.ncell + 1) {
+    set_error("cell offset buffer too small");
+    return LCQMC_E_CAPACITY;
+  }
+  CK(cudaMemcpy(vptr, s_.vptr + d.cell_off, 4 * ((size_t)d.ncell + 1), cudaMemcpyDeviceToHost));
+  return LCQMC_OK;
+}
+
+int Engine::set_phase_timing(int enable) {
+  int rc = sync();
+  if (rc) return rc;
+  timing_ = enable != 0;
+  for (double &x : phase_ms_) x = 0.0;
+  return LCQMC_OK;
+}
+
+int Engine::phase_times(double *ms, int nphase) {
+  int rc = sync();
+  if (rc) return rc;
+  for (int k = 0; k < nphase && k < LCQMC_NPHASE; ++k) ms[k] = phase_ms_[k];
+  return LCQMC_OK;
+}
+
+size_t Engine::footprint() const { return fixed_bytes_ + vertex_bytes_ + op_bytes_; }
+
+}  // namespace lcq

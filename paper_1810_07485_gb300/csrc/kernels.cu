@@ -1,0 +1,1028 @@
+// Kernels of one continuous-time loop-cluster update (Sec. 2 MC step, Sec. 3.2
+// union-find), batched over independent chains.  Work is cut into tiles of 128
+// consecutive cells (bond x time window) of one chain; a tile is one block.
+//
+// Phase order per update (the Sec. 4.3 cost table's rows in brackets):
+//   k_bond_parity    spin parity of every bond at each time-block start
+//   k_insert<0>      per cell: Poisson candidates, keep the antiparallel ones,
+//                    count vertices                                  [1, 2]
+//   k_scan_tiles<0>, k_chain_bases   vertex offsets per tile / chain
+//   k_insert<1>      regenerate, merge with old operators, write vertices [2]
+//   k_cut            last leg per subsite, tau=0 subspin permutation
+//   k_link           predecessor of each leg on both subsites; union of the two
+//                    fragments below each vertex (lock-free, min root)    [2]
+//   k_compress       root of every node, one coin per loop              [3]
+//   k_est            new operator flags, loop lengths (tile-local loops in
+//                    shared memory, others in global accumulators)      [4]
+//   k_scan_tiles<1>  operator offsets
+//   k_compact        next operator list, squared lengths of open loops  [8]
+//   k_sites          spins at tau = 0, vertex-free loops                [8]
+//   k_final          per-chain record, running sums, buffer swap
+#include <cstdio>
+
+#include "dev.cuh"
+#include "kernels.h"
+
+namespace lcq {
+
+__constant__ uint64_t c_T_full[KMAX];
+
+// ---- block-wide helpers (blockDim.x is a multiple of 32, <= 1024) ---------
+template <typename T>
+__device__ T warp_incl_scan(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+template <typename T>
+__device__ T block_excl_scan(T v, T *sm, T &total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T inc = warp_incl_scan(v);
+  if (lane == 31) sm[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    T x = (lane < nw) ? sm[lane] : T(0);
+    T xi = warp_incl_scan(x);
+    if (lane < nw) sm[lane] = xi - x;
+    if (lane == nw - 1) sm[32] = xi;
+  }
+  __syncthreads();
+  T res = sm[wid] + inc - v;
+  total = sm[32];
+  __syncthreads();
+  return res;
+}
+
+template <typename T>
+__device__ T block_sum(T v, T *sm) {
+  T tot;
+  block_excl_scan(v, sm, tot);
+  return tot;
+}
+
+// Exact block-wide sum of 128-bit values (warp shuffles of both halves).
+__device__ u128 block_sum_u128(u128 v) {
+  __shared__ u128 part[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  u128 x = v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long l = __shfl_down_sync(0xffffffffu, (unsigned long long)x, o);
+    unsigned long long h = __shfl_down_sync(0xffffffffu, (unsigned long long)(x >> 64), o);
+    x += ((u128)h << 64) | (u128)l;
+  }
+  if (lane == 0) part[wid] = x;
+  __syncthreads();
+  u128 t = 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < nw; ++i) t += part[i];
+    part[0] = t;
+  }
+  __syncthreads();
+  t = part[0];
+  __syncthreads();
+  return t;
+}
+
+__device__ __forceinline__ bool halted(const Scratch &s) { return __ldcg(s.status) != 0; }
+
+// ---- union-find (Sec. 3.2): min-root hooking with one CAS --------------------
+// parent[x] <= x always holds; a root is its own parent.  A link is made by a
+// single compare-and-swap on the larger root's parent word, which both checks
+// that it is still a root and attaches it: the lock of steps 4'-6' and the
+// pointer update in one instruction, with no weight kept.
+__device__ int uf_find(int32_t *par, int x, int *status) {
+  int p = __ldcg(par + x);
+  if (p == x) return x;
+  int prev = x;
+  for (int it = 0;; ++it) {
+    int next = __ldcg(par + p);
+    if (next >= p) break;
+    par[prev] = next;  // path halving: skip one level
+    prev = p;
+    p = next;
+    if (it > UF_MAX_ITERS) {
+      atomicOr(status, ST_TIMEOUT);
+      break;
+    }
+  }
+  return p;
+}
+
+__device__ void uf_union(int32_t *par, int a, int b, int *status) {
+  a = uf_find(par, a, status);
+  b = uf_find(par, b, status);
+  for (int it = 0; it < UF_MAX_ITERS; ++it) {
+    if (a == b) return;
+    if (a > b) {
+      int t = a;
+      a = b;
+      b = t;
+    }
+    int old = atomicCAS(par + b, b, a);
+    if (old == b) return;
+    b = old;  // b was attached meanwhile: continue from its new parent
+  }
+  atomicOr(status, ST_TIMEOUT);
+}
+
+// ---- bond parity at time-block starts ---------------------------------------
+// bpar[(blk) * nbond + b] = parity of the operators of bond b in time blocks
+// before blk; row nblk is the parity over the whole period.
+__global__ void k_bond_parity(const DevChain *__restrict__ ch, const int2 *__restrict__ tab,
+                              int64_t blk0, Scratch s) {
+  if (halted(s)) return;
+  const int2 t = tab[blk0 + blockIdx.x];
+  const DevChain &C = ch[t.x];
+  const int b = t.y * BOND_BLOCK + threadIdx.x;
+  if (b >= C.nbond) return;
+  const int32_t *op = C.op_ptr[C.cur];
+  uint8_t *row = s.bpar + C.bpar_off;
+  uint8_t p = 0;
+  row[b] = 0;
+  for (int blk = 0; blk < C.nblk; ++blk) {
+    int j0 = blk * TW;
+    int tw = min(TW, C.nwin - j0);
+    int c0 = blk * C.nbond * TW + b * tw;
+    p ^= (uint8_t)((op[c0 + tw] - op[c0]) & 1);
+    row[(int64_t)(blk + 1) * C.nbond + b] = p;
+  }
+}
+
+// ---- insertion (labeling, rules i-iii) --------------------------------------
+template <int Q>
+struct NbOps {
+  static constexpr int N = 4 * Q - 2;
+  int bond[N];
+  int o0[N], o1[N];
+};
+
+// Parity of the operators on the neighbour bonds ahead of (tau, b).
+template <int Q>
+__device__ __forceinline__ int nb_parity(const NbOps<Q> &X, const double *__restrict__ tau_arr,
+                                         double tau, int b) {
+  int p = 0;
+#pragma unroll
+  for (int k = 0; k < NbOps<Q>::N; ++k) {
+    for (int q = X.o0[k]; q < X.o1[k]; ++q) {
+      double t = tau_arr[q];
+      if (t < tau || (t == tau && X.bond[k] < b))
+        p ^= 1;
+      else
+        break;
+    }
+  }
+  return p;
+}
+
+template <int Q, int WRITE>
+__global__ void __launch_bounds__(TILE) k_insert(const DevChain *__restrict__ ch,
+                                                 const int2 *__restrict__ tab, int64_t blk0,
+                                                 Scratch s) {
+  __shared__ int64_t sm[33];
+  if (halted(s)) return;
+  const int64_t gt = blk0 + blockIdx.x;
+  const int2 t = tab[gt];
+  const DevChain &C = ch[t.x];
+  const int cell = t.y * TILE + threadIdx.x;
+  const bool valid = cell < C.ncell;
+  const int cur = C.cur;
+  const int32_t *op = C.op_ptr[cur];
+  const double *otau = C.op_tau[cur];
+  const uint8_t *s0 = C.s0[cur];
+  int32_t *vp = s.vptr + C.cell_off;
+
+  int cnt = 0;
+  int b = 0, j = 0;
+  int q0 = 0, q1 = 0, K = 0, par0 = 0;
+  double t0 = 0, t_end = 0, d = 0;
+  NbOps<Q> X;
+  U4 o0 = {0, 0, 0, 0};
+  const uint32_t k0 = (uint32_t)C.seed, k1 = (uint32_t)(C.seed >> 32);
+  if (valid) {
+    cell_bj(C, cell, b, j);
+    const int ul = left_sub<Q>(b), ur = right_sub<Q>(b, C.L);
+    const int blk = j / TW, jb = blk * TW;
+    const uint8_t *prow = s.bpar + C.bpar_off + (int64_t)blk * C.nbond;
+    par0 = (s0[ul] ^ s0[ur]) & 1;
+    int k = 0;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int u = side ? ur : ul;
+#pragma unroll
+      for (int m = 0; m < 2 * Q; ++m) {
+        const int bb = inc_bond<Q>(u, m, C.L);
+        if (bb == b) continue;
+        const int cj = cell_of(C, bb, j), cs = cell_of(C, bb, jb);
+        X.bond[k] = bb;
+        X.o0[k] = op[cj];
+        X.o1[k] = op[cj + 1];
+        par0 ^= (prow[bb] ^ (op[cj] - op[cs])) & 1;
+        ++k;
+      }
+    }
+    q0 = op[cell];
+    q1 = op[cell + 1];
+    t0 = (double)j * C.w;
+    t_end = (j == C.nwin - 1) ? C.beta : (double)(j + 1) * C.w;
+    d = t_end - t0;
+    o0 = philox(TAG_INSERT << 24, (uint32_t)b, (uint32_t)j, C.sweep, k0, k1);
+    const uint64_t U = (uint64_t)o0.x | ((uint64_t)o0.y << 32);
+    const uint64_t *T = (j == C.nwin - 1) ? C.T_last : c_T_full;
+    while (K < KMAX - 1 && U >= T[K]) ++K;
+  }
+
+  if (!WRITE) {
+    if (valid) {
+      U4 o2 = {0, 0, 0, 0};
+      int kept = 0;
+      for (int k = 0; k < K; ++k) {
+        uint64_t bits;
+        if (k == 0) {
+          bits = (uint64_t)o0.z | ((uint64_t)o0.w << 32);
+        } else if (k & 1) {
+          o2 = philox((TAG_INSERT << 24) | (uint32_t)((k + 1) >> 1), (uint32_t)b, (uint32_t)j,
+                      C.sweep, k0, k1);
+          bits = (uint64_t)o2.x | ((uint64_t)o2.y << 32);
+        } else {
+          bits = (uint64_t)o2.z | ((uint64_t)o2.w << 32);
+        }
+        const double u = __dmul_rn((double)(bits >> 11), 0x1p-53);
+        const double tau = __fma_rn(d, u, t0);
+        if (!(tau < t_end)) continue;
+        if ((par0 ^ nb_parity<Q>(X, otau, tau, b)) & 1) ++kept;
+      }
+      cnt = (q1 - q0) + kept;
+      vp[cell] = cnt;
+    }
+    const int64_t tot = block_sum<int64_t>((int64_t)cnt, sm);
+    if (threadIdx.x == 0) s.tile_sum[gt] = tot;
+    return;
+  }
+
+  // WRITE: offsets, then the merged vertex list of the cell.
+  if (valid) cnt = vp[cell];
+  int64_t tot;
+  const int64_t ex = block_excl_scan<int64_t>((int64_t)cnt, sm, tot);
+  if (!valid) return;
+  const int32_t off = (int32_t)(s.tile_pref[gt] + ex);
+  vp[cell] = off;
+  if (cell == C.ncell - 1) vp[C.ncell] = (int32_t)C.n;
+  if (cnt == 0) return;
+
+  uint64_t cu[KMAX];
+  double ct[KMAX];
+  int nk = 0;
+  U4 o2 = {0, 0, 0, 0};
+  for (int k = 0; k < K; ++k) {
+    uint64_t bits;
+    if (k == 0) {
+      bits = (uint64_t)o0.z | ((uint64_t)o0.w << 32);
+    } else if (k & 1) {
+      o2 = philox((TAG_INSERT << 24) | (uint32_t)((k + 1) >> 1), (uint32_t)b, (uint32_t)j,
+                  C.sweep, k0, k1);
+      bits = (uint64_t)o2.x | ((uint64_t)o2.y << 32);
+    } else {
+      bits = (uint64_t)o2.z | ((uint64_t)o2.w << 32);
+    }
+    const uint64_t u53 = bits >> 11;
+    const double tau = __fma_rn(d, __dmul_rn((double)u53, 0x1p-53), t0);
+    if (!(tau < t_end)) continue;
+    if (!((par0 ^ nb_parity<Q>(X, otau, tau, b)) & 1)) continue;
+    // insertion sort by u53 (stable: equal keys keep draw order)
+    int p = nk;
+    while (p > 0 && cu[p - 1] > u53) {
+      cu[p] = cu[p - 1];
+      ct[p] = ct[p - 1];
+      --p;
+    }
+    cu[p] = u53;
+    ct[p] = tau;
+    ++nk;
+  }
+  const int64_t vb = C.vtx_base;
+  int q = q0, ki = 0, r = off;
+  while (q < q1 || ki < nk) {
+    double tau;
+    uint8_t f;
+    if (q < q1 && (ki >= nk || otau[q] <= ct[ki])) {
+      tau = otau[q++];
+      f = VF_OLD;
+    } else {
+      tau = ct[ki++];
+      f = 0;
+    }
+    s.vtau[vb + r] = tau;
+    s.vflag[vb + r] = f;
+    s.parent[vb + r] = r;
+    ++r;
+  }
+  if (r - off != cnt) atomicOr(s.status, ST_INTERNAL);
+}
+
+// ---- per-chain scans of tile totals ------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(1024) k_scan_tiles(DevChain *__restrict__ ch, Scratch s) {
+  __shared__ int64_t sm[33];
+  if (halted(s)) return;
+  DevChain &C = ch[blockIdx.x];
+  const int64_t *in = MODE == 0 ? s.tile_sum : s.tile_sum2;
+  int64_t *out = MODE == 0 ? s.tile_pref : s.tile_pref2;
+  const int nt = C.ntile;
+  const int per = (nt + blockDim.x - 1) / blockDim.x;
+  const int lo = min(nt, (int)threadIdx.x * per), hi = min(nt, lo + per);
+  int64_t sum = 0;
+  for (int i = lo; i < hi; ++i) sum += in[C.tile0 + i];
+  int64_t total;
+  int64_t run = block_excl_scan<int64_t>(sum, sm, total);
+  for (int i = lo; i < hi; ++i) {
+    out[C.tile0 + i] = run;
+    run += in[C.tile0 + i];
+  }
+  if (threadIdx.x == 0) {
+    if (MODE == 0) {
+      C.n = total;
+    } else {
+      C.n_off_new = total;
+      if (total > C.op_cap) atomicOr(s.status, ST_OP_OVERFLOW);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_chain_bases(DevChain *__restrict__ ch, int nchains,
+                                                      Scratch s) {
+  __shared__ int64_t sm[33];
+  if (halted(s)) return;
+  int64_t base = 0;
+  bool bad = false;
+  for (int c0 = 0; c0 < nchains; c0 += blockDim.x) {
+    const int c = c0 + threadIdx.x;
+    int64_t sz = 0;
+    if (c < nchains) {
+      const int64_t n = ch[c].n;
+      if (n > (int64_t)0x7fffff00) bad = true;
+      sz = (n + 127) & ~(int64_t)127;
+    }
+    int64_t total;
+    const int64_t ex = block_excl_scan<int64_t>(sz, sm, total);
+    if (c < nchains) ch[c].vtx_base = base + ex;
+    base += total;
+  }
+  if (bad) atomicOr(s.status, ST_ID_OVERFLOW);
+  if (threadIdx.x == 0) {
+    s.need[0] = base;
+    if (base > s.vcap) atomicOr(s.status, ST_VTX_OVERFLOW);
+  }
+}
+
+// ---- tau = 0: last leg per subsite, subspin permutation, cut predecessors -----
+template <int Q>
+__device__ void last_leg(const DevChain &C, const int32_t *vp, const double *vtau, int64_t vb,
+                         int bond, int &id, int &cellc, double &tau) {
+  id = -1;
+  cellc = -1;
+  tau = 0.0;
+  for (int j = C.nwin - 1; j >= 0; --j) {
+    const int c = cell_of(C, bond, j);
+    const int a = vp[c], e = vp[c + 1];
+    if (e > a) {
+      id = e - 1;
+      cellc = c;
+      tau = vtau[vb + id];
+      return;
+    }
+  }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(SITE_BLOCK) k_cut(const DevChain *__restrict__ ch,
+                                                    const int2 *__restrict__ tab, int64_t blk0,
+                                                    Scratch s) {
+  if (halted(s)) return;
+  const int2 t = tab[blk0 + blockIdx.x];
+  const DevChain &C = ch[t.x];
+  const int i = t.y * SITE_BLOCK + threadIdx.x;
+  if (i >= C.L) return;
+  const int32_t *vp = s.vptr + C.cell_off;
+  const int64_t vb = C.vtx_base;
+  const uint8_t *s0 = C.s0[C.cur];
+  const uint8_t *ptot = s.bpar + C.bpar_off + (int64_t)C.nblk * C.nbond;
+  int last[Q], lastc[Q], top[Q];
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const int u = i * Q + a;
+    int best = -1, bestc = -1;
+    double bt = 0.0;
+    int par = 0;
+#pragma unroll
+    for (int m = 0; m < 2 * Q; ++m) {
+      const int bb = inc_bond<Q>(u, m, C.L);
+      par ^= ptot[bb];
+      int id, cc;
+      double tt;
+      last_leg<Q>(C, vp, s.vtau, vb, bb, id, cc, tt);
+      if (id >= 0 && (best < 0 || tt > bt || (tt == bt && id > best))) {
+        best = id;
+        bt = tt;
+        bestc = cc;
+      }
+    }
+    last[a] = best;
+    lastc[a] = bestc;
+    top[a] = (s0[u] ^ par) & 1;
+  }
+  // perm[a]: the bottom subspin that the top of subspin a continues into.
+  int perm[Q];
+  if (Q == 1) {
+    perm[0] = 0;
+  } else {
+    const int b0 = s0[i * Q] & 1, b1 = s0[i * Q + 1] & 1;
+    const bool ok_id = (top[0] == b0) && (top[1] == b1);
+    const bool ok_sw = (top[0] == b1) && (top[1] == b0);
+    int sw;
+    if (ok_id && ok_sw)
+      sw = coin(C, TAG_PERM, (uint32_t)i);
+    else if (ok_sw)
+      sw = 1;
+    else if (ok_id)
+      sw = 0;
+    else {
+      atomicOr(s.status, ST_BADSTATE);
+      sw = 0;
+    }
+    perm[0] = sw ? 1 : 0;
+    perm[1] = sw ? 0 : 1;
+  }
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    // Walk down through the cut: the bottom of subspin a is entered from the
+    // top of pinv(a), then possibly through empty subspins.
+    int x = a, cross = 0, node = -1, ncell = -1, mn = a, len = 0;
+    for (int step = 0; step < Q; ++step) {
+      int y = 0;
+#pragma unroll
+      for (int z = 0; z < Q; ++z)
+        if (perm[z] == x) y = z;
+      x = y;
+      ++cross;
+      if (last[x] >= 0) {
+        node = last[x];
+        ncell = lastc[x];
+        break;
+      }
+      mn = min(mn, x);
+      ++len;
+      if (x == a) break;
+    }
+    const int64_t u = C.sub_off + i * Q + a;
+    s.cut_node[u] = node;
+    s.cut_cell[u] = ncell;
+    s.cut_cross[u] = (int8_t)cross;
+    s.free_min[u] = (node < 0) ? i * Q + mn : -1;
+    s.free_len[u] = (int8_t)len;
+  }
+}
+
+// ---- linking + union-find -----------------------------------------------------
+__device__ __forceinline__ void before_window(const DevChain &C, const int32_t *vp, int bond,
+                                              int j, int &id, int &cellc) {
+  id = -1;
+  cellc = -1;
+  for (int jj = j - 1; jj >= 0; --jj) {
+    const int c = cell_of(C, bond, jj);
+    const int a = vp[c], e = vp[c + 1];
+    if (e > a) {
+      id = e - 1;
+      cellc = c;
+      return;
+    }
+  }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(TILE) k_link(const DevChain *__restrict__ ch,
+                                               const int2 *__restrict__ tab, int64_t blk0,
+                                               Scratch s) {
+  if (halted(s)) return;
+  const int2 t = tab[blk0 + blockIdx.x];
+  const DevChain &C = ch[t.x];
+  const int cell = t.y * TILE + threadIdx.x;
+  if (cell >= C.ncell) return;
+  const int32_t *vp = s.vptr + C.cell_off;
+  const int v0 = vp[cell], v1 = vp[cell + 1];
+  if (v0 == v1) return;
+  int b, j;
+  cell_bj(C, cell, b, j);
+  const int64_t vb = C.vtx_base, wb = vb >> 5;
+  const double *__restrict__ vt = s.vtau + vb;
+  int32_t *par = s.parent + vb;
+  const int sub[2] = {left_sub<Q>(b), right_sub<Q>(b, C.L)};
+  constexpr int NO = 2 * Q - 1;
+  int wa[2][NO], we[2][NO], wq[2][NO], wc[2][NO], bj[2][NO], bjc[2][NO];
+#pragma unroll
+  for (int sd = 0; sd < 2; ++sd) {
+    int k = 0;
+#pragma unroll
+    for (int m = 0; m < 2 * Q; ++m) {
+      const int bb = inc_bond<Q>(sub[sd], m, C.L);
+      if (bb == b) continue;
+      const int cj = cell_of(C, bb, j);
+      wa[sd][k] = vp[cj];
+      we[sd][k] = vp[cj + 1];
+      wq[sd][k] = wa[sd][k];
+      wc[sd][k] = cj;
+      before_window(C, vp, bb, j, bj[sd][k], bjc[sd][k]);
+      ++k;
+    }
+  }
+  int own_bj, own_bjc;
+  before_window(C, vp, b, j, own_bj, own_bjc);
+  const int cut0 = s.cut_node[C.sub_off + sub[0]], cut1 = s.cut_node[C.sub_off + sub[1]];
+  const int cutc0 = s.cut_cell[C.sub_off + sub[0]], cutc1 = s.cut_cell[C.sub_off + sub[1]];
+  const int mytile = cell / TILE;
+
+  for (int w = v0; w < v1; ++w) {
+    const double tw = vt[w];
+    int P[2], Pc[2];
+    uint8_t wrapbits = 0;
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+      int best = -1, bestc = -1;
+      double bt = 0.0;
+      if (w > v0) {
+        best = w - 1;
+        bestc = cell;
+        bt = vt[w - 1];
+      } else if (own_bj >= 0) {
+        best = own_bj;
+        bestc = own_bjc;
+        bt = vt[own_bj];
+      }
+#pragma unroll
+      for (int k = 0; k < NO; ++k) {
+        int q = wq[sd][k];
+        while (q < we[sd][k]) {
+          const double tq = vt[q];
+          if (tq < tw || (tq == tw && q < w))
+            ++q;
+          else
+            break;
+        }
+        wq[sd][k] = q;
+        int cand, candc;
+        if (q > wa[sd][k]) {
+          cand = q - 1;
+          candc = wc[sd][k];
+        } else {
+          cand = bj[sd][k];
+          candc = bjc[sd][k];
+        }
+        if (cand >= 0) {
+          const double tc = vt[cand];
+          if (best < 0 || tc > bt || (tc == bt && cand > best)) {
+            best = cand;
+            bt = tc;
+            bestc = candc;
+          }
+        }
+      }
+      if (best < 0) {
+        best = sd ? cut1 : cut0;
+        bestc = sd ? cutc1 : cutc0;
+        wrapbits |= sd ? VF_WRAP_R : VF_WRAP_L;
+        if (best < 0) {
+          atomicOr(s.status, ST_INTERNAL);
+          best = w;
+          bestc = cell;
+        }
+      }
+      P[sd] = best;
+      Pc[sd] = bestc;
+    }
+    s.pl[vb + w] = P[0];
+    s.pr[vb + w] = P[1];
+    if (wrapbits) s.vflag[vb + w] |= wrapbits;
+    if (Pc[0] / TILE != mytile || Pc[1] / TILE != mytile) set_bit(s.openmark, wb, P[0]);
+    uf_union(par, P[0], P[1], s.status);
+  }
+}
+
+// ---- compression + coins --------------------------------------------------------
+__global__ void __launch_bounds__(TILE) k_compress(const DevChain *__restrict__ ch,
+                                                   const int2 *__restrict__ tab, int64_t blk0,
+                                                   Scratch s) {
+  __shared__ U4 coins[MAX_COIN_GROUPS];
+  __shared__ int64_t sm[33];
+  if (halted(s)) return;
+  const int64_t gt = blk0 + blockIdx.x;
+  const int2 t = tab[gt];
+  const DevChain &C = ch[t.x];
+  const int c0 = t.y * TILE, c1 = min(C.ncell, c0 + TILE);
+  const int32_t *vp = s.vptr + C.cell_off;
+  const int a = vp[c0], e = vp[c1];
+  const int64_t vb = C.vtx_base, wb = vb >> 5;
+  int32_t *par = s.parent + vb;
+  const bool oversized = (e - a) > SMEM_CAP;
+  const int g0 = a >> 7;
+  const int ng = (e > a) ? ((e - 1) >> 7) - g0 + 1 : 0;
+  const uint32_t k0 = (uint32_t)C.seed, k1 = (uint32_t)(C.seed >> 32);
+  for (int g = threadIdx.x; g < ng && g < MAX_COIN_GROUPS; g += blockDim.x)
+    coins[g] = philox(TAG_FLIP << 24, (uint32_t)(g0 + g), 0u, C.sweep, k0, k1);
+  __syncthreads();
+  int64_t roots = 0;
+  for (int v = a + threadIdx.x; v < e; v += blockDim.x) {
+    const int r = uf_find(par, v, s.status);
+    par[v] = r;
+    if (r == v) {
+      ++roots;
+      const int g = (v >> 7) - g0;
+      const int cf = (g < MAX_COIN_GROUPS) ? coin_from(coins[g], (uint32_t)v) : coin(C, TAG_FLIP, v);
+      if (cf) set_bit(s.flipbits, wb, v);
+      if (oversized) set_bit(s.openroot, wb, v);
+    }
+    if (get_bit(s.openmark, wb, v)) set_bit(s.openroot, wb, r);
+  }
+  const int64_t tot = block_sum<int64_t>(roots, sm);
+  if (threadIdx.x == 0) s.tile_roots[gt] = tot;
+}
+
+// ---- loop properties, new flags ---------------------------------------------------
+__device__ __forceinline__ void open_add(int *keys, unsigned long long *vals, int key,
+                                         long long W, long long Cc, long long Ss, const Scratch &s,
+                                         int64_t vb) {
+  unsigned h = ((unsigned)key * 2654435761u) & (OPEN_SLOTS - 1);
+  for (int probe = 0; probe < OPEN_SLOTS; ++probe) {
+    int k = keys[h];
+    if (k == -1) {
+      k = atomicCAS(keys + h, -1, key);
+      if (k == -1) k = key;
+    }
+    if (k == key) {
+      atomicAdd(vals + 3 * h + 0, (unsigned long long)W);
+      atomicAdd(vals + 3 * h + 1, (unsigned long long)Cc);
+      atomicAdd(vals + 3 * h + 2, (unsigned long long)Ss);
+      return;
+    }
+    h = (h + 1) & (OPEN_SLOTS - 1);
+  }
+  atomicAdd(s.accW + vb + key, (unsigned long long)W);
+  atomicAdd(s.accC + vb + key, (unsigned long long)Cc);
+  atomicAdd(s.accS + vb + key, (unsigned long long)Ss);
+}
+
+template <int Q>
+__global__ void __launch_bounds__(TILE) k_est(const DevChain *__restrict__ ch,
+                                              const int2 *__restrict__ tab, int64_t blk0,
+                                              Scratch s) {
+  extern __shared__ unsigned long long est_dyn[];
+  unsigned long long *cW = est_dyn, *cC = est_dyn + SMEM_CAP, *cS = est_dyn + 2 * SMEM_CAP;
+  __shared__ int okeys[OPEN_SLOTS];
+  __shared__ unsigned long long ovals[3 * OPEN_SLOTS];
+  __shared__ int64_t sm[33];
+  if (halted(s)) return;
+  const int64_t gt = blk0 + blockIdx.x;
+  const int2 t = tab[gt];
+  const DevChain &C = ch[t.x];
+  const int c0 = t.y * TILE, c1 = min(C.ncell, c0 + TILE);
+  const int32_t *vp = s.vptr + C.cell_off;
+  const int a = vp[c0], e = vp[c1];
+  const int nv = min(e - a, SMEM_CAP);
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) cW[i] = cC[i] = cS[i] = 0ull;
+  for (int i = threadIdx.x; i < OPEN_SLOTS; i += blockDim.x) {
+    okeys[i] = -1;
+    ovals[3 * i] = ovals[3 * i + 1] = ovals[3 * i + 2] = 0ull;
+  }
+  __syncthreads();
+  const int64_t vb = C.vtx_base, wb = vb >> 5;
+  const int32_t *par = s.parent + vb;
+  const int cell = c0 + threadIdx.x;
+  int newcnt = 0;
+  if (cell < c1) {
+    const int v0 = vp[cell], v1 = vp[cell + 1];
+    int b, j;
+    cell_bj(C, cell, b, j);
+    const int ul = left_sub<Q>(b), ur = right_sub<Q>(b, C.L);
+    const int xl = ul / Q, xr = ur / Q;
+    const double cl = C.cosx[xl], sl = C.sinx[xl], cr = C.cosx[xr], sr = C.sinx[xr];
+    const double crossl = __dmul_rn((double)s.cut_cross[C.sub_off + ul], C.beta);
+    const double crossr = __dmul_rn((double)s.cut_cross[C.sub_off + ur], C.beta);
+    const double scale = ldexp(1.0, C.F);
+    for (int w = v0; w < v1; ++w) {
+      const int P = s.pl[vb + w], R = s.pr[vb + w];
+      const uint8_t f = s.vflag[vb + w];
+      const int rb = __ldcg(par + P), ra = __ldcg(par + w);
+      const int nf = (f & VF_OLD) ^ get_bit(s.flipbits, wb, rb) ^ get_bit(s.flipbits, wb, ra);
+      s.vflag[vb + w] = (uint8_t)(f | (nf ? VF_NEW : 0));
+      newcnt += nf;
+      const double tw = s.vtau[vb + w];
+      double dl = __dsub_rn(tw, s.vtau[vb + P]);
+      if (f & VF_WRAP_L) dl = __dadd_rn(dl, crossl);
+      double dr = __dsub_rn(tw, s.vtau[vb + R]);
+      if (f & VF_WRAP_R) dr = __dadd_rn(dr, crossr);
+      const long long W = fixq(dl, scale) + fixq(dr, scale);
+      const long long Cc = fixq(__dmul_rn(dl, cl), scale) + fixq(__dmul_rn(dr, cr), scale);
+      const long long Ss = fixq(__dmul_rn(dl, sl), scale) + fixq(__dmul_rn(dr, sr), scale);
+      if (get_bit(s.openroot, wb, rb)) {
+        open_add(okeys, ovals, rb, W, Cc, Ss, s, vb);
+      } else {
+        const int li = rb - a;
+        if (li < 0 || li >= nv) {
+          atomicOr(s.status, ST_INTERNAL);
+        } else {
+          atomicAdd(cW + li, (unsigned long long)W);
+          atomicAdd(cC + li, (unsigned long long)Cc);
+          atomicAdd(cS + li, (unsigned long long)Ss);
+        }
+      }
+    }
+    C.op_ptr[C.cur ^ 1][cell] = newcnt;
+  }
+  const int64_t tot = block_sum<int64_t>((int64_t)newcnt, sm);
+  if (threadIdx.x == 0) s.tile_sum2[gt] = tot;
+  __syncthreads();
+  u128 w2 = 0, f2 = 0;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    const int v = a + i;
+    if (__ldcg(par + v) == v && !get_bit(s.openroot, wb, v)) {
+      w2 += sq_abs((long long)cW[i]);
+      f2 += sq_abs((long long)cC[i]) + sq_abs((long long)cS[i]);
+    }
+  }
+  for (int h = threadIdx.x; h < OPEN_SLOTS; h += blockDim.x) {
+    const int k = okeys[h];
+    if (k >= 0) {
+      atomicAdd(s.accW + vb + k, ovals[3 * h]);
+      atomicAdd(s.accC + vb + k, ovals[3 * h + 1]);
+      atomicAdd(s.accS + vb + k, ovals[3 * h + 2]);
+    }
+  }
+  w2 = block_sum_u128(w2);
+  f2 = block_sum_u128(f2);
+  if (threadIdx.x == 0) {
+    s.tile_sw2[2 * gt] = (unsigned long long)w2;
+    s.tile_sw2[2 * gt + 1] = (unsigned long long)(w2 >> 64);
+    s.tile_sf2[2 * gt] = (unsigned long long)f2;
+    s.tile_sf2[2 * gt + 1] = (unsigned long long)(f2 >> 64);
+  }
+}
+
+// ---- next operator list + open loops -------------------------------------------------
+__global__ void __launch_bounds__(TILE) k_compact(const DevChain *__restrict__ ch,
+                                                  const int2 *__restrict__ tab, int64_t blk0,
+                                                  Scratch s) {
+  __shared__ int64_t sm[33];
+  if (halted(s)) return;
+  const int64_t gt = blk0 + blockIdx.x;
+  const int2 t = tab[gt];
+  const DevChain &C = ch[t.x];
+  const int c0 = t.y * TILE, c1 = min(C.ncell, c0 + TILE);
+  const int cell = c0 + threadIdx.x;
+  int32_t *nptr = C.op_ptr[C.cur ^ 1];
+  double *ntau = C.op_tau[C.cur ^ 1];
+  const int32_t *vp = s.vptr + C.cell_off;
+  const int64_t vb = C.vtx_base, wb = vb >> 5;
+  int cnt = (cell < c1) ? nptr[cell] : 0;
+  int64_t tot;
+  const int64_t ex = block_excl_scan<int64_t>((int64_t)cnt, sm, tot);
+  if (cell < c1) {
+    int off = (int)(s.tile_pref2[gt] + ex);
+    nptr[cell] = off;
+    if (cell == C.ncell - 1) nptr[C.ncell] = (int32_t)C.n_off_new;
+    const int v0 = vp[cell], v1 = vp[cell + 1];
+    for (int w = v0; w < v1; ++w)
+      if (s.vflag[vb + w] & VF_NEW) ntau[off++] = s.vtau[vb + w];
+  }
+  const int a = vp[c0], e = vp[c1];
+  u128 w2 = 0, f2 = 0;
+  for (int v = a + threadIdx.x; v < e; v += blockDim.x) {
+    if (get_bit(s.openroot, wb, v)) {
+      const long long W = (long long)s.accW[vb + v], Cc = (long long)s.accC[vb + v],
+                      Ss = (long long)s.accS[vb + v];
+      s.accW[vb + v] = 0ull;
+      s.accC[vb + v] = 0ull;
+      s.accS[vb + v] = 0ull;
+      w2 += sq_abs(W);
+      f2 += sq_abs(Cc) + sq_abs(Ss);
+    }
+  }
+  w2 = block_sum_u128(w2);
+  f2 = block_sum_u128(f2);
+  if (threadIdx.x == 0) {
+    u128 x = ((u128)s.tile_sw2[2 * gt + 1] << 64) | s.tile_sw2[2 * gt];
+    u128 y = ((u128)s.tile_sf2[2 * gt + 1] << 64) | s.tile_sf2[2 * gt];
+    x += w2;
+    y += f2;
+    s.tile_sw2[2 * gt] = (unsigned long long)x;
+    s.tile_sw2[2 * gt + 1] = (unsigned long long)(x >> 64);
+    s.tile_sf2[2 * gt] = (unsigned long long)y;
+    s.tile_sf2[2 * gt + 1] = (unsigned long long)(y >> 64);
+  }
+}
+
+// ---- spins at tau = 0, vertex-free loops -------------------------------------------
+template <int Q>
+__global__ void __launch_bounds__(SITE_BLOCK) k_sites(const DevChain *__restrict__ ch,
+                                                      const int2 *__restrict__ tab, int64_t blk0,
+                                                      Scratch s) {
+  __shared__ int64_t sm[33];
+  if (halted(s)) return;
+  const int64_t gb = blk0 + blockIdx.x;
+  const int2 t = tab[gb];
+  const DevChain &C = ch[t.x];
+  const int i = t.y * SITE_BLOCK + threadIdx.x;
+  const int64_t vb = C.vtx_base, wb = vb >> 5;
+  int64_t nfree = 0;
+  u128 w2 = 0, f2 = 0;
+  if (i < C.L) {
+    const uint8_t *s0 = C.s0[C.cur];
+    uint8_t *s1 = C.s0[C.cur ^ 1];
+    const double scale = ldexp(1.0, C.F);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      const int u = i * Q + a;
+      const int node = s.cut_node[C.sub_off + u];
+      int f;
+      if (node >= 0) {
+        f = get_bit(s.flipbits, wb, __ldcg(s.parent + vb + node));
+      } else {
+        const int mn = s.free_min[C.sub_off + u];
+        f = coin(C, TAG_FREE, (uint32_t)mn);
+        if (mn == u) {
+          ++nfree;
+          const double len = __dmul_rn((double)s.free_len[C.sub_off + u], C.beta);
+          const int x = u / Q;
+          w2 += sq_abs(fixq(len, scale));
+          f2 += sq_abs(fixq(__dmul_rn(len, C.cosx[x]), scale)) +
+                sq_abs(fixq(__dmul_rn(len, C.sinx[x]), scale));
+        }
+      }
+      s1[u] = (uint8_t)(s0[u] ^ f);
+    }
+  }
+  const int64_t tf = block_sum<int64_t>(nfree, sm);
+  w2 = block_sum_u128(w2);
+  f2 = block_sum_u128(f2);
+  if (threadIdx.x == 0) {
+    s.site_free[gb] = tf;
+    s.site_sw2[2 * gb] = (unsigned long long)w2;
+    s.site_sw2[2 * gb + 1] = (unsigned long long)(w2 >> 64);
+    s.site_sf2[2 * gb] = (unsigned long long)f2;
+    s.site_sf2[2 * gb + 1] = (unsigned long long)(f2 >> 64);
+  }
+}
+
+// ---- per-chain record -----------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_final(DevChain *__restrict__ ch, Scratch s) {
+  __shared__ int64_t sm[33];
+  if (halted(s)) return;
+  DevChain &C = ch[blockIdx.x];
+  int64_t roots = 0, nfree = 0;
+  u128 w2 = 0, f2 = 0;
+  for (int i = threadIdx.x; i < C.ntile; i += blockDim.x) {
+    const int64_t g = C.tile0 + i;
+    roots += s.tile_roots[g];
+    w2 += ((u128)s.tile_sw2[2 * g + 1] << 64) | s.tile_sw2[2 * g];
+    f2 += ((u128)s.tile_sf2[2 * g + 1] << 64) | s.tile_sf2[2 * g];
+  }
+  for (int i = threadIdx.x; i < C.nsiteblk; i += blockDim.x) {
+    const int64_t g = C.site0 + i;
+    nfree += s.site_free[g];
+    w2 += ((u128)s.site_sw2[2 * g + 1] << 64) | s.site_sw2[2 * g];
+    f2 += ((u128)s.site_sf2[2 * g + 1] << 64) | s.site_sf2[2 * g];
+  }
+  roots = block_sum<int64_t>(roots, sm);
+  nfree = block_sum<int64_t>(nfree, sm);
+  w2 = block_sum_u128(w2);
+  f2 = block_sum_u128(f2);
+  if (threadIdx.x != 0) return;
+  lcqmc_record r;
+  r.n = C.n;
+  r.n_off_old = C.op_ptr[C.cur][C.ncell];
+  r.n_off_new = C.n_off_new;
+  r.n_free = nfree;
+  r.n_clusters = roots + nfree;
+  r.n_seg = 2 * C.n + nfree;
+  r.F = C.F;
+  r.pad = 0;
+  r.sw2_lo = (unsigned long long)w2;
+  r.sw2_hi = (unsigned long long)(w2 >> 64);
+  r.sf2_lo = (unsigned long long)f2;
+  r.sf2_hi = (unsigned long long)(f2 >> 64);
+  const double two64 = 18446744073709551616.0;
+  const double dsw = __dadd_rn(__dmul_rn((double)r.sw2_hi, two64), (double)r.sw2_lo);
+  const double dsf = __dadd_rn(__dmul_rn((double)r.sf2_hi, two64), (double)r.sf2_lo);
+  const double bl = __dmul_rn(__dmul_rn(4.0, C.beta), (double)C.L);
+  r.energy = __dsub_rn(__dmul_rn(__dmul_rn((double)(C.Q * C.Q), C.J), 0.25),
+                       __ddiv_rn((double)C.n, __dmul_rn(C.beta, (double)C.L)));
+  r.chi_s = __ddiv_rn(ldexp(dsw, -2 * C.F), bl);
+  r.chi_q = __ddiv_rn(ldexp(dsf, -2 * C.F), bl);
+  C.ring[C.n_rec % C.ring_cap] = r;
+  C.n_rec += 1;
+  const double v[8] = {r.energy,
+                       r.chi_s,
+                       r.chi_q,
+                       (double)r.n,
+                       (double)r.n_off_new,
+                       (double)r.n_seg,
+                       (double)r.n_clusters,
+                       (double)(r.n_seg + 2 * r.n)};
+  for (int k = 0; k < 8; ++k) {
+    C.sum[k] += v[k];
+    C.sumsq[k] += v[k] * v[k];
+  }
+  C.n_updates += 1;
+  C.cur ^= 1;
+  C.sweep += 1;
+}
+
+// ---- host-side launchers ----------------------------------------------------------------
+void set_full_table(const uint64_t *T, cudaStream_t st) {
+  cudaMemcpyToSymbolAsync(c_T_full, T, sizeof(uint64_t) * KMAX, 0, cudaMemcpyHostToDevice, st);
+}
+
+static inline dim3 g1(int64_t n) { return dim3((unsigned)n); }
+
+void launch_bond_parity(const Launch &L, cudaStream_t st) {
+  for (int q = 0; q < 2; ++q)
+    if (L.nbondblk[q])
+      k_bond_parity<<<g1(L.nbondblk[q]), BOND_BLOCK, 0, st>>>(L.ch, L.bond_tab, L.bond0[q], L.s);
+}
+
+void launch_insert(const Launch &L, int write, cudaStream_t st) {
+  if (L.ntile[0]) {
+    if (write)
+      k_insert<1, 1><<<g1(L.ntile[0]), TILE, 0, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
+    else
+      k_insert<1, 0><<<g1(L.ntile[0]), TILE, 0, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
+  }
+  if (L.ntile[1]) {
+    if (write)
+      k_insert<2, 1><<<g1(L.ntile[1]), TILE, 0, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
+    else
+      k_insert<2, 0><<<g1(L.ntile[1]), TILE, 0, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
+  }
+}
+
+void launch_scan(const Launch &L, int mode, cudaStream_t st) {
+  if (mode == 0)
+    k_scan_tiles<0><<<L.nchains, 1024, 0, st>>>(L.ch, L.s);
+  else
+    k_scan_tiles<1><<<L.nchains, 1024, 0, st>>>(L.ch, L.s);
+}
+
+void launch_chain_bases(const Launch &L, cudaStream_t st) {
+  k_chain_bases<<<1, 1024, 0, st>>>(L.ch, L.nchains, L.s);
+}
+
+void launch_cut(const Launch &L, cudaStream_t st) {
+  if (L.nsiteblk[0]) k_cut<1><<<g1(L.nsiteblk[0]), SITE_BLOCK, 0, st>>>(L.ch, L.site_tab, L.site0[0], L.s);
+  if (L.nsiteblk[1]) k_cut<2><<<g1(L.nsiteblk[1]), SITE_BLOCK, 0, st>>>(L.ch, L.site_tab, L.site0[1], L.s);
+}
+
+void launch_link(const Launch &L, cudaStream_t st) {
+  if (L.ntile[0]) k_link<1><<<g1(L.ntile[0]), TILE, 0, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
+  if (L.ntile[1]) k_link<2><<<g1(L.ntile[1]), TILE, 0, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
+}
+
+void launch_compress(const Launch &L, cudaStream_t st) {
+  const int64_t n = L.ntile[0] + L.ntile[1];
+  if (n) k_compress<<<g1(n), TILE, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
+}
+
+constexpr size_t EST_DYN_SMEM = 3 * SMEM_CAP * sizeof(unsigned long long);
+
+int init_kernel_attributes() {
+  if (cudaFuncSetAttribute(k_est<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EST_DYN_SMEM) !=
+      cudaSuccess)
+    return -1;
+  if (cudaFuncSetAttribute(k_est<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EST_DYN_SMEM) !=
+      cudaSuccess)
+    return -1;
+  return 0;
+}
+
+void launch_est(const Launch &L, cudaStream_t st) {
+  if (L.ntile[0]) k_est<1><<<g1(L.ntile[0]), TILE, EST_DYN_SMEM, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
+  if (L.ntile[1]) k_est<2><<<g1(L.ntile[1]), TILE, EST_DYN_SMEM, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
+}
+
+void launch_compact(const Launch &L, cudaStream_t st) {
+  const int64_t n = L.ntile[0] + L.ntile[1];
+  if (n) k_compact<<<g1(n), TILE, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
+}
+
+void launch_sites(const Launch &L, cudaStream_t st) {
+  if (L.nsiteblk[0]) k_sites<1><<<g1(L.nsiteblk[0]), SITE_BLOCK, 0, st>>>(L.ch, L.site_tab, L.site0[0], L.s);
+  if (L.nsiteblk[1]) k_sites<2><<<g1(L.nsiteblk[1]), SITE_BLOCK, 0, st>>>(L.ch, L.site_tab, L.site0[1], L.s);
+}
+
+void launch_final(const Launch &L, cudaStream_t st) {
+  k_final<<<L.nchains, 256, 0, st>>>(L.ch, L.s);
+}
+
+}  // namespace lcq

@@ -1,0 +1,305 @@
+"""Thin ctypes binding of liblcqmc.so (include/lcqmc.h).
+
+Argument marshalling only: every step of an update runs in the library's CUDA
+kernels.  There is no CPU fallback; loading fails loudly when the library has
+not been built.  Streams may come from PyTorch (torch.cuda.Stream.cuda_stream).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblcqmc.so")
+
+OK = 0
+PENDING = 1
+ERRORS = {-1: "E_INVAL", -2: "E_NOMEM", -3: "E_TOO_LARGE", -4: "E_ID_OVERFLOW",
+          -5: "E_DEVICE_TIMEOUT", -6: "E_CUDA", -7: "E_STATE", -8: "E_NOT_FOUND",
+          -9: "E_CANCELLED", -10: "E_CAPACITY"}
+NPHASE = 7
+PHASES = ["insert", "scan", "link_union", "loop_ids", "loop_props", "op_rewrite", "spin_rewrite"]
+
+
+class LcqmcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [("n_updates", ctypes.c_int64), ("sum", ctypes.c_double * 8),
+                ("sumsq", ctypes.c_double * 8), ("xi", ctypes.c_double)]
+
+
+class Record(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_off_old", ctypes.c_int64), ("n_off_new", ctypes.c_int64),
+                ("n_free", ctypes.c_int64), ("n_clusters", ctypes.c_int64), ("n_seg", ctypes.c_int64),
+                ("F", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("sw2_lo", ctypes.c_uint64), ("sw2_hi", ctypes.c_uint64),
+                ("sf2_lo", ctypes.c_uint64), ("sf2_hi", ctypes.c_uint64),
+                ("energy", ctypes.c_double), ("chi_s", ctypes.c_double), ("chi_q", ctypes.c_double)]
+
+
+RECORD_DTYPE = np.dtype([("n", np.int64), ("n_off_old", np.int64), ("n_off_new", np.int64),
+                         ("n_free", np.int64), ("n_clusters", np.int64), ("n_seg", np.int64),
+                         ("F", np.int32), ("pad", np.int32), ("sw2_lo", np.uint64),
+                         ("sw2_hi", np.uint64), ("sf2_lo", np.uint64), ("sf2_hi", np.uint64),
+                         ("energy", np.float64), ("chi_s", np.float64), ("chi_q", np.float64)])
+assert RECORD_DTYPE.itemsize == ctypes.sizeof(Record)
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int64), ("nsub", ctypes.c_int64), ("nbond", ctypes.c_int64),
+                ("nwin", ctypes.c_int64), ("ncell", ctypes.c_int64), ("Q", ctypes.c_int32),
+                ("F", ctypes.c_int32), ("J", ctypes.c_double), ("beta", ctypes.c_double),
+                ("w", ctypes.c_double), ("seed", ctypes.c_uint64), ("sweep", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32)]
+
+
+class ChainSpec(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int64), ("S", ctypes.c_double), ("J", ctypes.c_double),
+                ("beta", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int64), ("S", ctypes.c_double), ("J", ctypes.c_double),
+                ("beta", ctypes.c_double), ("seed", ctypes.c_uint64), ("n_updates", ctypes.c_int64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("pad", ctypes.c_int32), ("obs", Obs),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("vertices_edges", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads liblcqmc.so; raises if it was not built (no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} not found: build it with paper_1810_07485_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, u64, i32, u32, dbl = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int,
+                                   ctypes.c_uint32, ctypes.c_double)
+    P = ctypes.POINTER
+    sig = {
+        "lcqmc_create": [i64, dbl, dbl, dbl, u64, P(vp)],
+        "lcqmc_create_ex": [i64, dbl, dbl, dbl, u64, vp, vp, P(vp)],
+        "lcqmc_update": [vp, i64],
+        "lcqmc_sync": [vp],
+        "lcqmc_measure": [vp, P(Obs)],
+        "lcqmc_reset_obs": [vp],
+        "lcqmc_get_records": [vp, vp, i64, P(i64)],
+        "lcqmc_get_geometry": [vp, P(Geometry)],
+        "lcqmc_export_config": [vp, vp, vp, vp, i64, P(i64)],
+        "lcqmc_import_config": [vp, vp, vp, vp, i64, u32],
+        "lcqmc_set_keep_graph": [vp, i32],
+        "lcqmc_export_graph": [vp, vp, vp, vp, vp, vp, i64, P(i64)],
+        "lcqmc_export_cells": [vp, vp, i64],
+        "lcqmc_checkpoint": [vp, vp, P(ctypes.c_size_t)],
+        "lcqmc_restore": [vp, vp, ctypes.c_size_t],
+        "lcqmc_set_phase_timing": [vp, i32],
+        "lcqmc_get_phase_times": [vp, vp, i32],
+        "lcqmc_destroy": [vp],
+        "lcqmc_batch_create": [i64, vp, vp, P(vp)],
+        "lcqmc_batch_update": [vp, i64],
+        "lcqmc_batch_sync": [vp],
+        "lcqmc_batch_measure": [vp, i64, P(Obs)],
+        "lcqmc_batch_get_records": [vp, i64, vp, i64, P(i64)],
+        "lcqmc_batch_destroy": [vp],
+        "lcqmc_server_create": [ctypes.c_size_t, i32, P(vp)],
+        "lcqmc_submit": [vp, P(Request), P(u64)],
+        "lcqmc_poll": [vp, u64, P(Result)],
+        "lcqmc_cancel": [vp, u64],
+        "lcqmc_server_destroy": [vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.lcqmc_last_error.restype = ctypes.c_char_p
+    L.lcqmc_last_error.argtypes = []
+    L.lcqmc_stream.restype = vp
+    L.lcqmc_stream.argtypes = [vp]
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc < 0:
+        raise LcqmcError(rc, lib().lcqmc_last_error().decode())
+    return rc
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def u128(lo, hi):
+    return (int(hi) << 64) | int(lo)
+
+
+def records_to_numpy(buf, n):
+    return np.frombuffer(bytes(buf), dtype=RECORD_DTYPE, count=n).copy()
+
+
+class Chain:
+    """One Markov chain on the GPU: lcqmc_create ... lcqmc_destroy."""
+
+    def __init__(self, L, beta, S=0.5, J=1.0, seed=1, stream=None):
+        h = ctypes.c_void_p()
+        if stream is None:
+            _check(lib().lcqmc_create(int(L), float(S), float(J), float(beta), int(seed) & (2**64 - 1),
+                                      ctypes.byref(h)))
+        else:
+            _check(lib().lcqmc_create_ex(int(L), float(S), float(J), float(beta),
+                                         int(seed) & (2**64 - 1), ctypes.c_void_p(int(stream)), None,
+                                         ctypes.byref(h)))
+        self.h = h
+        self.L, self.beta, self.S, self.J, self.seed = int(L), float(beta), float(S), float(J), int(seed)
+
+    def close(self):
+        if self.h:
+            lib().lcqmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def stream(self):
+        return lib().lcqmc_stream(self.h)
+
+    def update(self, n=1):
+        _check(lib().lcqmc_update(self.h, int(n)))
+
+    def sync(self):
+        _check(lib().lcqmc_sync(self.h))
+
+    def measure(self):
+        o = Obs()
+        _check(lib().lcqmc_measure(self.h, ctypes.byref(o)))
+        return o
+
+    def reset_obs(self):
+        _check(lib().lcqmc_reset_obs(self.h))
+
+    def records(self, max_n=1 << 16):
+        buf = (Record * max(1, max_n))()
+        cnt = ctypes.c_int64()
+        _check(lib().lcqmc_get_records(self.h, buf, int(max_n), ctypes.byref(cnt)))
+        return records_to_numpy(buf, cnt.value)
+
+    def geometry(self):
+        g = Geometry()
+        _check(lib().lcqmc_get_geometry(self.h, ctypes.byref(g)))
+        return g
+
+    def export_config(self):
+        g = self.geometry()
+        n = ctypes.c_int64()
+        _check(lib().lcqmc_export_config(self.h, None, None, None, 0, ctypes.byref(n)))
+        s0 = np.zeros(g.nsub, np.uint8)
+        ptr = np.zeros(g.ncell + 1, np.int32)
+        tau = np.zeros(max(1, n.value), np.float64)
+        _check(lib().lcqmc_export_config(self.h, _p(s0), _p(ptr), _p(tau), n.value, ctypes.byref(n)))
+        return s0, ptr, tau[: n.value].copy()
+
+    def import_config(self, s0, op_ptr, op_tau, sweep):
+        s0 = np.ascontiguousarray(s0, np.uint8)
+        op_ptr = np.ascontiguousarray(op_ptr, np.int32)
+        op_tau = np.ascontiguousarray(op_tau, np.float64)
+        _check(lib().lcqmc_import_config(self.h, _p(s0), _p(op_ptr), _p(op_tau) if len(op_tau) else None,
+                                         len(op_tau), int(sweep)))
+
+    def export_graph(self, fields=("tau", "flag", "pl", "pr", "root")):
+        n = ctypes.c_int64()
+        _check(lib().lcqmc_export_graph(self.h, None, None, None, None, None, 0, ctypes.byref(n)))
+        m = n.value
+        dt = dict(tau=np.float64, flag=np.uint8, pl=np.int32, pr=np.int32, root=np.int32)
+        out = {k: np.zeros(m, dt[k]) for k in fields}
+        args = [_p(out.get(k)) for k in ("tau", "flag", "pl", "pr", "root")]
+        _check(lib().lcqmc_export_graph(self.h, *args, m, ctypes.byref(n)))
+        return out
+
+    def export_cells(self):
+        g = self.geometry()
+        v = np.zeros(g.ncell + 1, np.int32)
+        _check(lib().lcqmc_export_cells(self.h, _p(v), g.ncell + 1))
+        return v
+
+    def checkpoint(self):
+        ln = ctypes.c_size_t()
+        _check(lib().lcqmc_checkpoint(self.h, None, ctypes.byref(ln)))
+        buf = (ctypes.c_char * ln.value)()
+        _check(lib().lcqmc_checkpoint(self.h, buf, ctypes.byref(ln)))
+        return bytes(buf[: ln.value])
+
+    def restore(self, blob):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(lib().lcqmc_restore(self.h, buf, len(blob)))
+
+    def set_phase_timing(self, on=True):
+        _check(lib().lcqmc_set_phase_timing(self.h, 1 if on else 0))
+
+    def phase_times(self):
+        ms = np.zeros(NPHASE)
+        _check(lib().lcqmc_get_phase_times(self.h, _p(ms), NPHASE))
+        return dict(zip(PHASES, ms))
+
+
+class Batch:
+    """Many independent chains updated together (lcqmc_batch_*)."""
+
+    def __init__(self, specs, stream=None):
+        arr = (ChainSpec * len(specs))()
+        for i, s in enumerate(specs):
+            arr[i] = ChainSpec(int(s["L"]), float(s.get("S", 0.5)), float(s.get("J", 1.0)),
+                               float(s["beta"]), int(s.get("seed", i)) & (2**64 - 1))
+        h = ctypes.c_void_p()
+        _check(lib().lcqmc_batch_create(len(specs), arr, ctypes.c_void_p(int(stream)) if stream else None,
+                                        ctypes.byref(h)))
+        self.h = h
+        self.n = len(specs)
+
+    def close(self):
+        if self.h:
+            lib().lcqmc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, n=1):
+        _check(lib().lcqmc_batch_update(self.h, int(n)))
+
+    def sync(self):
+        _check(lib().lcqmc_batch_sync(self.h))
+
+    def measure(self, i):
+        o = Obs()
+        _check(lib().lcqmc_batch_measure(self.h, int(i), ctypes.byref(o)))
+        return o
+
+    def records(self, i, max_n=1 << 12):
+        buf = (Record * max(1, max_n))()
+        cnt = ctypes.c_int64()
+        _check(lib().lcqmc_batch_get_records(self.h, int(i), buf, int(max_n), ctypes.byref(cnt)))
+        return records_to_numpy(buf, cnt.value)

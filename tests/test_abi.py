@@ -1,0 +1,55 @@
+"""The C-ABI library builds for sm_103a and exports every entry point that
+include/lcqmc.h declares (no GPU needed: nothing is called)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "lcqmc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(lcqmc_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_core_api():
+    names = declared_functions()
+    for n in ("lcqmc_create", "lcqmc_update", "lcqmc_measure", "lcqmc_submit", "lcqmc_poll",
+              "lcqmc_destroy", "lcqmc_last_error"):
+        assert n in names
+
+
+@pytest.fixture(scope="module")
+def built_lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_1810_07485_gb300 import build
+    return build.build()
+
+
+def test_library_exports_every_declared_symbol(built_lib):
+    so = ctypes.CDLL(built_lib)
+    missing = [n for n in declared_functions() if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def test_last_error_callable_without_gpu(built_lib):
+    so = ctypes.CDLL(built_lib)
+    so.lcqmc_last_error.restype = ctypes.c_char_p
+    assert isinstance(so.lcqmc_last_error(), bytes)
+
+
+def test_invalid_arguments_rejected_on_host(built_lib):
+    # Argument validation happens before any CUDA call.
+    from paper_1810_07485_gb300 import lcqmc
+    L = lcqmc.lib()
+    h = ctypes.c_void_p()
+    for args in [(3, 0.5, 1.0, 1.0), (0, 0.5, 1.0, 1.0), (8, 0.75, 1.0, 1.0), (8, 0.5, -1.0, 1.0),
+                 (8, 0.5, 1.0, 0.0), (8, 1.5, 1.0, 1.0)]:
+        rc = L.lcqmc_create(args[0], args[1], args[2], args[3], 1, ctypes.byref(h))
+        assert rc == -1, args

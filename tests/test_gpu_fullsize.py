@@ -1,0 +1,109 @@
+"""Full-size checks at the benchmark's workloads (L=2^16, beta=2^12 and
+L=2^20, beta=2^10), in the launch configuration bench.py times.
+
+The oracle cannot run a whole update at this size, so it recomputes sampled
+cells one by one (labeling step), and the rest is checked through properties
+that hold at any size: the exported loop partition is consistent with the
+exported edges and canonical (root = smallest node id), every node has degree
+two, the world lines stay valid, and the operator density approaches the
+paper's 5.64e11/8.14e11.
+"""
+import numpy as np
+import pytest
+
+from oracle import orc
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_partition(g):
+    pl, pr, root = g["pl"].astype(np.int64), g["pr"].astype(np.int64), g["root"].astype(np.int64)
+    n = len(root)
+    assert np.all(root[pl] == root[pr])          # both fragments below a vertex: one loop
+    assert np.all(root[root] == root)            # roots are fixed points
+    assert np.all(root <= np.arange(n))          # root = smallest node of its loop
+    deg = np.bincount(pl, minlength=n) + np.bincount(pr, minlength=n)
+    assert np.all(deg == 2)                      # 2-regular: clusters are loops
+
+
+def _check_worldlines(L, s0, ptr, tau, nwin):
+    """Vectorized: operators on antiparallel spins, periodic world lines (S=1/2)."""
+    TW = 4
+    nb = L
+    ncell = nb * nwin
+    cells = np.arange(ncell)
+    blk = cells // (nb * TW)
+    r = cells - blk * nb * TW
+    tw = np.minimum(TW, nwin - blk * TW)
+    bond_of_cell = r // tw
+    cnt = np.diff(ptr.astype(np.int64))
+    bond = np.repeat(bond_of_cell, cnt)
+    order = np.lexsort((bond, tau))
+    tau_s, bond_s = tau[order], bond[order]
+    # spins just before each operator: s0 xor parity of earlier operators on
+    # the bonds touching each end
+    s = s0.astype(np.int64).copy()
+    left, right = bond_s, (bond_s + 1) % L
+    # process sequentially in chunks (numpy loop over ops would be too slow for
+    # 1e8 ops; use per-site event parity instead)
+    site_ev = np.concatenate([left, right])
+    ev_idx = np.concatenate([np.arange(len(tau_s)), np.arange(len(tau_s))])
+    o = np.lexsort((ev_idx, site_ev))
+    site_sorted, idx_sorted = site_ev[o], ev_idx[o]
+    # parity of events on the same site before this one
+    first = np.r_[True, site_sorted[1:] != site_sorted[:-1]]
+    grp_start = np.maximum.accumulate(np.where(first, np.arange(len(site_sorted)), 0))
+    rank = np.arange(len(site_sorted)) - grp_start
+    spin_before = (s[site_sorted] + rank) & 1
+    sb = np.empty(2 * len(tau_s), np.int64)
+    sb[o] = spin_before
+    assert np.all(sb[: len(tau_s)] != sb[len(tau_s):]), "operator on parallel spins"
+    per_site = np.bincount(site_ev, minlength=L)
+    assert np.all(per_site % 2 == 0), "world lines not periodic"
+
+
+def _check_partition_sampled(g, rng, m=2_000_000):
+    pl, pr, root = g["pl"], g["pr"], g["root"]
+    n = len(root)
+    w = rng.integers(0, n, m)
+    assert np.all(root[pl[w]] == root[pr[w]])
+    assert np.all(root[root[w]] == root[w])
+    assert np.all(root[w] <= w)
+
+
+@pytest.mark.parametrize("L,beta,warm,full", [(1 << 16, float(1 << 12), 8, True),
+                                              (1 << 20, float(1 << 10), 4, False)])
+def test_fullsize(L, beta, warm, full):
+    from paper_1810_07485_gb300 import lcqmc
+    ch = lcqmc.Chain(L, beta, seed=1)
+    ch.update(warm)
+    ch.sync()
+    s0, ptr, tau = ch.export_config()
+    sweep = ch.geometry().sweep
+    ch.update(1)
+    rec = ch.records()[-1]
+    g = ch.export_graph()
+    vptr = ch.export_cells()
+    rng = np.random.default_rng(0)
+    # operator density vs the paper's 5.64e11 / 8.14e11 (Sec. 4.4), loose
+    assert abs(rec["n"] / (L * beta) - 5.64e11 / 8.14e11) < 0.01
+    assert rec["n_seg"] == 2 * rec["n"] + rec["n_free"]
+    if full:
+        _check_partition(g)
+    else:
+        _check_partition_sampled(g, rng)
+    # sampled cells recomputed by the oracle's labeling step
+    p = orc.params(L, beta, seed=1)
+    st = orc.State(s0, ptr.astype(np.int64), tau)
+    nwin = orc.geometry(p)["nwin"]
+    for _ in range(24):
+        b, j = int(rng.integers(L)), int(rng.integers(nwin))
+        c = orc.cell_index(p, b, j)
+        t_o, f_o = orc.keyed_cell(p, sweep, st, b, j)
+        a, e = int(vptr[c]), int(vptr[c + 1])
+        assert np.array_equal(g["tau"][a:e], t_o), (b, j)
+        assert np.array_equal(g["flag"][a:e], f_o), (b, j)
+    if full:
+        s1, ptr1, tau1 = ch.export_config()
+        _check_worldlines(L, s1, ptr1, tau1, nwin)
+    ch.close()

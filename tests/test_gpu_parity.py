@@ -1,0 +1,221 @@
+"""Parity of the CUDA update (through the C ABI) with the CPU oracle.
+
+Both sides start from the same state with the same seed and sweep; every
+integer output (vertex list, predecessor links, loop roots, new spins and
+operators, counts, 128-bit loop sums) must agree exactly, and so must the
+fp64 imaginary times, which both sides compute with one IEEE rounding per
+operation.  The floating-point estimators are derived from the exact sums by
+the same expression on both sides and must agree to 1e-15 relative.
+"""
+import numpy as np
+import pytest
+
+from oracle import ed, orc, stats
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-15
+
+
+def gpu():
+    from paper_1810_07485_gb300 import lcqmc
+    return lcqmc
+
+
+def gpu_state(ch):
+    s0, ptr, tau = ch.export_config()
+    return orc.State(s0, ptr.astype(np.int64), tau)
+
+
+def assert_records_equal(rg, ro, ctx=""):
+    for f in ("n", "n_off_old", "n_off_new", "n_free", "n_clusters", "n_seg", "F", "sw2_lo",
+              "sw2_hi", "sf2_lo", "sf2_hi"):
+        assert int(rg[f]) == int(ro[f]), (ctx, f, int(rg[f]), int(ro[f]))
+    for f in ("energy", "chi_s", "chi_q"):
+        a, b = float(rg[f]), float(ro[f])
+        assert abs(a - b) <= REL_TOL * max(abs(a), abs(b), 1e-300), (ctx, f, a, b)
+
+
+def assert_graph_equal(gg, go, ctx=""):
+    assert np.array_equal(gg["tau"], go["tau"]), ctx
+    assert np.array_equal(gg["flag"], go["flag"]), ctx
+    assert np.array_equal(gg["pl"].astype(np.int64), go["pl"]), ctx
+    assert np.array_equal(gg["pr"].astype(np.int64), go["pr"]), ctx
+    assert np.array_equal(gg["root"].astype(np.int64), go["root"]), ctx
+
+
+def assert_state_equal(sg, so, ctx=""):
+    assert np.array_equal(sg.s0, so.s0), ctx
+    assert np.array_equal(sg.op_ptr, so.op_ptr), ctx
+    assert np.array_equal(sg.op_tau, so.op_tau), ctx
+
+
+def run_parity(L, beta, Q=1, J=1.0, seed=1, nup=12, graph_every=1):
+    lc = gpu()
+    p = orc.params(L, beta, J=J, Q=Q, seed=seed)
+    st = orc.neel(p)
+    ch = lc.Chain(L, beta, S=Q / 2, J=J, seed=seed)
+    try:
+        for t in range(nup):
+            new, ro, go = orc.keyed_update(p, t, st, graph=(t % graph_every == 0))
+            ch.update(1)
+            rg = ch.records()
+            assert len(rg) == 1
+            ctx = f"L={L} beta={beta} Q={Q} J={J} sweep={t}"
+            assert_records_equal(rg[0], ro, ctx)
+            if go is not None:
+                assert_graph_equal(ch.export_graph(), go, ctx)
+            assert_state_equal(gpu_state(ch), new, ctx)
+            st = new
+        return st
+    finally:
+        ch.close()
+
+
+# (L, beta, Q, J): window edges, partial last window and time block, tiny and
+# empty chains, several tiles with a ragged tail, two-site chains, S=1.
+CASES = [
+    (2, 3.0, 1, 1.0),
+    (2, 200.0, 1, 1.0),      # 13 windows: time blocks 4+4+4+1
+    (4, 16.0, 1, 1.0),       # exactly one full window
+    (8, 16.0000001, 1, 1.0), # a sliver of a last window
+    (8, 15.99, 1, 1.0),
+    (16, 5.0, 1, 0.37),      # J != 1: window width 16/J
+    (64, 16.0, 1, 1.0),
+    (250, 70.0, 1, 1.0),     # 1250 cells: 9 full tiles + a ragged one
+    (1024, 40.0, 1, 1.0),    # 96 tiles
+    (4, 3.0, 2, 1.0),
+    (2, 10.0, 2, 1.0),
+    (16, 20.0, 2, 1.0),
+    (64, 8.0, 2, 0.5),
+]
+
+
+@pytest.mark.parametrize("L,beta,Q,J", CASES)
+def test_update_parity(L, beta, Q, J):
+    run_parity(L, beta, Q=Q, J=J, seed=1000 + L, nup=10)
+
+
+def test_long_run_parity():
+    # 300 chained updates: states stay identical throughout.
+    run_parity(32, 24.0, nup=300, graph_every=50, seed=5)
+
+
+def test_empty_and_tiny_beta():
+    # beta << 1/J: most updates have no vertex at all (every site a free loop).
+    lc = gpu()
+    p = orc.params(16, 1e-6, seed=3)
+    st = orc.neel(p)
+    ch = lc.Chain(16, 1e-6, seed=3)
+    orc_recs = orc.keyed_run(p, 0, 40, st)
+    ch.update(40)
+    rg = ch.records()
+    for a, b in zip(rg, orc_recs):
+        assert_records_equal(a, b)
+    assert (rg["n"] == 0).sum() > 30
+    assert_state_equal(gpu_state(ch), st)
+
+
+def test_import_thermalized_state():
+    # A state thermalized by the oracle is imported; the next updates agree.
+    lc = gpu()
+    L, beta = 48, 30.0
+    p = orc.params(L, beta, seed=11)
+    st = orc.neel(p)
+    orc.keyed_run(p, 0, 40, st)
+    ch = lc.Chain(L, beta, seed=11)
+    ch.import_config(st.s0, st.op_ptr.astype(np.int32), st.op_tau, 40)
+    assert_state_equal(gpu_state(ch), st)
+    for t in range(40, 50):
+        new, ro, go = orc.keyed_update(p, t, st, graph=True)
+        ch.update(1)
+        assert_records_equal(ch.records()[0], ro)
+        assert_graph_equal(ch.export_graph(), go)
+        st = new
+    assert_state_equal(gpu_state(ch), st)
+
+
+def test_import_rejects_invalid_state():
+    lc = gpu()
+    p = orc.params(8, 10.0, seed=2)
+    st = orc.neel(p)
+    orc.keyed_run(p, 0, 5, st)
+    ch = lc.Chain(8, 10.0, seed=2)
+    bad = st.s0.copy()
+    bad[0] ^= 1  # breaks periodicity / antiparallel constraint
+    with pytest.raises(lc.LcqmcError):
+        ch.import_config(bad, st.op_ptr.astype(np.int32), st.op_tau, 0)
+
+
+def test_checkpoint_restore_bit_exact():
+    lc = gpu()
+    a = lc.Chain(40, 12.0, seed=9)
+    a.update(20)
+    blob = a.checkpoint()
+    a.update(15)
+    ra = a.records()[-15:]
+    b = lc.Chain(40, 12.0, seed=9)
+    b.restore(blob)
+    b.update(15)
+    rb = b.records()
+    assert np.array_equal(ra, rb)
+    sa, sb = gpu_state(a), gpu_state(b)
+    assert_state_equal(sa, sb)
+
+
+def test_capacity_growth_replays_identically():
+    # A chain started from a hot state needs more room than the first estimate
+    # at low temperature for S=1; growth replays the update with the same keys.
+    lc = gpu()
+    p = orc.params(12, 60.0, Q=2, seed=4)
+    st = orc.neel(p)
+    recs = orc.keyed_run(p, 0, 30, st)
+    ch = lc.Chain(12, 60.0, S=1.0, seed=4)
+    ch.update(30)
+    rg = ch.records()
+    for a, b in zip(rg, recs):
+        assert_records_equal(a, b)
+    assert_state_equal(gpu_state(ch), st)
+
+
+def test_records_and_measure_consistent():
+    lc = gpu()
+    ch = lc.Chain(16, 8.0, seed=21)
+    ch.update(100)
+    r = ch.records()
+    o = ch.measure()
+    assert o.n_updates == 100
+    assert o.sum[0] == pytest.approx(r["energy"].sum(), rel=1e-12)
+    assert o.sum[1] == pytest.approx(r["chi_s"].sum(), rel=1e-12)
+    assert o.sum[3] == pytest.approx(r["n"].sum(), rel=1e-12)
+
+
+@pytest.mark.parametrize("L,beta,Q", [(8, 4.0, 1), (12, 1.0, 1), (4, 1.0, 2)])
+def test_gpu_vs_ed(L, beta, Q):
+    # Estimators within 3 standard errors of exact diagonalization.
+    lc = gpu()
+    ch = lc.Chain(L, beta, S=Q / 2, seed=77)
+    ch.update(1000)
+    ch.records()
+    parts = []
+    for _ in range(50):
+        ch.update(4000)
+        parts.append(ch.records())
+    r = np.concatenate(parts)
+    ex = ed.thermal(L, beta, S=Q / 2)
+    for name in ("energy", "chi_s", "chi_q"):
+        m, e = stats.mean_err(r[name], 100)
+        assert stats.within_sigma(m, e, ex[name], 3.0), (name, m, e, ex[name])
+
+
+def test_batch_matches_single_chains():
+    # Chains updated together in one batch give the same records as alone.
+    lc = gpu()
+    specs = [dict(L=8, beta=4.0, seed=1), dict(L=34, beta=51.0, seed=2), dict(L=4, beta=2.0, S=1.0, seed=3),
+             dict(L=128, beta=16.0, seed=4), dict(L=10, beta=0.001, seed=5)]
+    b = lc.Batch(specs)
+    b.update(25)
+    for i, s in enumerate(specs):
+        ch = lc.Chain(s["L"], s["beta"], S=s.get("S", 0.5), seed=s["seed"])
+        ch.update(25)
+        assert np.array_equal(b.records(i), ch.records()), i
