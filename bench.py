@@ -30,6 +30,7 @@ WORKLOADS = {
     "L65536_beta4096": (1 << 16, float(1 << 12), 6),
     "L1048576_beta1024": (1 << 20, float(1 << 10), 4),
     "L64_beta16": (64, 16.0, 1000),
+    "L16384_beta4096": (1 << 14, float(1 << 12), 6),
 }
 DEFAULT_WORKLOAD = "L65536_beta4096"
 # Oracle sample of the same workload: same beta, fewer sites.
@@ -52,9 +53,11 @@ def phase_bytes(rec, ncell, L):
     n = float(rec["n"])
     no, nn = float(rec["n_off_old"]), float(rec["n_off_new"])
     return {
-        # read old operator times, write vertex time/flag/parent, cell counts
-        "insert": 8 * no + 13 * n + 12 * ncell,
-        "scan": 16 * (ncell / 128.0),
+        # read old operator times (neighbour bonds come from cache), cell counts
+        "insert_count": 8 * no + 8 * ncell,
+        "offsets": 16 * (ncell / 128.0) + 3 * n / 8,
+        # read old operator times again, write vertex time/flag/parent, offsets
+        "insert_write": 8 * no + 13 * n + 8 * ncell,
         # vertex times once, predecessor links out, flag RMW, two parent reads per edge
         "link_union": 26 * n + 4 * ncell,
         # parent read + root write + three bitmaps

@@ -171,10 +171,11 @@ int lcqmc_checkpoint(lcqmc_handle h, void *buf, size_t *len);
 int lcqmc_restore(lcqmc_handle h, const void *buf, size_t len);
 
 /* Per-phase device time (ms) accumulated over updates while enabled, in the
- * order of the cost table of Sec. 4.3: 0 random numbers and insertion,
- * 1 scans, 2 linking and union-find, 3 loop ids (compression, coins),
- * 4 loop properties and flags, 5 operator rewrite, 6 spin rewrite and record. */
-#define LCQMC_NPHASE 7
+ * spirit of the cost table of Sec. 4.3: 0 random numbers and labeling count,
+ * 1 vertex offsets, 2 labeling write, 3 linking and union-find, 4 loop ids
+ * (compression, coins), 5 loop properties and new flags, 6 operator rewrite,
+ * 7 spin rewrite and record. */
+#define LCQMC_NPHASE 8
 int lcqmc_set_phase_timing(lcqmc_handle h, int enable);
 int lcqmc_get_phase_times(lcqmc_handle h, double *ms, int nphase);
 
@@ -228,6 +229,12 @@ int lcqmc_submit(lcqmc_server_t s, const lcqmc_request *req, uint64_t *ticket);
 int lcqmc_poll(lcqmc_server_t s, uint64_t ticket, lcqmc_result *out);
 int lcqmc_cancel(lcqmc_server_t s, uint64_t ticket);
 int lcqmc_server_destroy(lcqmc_server_t s);
+
+/* Host-side self-test of the integer forms of the update's two rounding steps
+ * (which = 0: the candidate time fma(t_end - t0, u, t0) over random window
+ * geometries; which = 1: rint(x 2^F)) against the C library, on n random
+ * inputs from seed.  *mismatches receives the count.  Needs no GPU. */
+int lcqmc_selftest(int which, int64_t n, uint64_t seed, int64_t *mismatches);
 
 /* Message of the calling thread's last failure ("" if none). */
 const char *lcqmc_last_error(void);

@@ -238,6 +238,12 @@ int orc_keyed_cell(const orc_params *p, uint32_t sweep, const uint8_t *s0, const
 
 typedef unsigned __int128 u128;
 
+/* floor((v c + 2^31) / 2^32): v c / 2^32 rounded to nearest, ties up (exact). */
+static int64_t mul_q32(int64_t v, int64_t c) {
+  __int128 p = (__int128)v * (__int128)c + ((__int128)1 << 31);
+  return (int64_t)(p >> 32);
+}
+
 int orc_keyed_update(const orc_params *p, uint32_t sweep, const uint8_t *s0,
                      const int64_t *op_ptr, const double *op_tau, uint8_t *s0_out,
                      int64_t *op_ptr_out, double *op_tau_out, int64_t op_cap,
@@ -483,17 +489,22 @@ int orc_keyed_update(const orc_params *p, uint32_t sweep, const uint8_t *s0,
       for (int64_t c = 0; c < NC; ++c) op_ptr_out[c + 1] += op_ptr_out[c];
       if (n_new > op_cap) rc = -1;
 
-      /* 5. Measurement: per loop, fixed-point sums over fragments. */
+      /* 5. Measurement: per loop, fixed-point sums over fragments.  Times are
+         measured in ticks of 2^-F: q(x) = rint(x 2^F); a fragment from time a up
+         to time b across c cuts at tau = beta has length q(b) - q(a) + c q(beta),
+         and contributes rint(len cos(kx) 2^32) / 2^32 (ties up) to the Fourier
+         sums, with cos(kx) itself rounded to 32 fractional bits. */
       int F = orc_fixed_exponent(p);
+      const int64_t qbeta = llrint(ldexp(beta, F));
       int64_t *Wq = (int64_t *)calloc((size_t)nloop + 1, sizeof(int64_t));
       int64_t *Cq = (int64_t *)calloc((size_t)nloop + 1, sizeof(int64_t));
       int64_t *Sq = (int64_t *)calloc((size_t)nloop + 1, sizeof(int64_t));
-      double *cx = (double *)malloc(sizeof(double) * (size_t)L);
-      double *sx = (double *)malloc(sizeof(double) * (size_t)L);
+      int64_t *cx = (int64_t *)malloc(sizeof(int64_t) * (size_t)L);
+      int64_t *sx = (int64_t *)malloc(sizeof(int64_t) * (size_t)L);
       for (int64_t x = 0; x < L; ++x) {
         double ang = (2.0 * M_PI * (double)x) / (double)L;
-        cx[x] = cos(ang);
-        sx[x] = sin(ang);
+        cx[x] = llrint(ldexp(cos(ang), 32));
+        sx[x] = llrint(ldexp(sin(ang), 32));
       }
       for (int64_t v = 0; v < n; ++v) {
         int64_t ul, ur;
@@ -507,22 +518,22 @@ int orc_keyed_update(const orc_params *p, uint32_t sweep, const uint8_t *s0,
             q = partner[2 * q + 1] / 2;
             if (++guard > NS + 2) { rc = -7; break; }
           }
-          double len = vtx[top_v[q]].tau - vtx[v].tau;
-          if (cross > 0) len = len + (double)cross * beta;
+          int64_t len = llrint(ldexp(vtx[top_v[q]].tau, F)) - llrint(ldexp(vtx[v].tau, F)) +
+                        cross * qbeta;
           int64_t x = u / Q;
           int64_t l = loop[poff[u] + (side ? pos_r[v] : pos_l[v]) + 1];
-          Wq[l] += llrint(ldexp(len, F));
-          Cq[l] += llrint(ldexp(len * cx[x], F));
-          Sq[l] += llrint(ldexp(len * sx[x], F));
+          Wq[l] += len;
+          Cq[l] += mul_q32(len, cx[x]);
+          Sq[l] += mul_q32(len, sx[x]);
         }
       }
       for (int64_t l = 0; l < nloop; ++l) {
         if (!is_free[l]) continue;
-        double len = (double)npieces[l] * beta;
+        int64_t len = npieces[l] * qbeta;
         int64_t x = canon[l] / Q;
-        Wq[l] += llrint(ldexp(len, F));
-        Cq[l] += llrint(ldexp(len * cx[x], F));
-        Sq[l] += llrint(ldexp(len * sx[x], F));
+        Wq[l] += len;
+        Cq[l] += mul_q32(len, cx[x]);
+        Sq[l] += mul_q32(len, sx[x]);
       }
       u128 sw2 = 0, sf2 = 0;
       for (int64_t l = 0; l < nloop; ++l) {

@@ -64,6 +64,8 @@ typedef struct {
   int64_t n_seg;        /* world-line fragments (pieces between vertices) */
   int32_t F;            /* fixed-point exponent of the per-loop sums */
   int32_t pad;
+  /* Loop sums in ticks of 2^-F (fragment length = q(top) - q(bottom) + crossings
+     x q(beta), q(x) = rint(x 2^F)); Fourier terms with cos, sin in 2^-32 units. */
   uint64_t sw2_lo, sw2_hi;  /* sum over loops of Wq^2 (128-bit) */
   uint64_t sf2_lo, sf2_hi;  /* sum over loops of Cq^2 + Sq^2 (128-bit) */
   double energy;        /* E/L = (Q^2 J/4) - n/(beta L) */

@@ -1,4 +1,5 @@
 // extern "C" entry points of include/lcqmc.h: single chains and batches.
+#include <cmath>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -64,6 +65,60 @@ int make_chain(int64_t L, double S, double J, double beta, uint64_t seed, void *
 extern "C" {
 
 const char *lcqmc_last_error(void) { return lcq::last_error(); }
+
+// Host-side check of the integer forms of the method's rounding steps (the
+// same functions the kernels run) against the C library's fma / llrint.
+int lcqmc_selftest(int which, int64_t n, uint64_t seed, int64_t *mismatches) {
+  if (!mismatches || n < 0) return LCQMC_E_INVAL;
+  uint64_t x = seed * 0x9E3779B97F4A7C15ull + 1;
+  auto next = [&x]() {  // splitmix64
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  auto unif = [&]() { return (double)(next() >> 11) * 0x1p-53; };
+  int64_t bad = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (which == 0) {
+      // window geometry as the update builds it, J and beta spread over decades
+      const double J = std::exp((unif() - 0.5) * 12.0);
+      const double w = 16.0 / J;
+      const int64_t nwin = 1 + (int64_t)(next() % 100000);
+      const double beta = ((double)(nwin - 1) + unif()) * w;
+      const int64_t j = (int64_t)(next() % (uint64_t)nwin);
+      const double t0 = (double)j * w;
+      const double te = (j == nwin - 1) ? beta : (double)(j + 1) * w;
+      const double d = te - t0;
+      if (!(d > 0.0)) continue;
+      uint64_t u53 = next() >> 11;
+      const int mode = (int)(next() % 4);
+      if (mode == 1) u53 &= 0xFFFF;                   // small u
+      if (mode == 2) u53 |= (1ull << 53) - (1ull << 20);  // u close to 1
+      double db, tb;
+      std::memcpy(&db, &d, 8);
+      std::memcpy(&tb, &t0, 8);
+      uint64_t dbits, tbits;
+      std::memcpy(&dbits, &d, 8);
+      std::memcpy(&tbits, &t0, 8);
+      const double ref = std::fma(d, std::ldexp((double)u53, -53), t0);
+      uint64_t rbits;
+      std::memcpy(&rbits, &ref, 8);
+      if (lcq::tau_fma_bits(dbits, tbits, u53) != rbits) ++bad;
+    } else if (which == 1) {
+      const int F = (int)(next() % 63);
+      const double v = std::ldexp(unif() + 0.5, (int)(next() % 60) - 40);
+      if (!(std::ldexp(v, F) < 0x1p62)) continue;
+      uint64_t vb;
+      std::memcpy(&vb, &v, 8);
+      if (lcq::q_time(vb, F) != std::llrint(std::ldexp(v, F))) ++bad;
+    } else {
+      return LCQMC_E_INVAL;
+    }
+  }
+  *mismatches = bad;
+  return LCQMC_OK;
+}
 
 int lcqmc_create(int64_t L, double S, double J, double beta, uint64_t seed, lcqmc_handle *out) {
   return make_chain(L, S, J, beta, seed, nullptr, nullptr, out);

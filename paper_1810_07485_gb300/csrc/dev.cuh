@@ -41,8 +41,10 @@ struct DevChain {
   double beta, J, w;
   uint64_t seed;
   // tables
-  const uint64_t *T_last;
-  const double *cosx, *sinx;
+  const uint64_t *T_last;      // Poisson thresholds of the last window
+  const uint64_t *win;         // per window: bits of t0, t_end, t_end - t0
+  const long long *cosq, *sinq;  // rint(2^32 cos(2 pi x / L)), rint(2^32 sin(...))
+  long long qbeta;             // rint(beta 2^F)
   // persistent state, double-buffered (index cur is current)
   uint8_t *s0[2];
   int32_t *op_ptr[2];
@@ -84,7 +86,21 @@ struct Scratch {
   int64_t vcap;
   int *status;
   int64_t *need;  // [0] vertex capacity needed by the last update
+  long long *dbg; // first failed consistency check: code, then 7 details
 };
+
+// Records the first failed consistency check (code > 0) and sets ST_INTERNAL.
+__device__ __forceinline__ void fail_check(const Scratch &s, int code, long long a, long long b,
+                                           long long c, long long d, long long e) {
+  if (atomicCAS((unsigned long long *)s.dbg, 0ull, (unsigned long long)code) == 0ull) {
+    s.dbg[1] = a;
+    s.dbg[2] = b;
+    s.dbg[3] = c;
+    s.dbg[4] = d;
+    s.dbg[5] = e;
+  }
+  atomicOr(s.status, ST_INTERNAL);
+}
 
 // ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) -----------------
 struct U4 {
@@ -166,17 +182,112 @@ __device__ __forceinline__ void set_bit(uint32_t *bits, int64_t word0, int32_t i
   atomicOr(bits + word0 + (i >> 5), 1u << (i & 31));
 }
 
-// ---- exact fixed-point helpers ---------------------------------------------
-// len * 2^F rounded to nearest (ties to even), as llrint(ldexp(len, F)).
-__device__ __forceinline__ long long fixq(double len, double scale) {
-  return __double2ll_rn(__dmul_rn(len, scale));
-}
-
 typedef unsigned __int128 u128;
 
 __device__ __forceinline__ u128 sq_abs(long long v) {
   unsigned long long a = (unsigned long long)(v < 0 ? -v : v);
   return (u128)a * (u128)a;
+}
+
+// ---- exact integer forms of the few fp64 operations of the method ------------
+// GB300 executes fp64 instructions on a handful of lanes per SM, so the hot
+// loops keep imaginary times as the bit patterns of non-negative doubles
+// (ordered like the doubles themselves when read as int64) and evaluate the
+// method's two rounding steps with integer arithmetic, exactly as IEEE 754
+// defines them (round to nearest, ties to even).
+
+constexpr uint64_t M52 = (1ull << 52) - 1;
+
+__host__ __device__ __forceinline__ int clz128(u128 x) {
+  const uint64_t hi = (uint64_t)(x >> 64), lo = (uint64_t)x;
+#ifdef __CUDA_ARCH__
+  return hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+#else
+  return hi ? __builtin_clzll(hi) : (lo ? 64 + __builtin_clzll(lo) : 128);
+#endif
+}
+
+// Bits of the positive double nearest to S * 2^e (S > 0, S < 2^127; normal
+// range), ties to even.
+__host__ __device__ __forceinline__ uint64_t round_to_double_bits(u128 S, int e) {
+  const int nb = 128 - clz128(S);
+  uint64_t q;
+  if (nb <= 53) {
+    q = (uint64_t)S << (53 - nb);
+    e -= 53 - nb;
+  } else {
+    const int sh = nb - 53;
+    q = (uint64_t)(S >> sh);
+    const u128 rem = S - ((u128)q << sh);
+    const u128 half = (u128)1 << (sh - 1);
+    if (rem > half || (rem == half && (q & 1))) ++q;
+    e += sh;
+    if (q >> 53) {
+      q >>= 1;
+      ++e;
+    }
+  }
+  return ((uint64_t)(e + 1075) << 52) | (q & M52);
+}
+
+// Bits of fma(d, u53 * 2^-53, t0) for d > 0 and t0 >= 0 normal doubles given as
+// bit patterns and u53 < 2^53: the exact product plus t0, rounded once.
+__host__ __device__ __forceinline__ uint64_t tau_fma_bits(uint64_t d_bits, uint64_t t0_bits,
+                                                         uint64_t u53) {
+  if (u53 == 0) return t0_bits;
+  const int ed = (int)((d_bits >> 52) & 0x7ff);
+  const uint64_t md = (d_bits & M52) | (1ull << 52);
+  u128 X = (u128)md * (u128)u53;  // product, scale 2^eX, < 2^106
+  int eX = ed - 1075 - 53;
+  if (t0_bits == 0) return round_to_double_bits(X, eX);
+  const int et = (int)((t0_bits >> 52) & 0x7ff);
+  u128 Y = (u128)((t0_bits & M52) | (1ull << 52));
+  int eY = et - 1075;
+  // align: the operand with the larger exponent is shifted left as far as the
+  // sum stays below 2^127; the other one is shifted right with a sticky bit.
+  u128 hi = X, lo = Y;
+  int ehi = eX, elo = eY;
+  if (eY > eX) {
+    hi = Y;
+    lo = X;
+    ehi = eY;
+    elo = eX;
+  }
+  const int diff = ehi - elo;
+  const int room = 126 - (128 - clz128(hi));
+  const int s = diff < room ? diff : room;
+  hi <<= s;
+  const int r = diff - s;
+  if (r > 0) {
+    if (r >= 128) {
+      lo = lo ? 1 : 0;
+    } else {
+      const u128 out = lo & (((u128)1 << r) - 1);
+      lo = (lo >> r) | (out ? 1 : 0);
+    }
+  }
+  return round_to_double_bits(hi + lo, ehi - s);
+}
+
+// llrint(ldexp(x, F)) for a non-negative double x given as bits (x 2^F < 2^62).
+__host__ __device__ __forceinline__ long long q_time(uint64_t x_bits, int F) {
+  if (x_bits == 0) return 0;
+  const int ex = (int)((x_bits >> 52) & 0x7ff);
+  const uint64_t m = (x_bits & M52) | (ex ? (1ull << 52) : 0);
+  const int sh = (ex ? ex : 1) - 1075 + F;  // x 2^F = m 2^sh
+  if (sh >= 0) return (long long)(m << sh);
+  const int r = -sh;
+  if (r > 63) return 0;  // m < 2^53 <= 2^(r-1): below one half
+  uint64_t q = m >> r;
+  const uint64_t rem = m & ((1ull << r) - 1), half = 1ull << (r - 1);
+  if (rem > half || (rem == half && (q & 1))) ++q;
+  return (long long)q;
+}
+
+// round(v * c / 2^32) with ties upward: floor((v c + 2^31) / 2^32), 128-bit exact.
+__host__ __device__ __forceinline__ long long mul_q32(long long v, long long c) {
+  const __int128 p = (__int128)v * (__int128)c + ((__int128)1 << 31);
+  return (long long)(p >> 32);
 }
 
 }  // namespace lcq

@@ -107,7 +107,7 @@ size_t Engine::estimate_footprint(const std::vector<ChainSpec> &specs, int ring_
   for (const auto &c : specs) {
     Geo g = geo_of(c);
     bytes += 2 * (g.nsub + 2 * 4 * (g.ncell + 1) + 8 * op_estimate(c));
-    bytes += 8 * KMAX + 16 * c.L + sizeof(lcqmc_record) * ring_cap;
+    bytes += 8 * KMAX + 16 * c.L + 24 * g.nwin + sizeof(lcqmc_record) * ring_cap;
     bytes += 4 * (g.ncell + 1) + 64 * g.ntile + 48 * g.nsiteblk + (g.nblk + 1) * g.nbond +
              14 * g.nsub + sizeof(DevChain) + 8 * (g.ntile + g.nsiteblk + g.nbondblk);
     vc += (vertex_estimate(c) + 127) / 128 * 128;
@@ -207,8 +207,9 @@ Engine::~Engine() {
       dfree(b.op_tau[k]);
     }
     dfree(b.T_last);
-    dfree(b.cosx);
-    dfree(b.sinx);
+    dfree(b.cosq);
+    dfree(b.sinq);
+    dfree(b.win);
     dfree(b.ring);
   }
   dfree(dch_);
@@ -234,6 +235,7 @@ Engine::~Engine() {
   dfree(s_.free_len);
   dfree(s_.status);
   dfree(s_.need);
+  dfree(s_.dbg);
   if (own_stream_ && st_) cudaStreamDestroy(st_);
 }
 
@@ -337,20 +339,35 @@ int Engine::init(const std::vector<ChainSpec> &specs, void *stream, const lcqmc_
     poisson_table(dl > 0.0 ? d.J * dl * 0.5 : 0.0, T.data());
     DALLOC(b.T_last, uint64_t, KMAX);
     CK(cudaMemcpyAsync(b.T_last, T.data(), 8 * KMAX, cudaMemcpyHostToDevice, st_));
-    std::vector<double> cs(d.L), sn(d.L);
+    // 2^32 cos(k x), 2^32 sin(k x), k = 2 pi / L, rounded to integers.
+    std::vector<long long> cs(d.L), sn(d.L);
     for (int x = 0; x < d.L; ++x) {
       const double ang = (2.0 * M_PI * (double)x) / (double)d.L;
-      cs[x] = std::cos(ang);
-      sn[x] = std::sin(ang);
+      cs[x] = std::llrint(std::ldexp(std::cos(ang), 32));
+      sn[x] = std::llrint(std::ldexp(std::sin(ang), 32));
     }
-    DALLOC(b.cosx, double, d.L);
-    DALLOC(b.sinx, double, d.L);
-    CK(cudaMemcpyAsync(b.cosx, cs.data(), 8 * (size_t)d.L, cudaMemcpyHostToDevice, st_));
-    CK(cudaMemcpyAsync(b.sinx, sn.data(), 8 * (size_t)d.L, cudaMemcpyHostToDevice, st_));
+    DALLOC(b.cosq, long long, d.L);
+    DALLOC(b.sinq, long long, d.L);
+    CK(cudaMemcpyAsync(b.cosq, cs.data(), 8 * (size_t)d.L, cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync(b.sinq, sn.data(), 8 * (size_t)d.L, cudaMemcpyHostToDevice, st_));
+    // Window j covers [t0, t_end): t0 = j w, t_end = (j+1) w or beta for the last.
+    std::vector<uint64_t> win(3 * (size_t)d.nwin);
+    for (int j = 0; j < d.nwin; ++j) {
+      const double t0 = (double)j * d.w;
+      const double te = (j == d.nwin - 1) ? d.beta : (double)(j + 1) * d.w;
+      const double dd = te - t0;
+      std::memcpy(&win[3 * (size_t)j], &t0, 8);
+      std::memcpy(&win[3 * (size_t)j + 1], &te, 8);
+      std::memcpy(&win[3 * (size_t)j + 2], &dd, 8);
+    }
+    DALLOC(b.win, uint64_t, 3 * (size_t)d.nwin);
+    CK(cudaMemcpyAsync(b.win, win.data(), 8 * win.size(), cudaMemcpyHostToDevice, st_));
     DALLOC(b.ring, lcqmc_record, ring_cap);
     d.T_last = b.T_last;
-    d.cosx = b.cosx;
-    d.sinx = b.sinx;
+    d.cosq = b.cosq;
+    d.sinq = b.sinq;
+    d.win = b.win;
+    d.qbeta = std::llrint(std::ldexp(d.beta, d.F));
     d.ring = b.ring;
     op_bytes_ += 2 * (8 * (size_t)d.op_cap);
     CK(cudaStreamSynchronize(st_));  // host vectors above go out of scope
@@ -387,6 +404,8 @@ int Engine::init(const std::vector<ChainSpec> &specs, void *stream, const lcqmc_
   DALLOC(s_.free_len, int8_t, nsub_tot_);
   DALLOC(s_.status, int, 1);
   DALLOC(s_.need, int64_t, 4);
+  DALLOC(s_.dbg, long long, 8);
+  CK(cudaMemsetAsync(s_.dbg, 0, 8 * sizeof(long long), st_));
   CK(cudaMemsetAsync(s_.status, 0, sizeof(int), st_));
   fixed_bytes_ = 4 * (size_t)ncell_tot_ + 64 * (size_t)nt + 48 * (size_t)ns + bpar_tot_ +
                  14 * (size_t)nsub_tot_ + sizeof(DevChain) * nc;
@@ -412,30 +431,31 @@ int Engine::enqueue_one(bool timed, int slot) {
   auto mark = [&](int k) {
     if (timed) cudaEventRecord(ev_[slot * (LCQMC_NPHASE + 1) + k], st_);
   };
-  mark(0);
+  mark(0);  // [0] random numbers + labeling count
   launch_bond_parity(L_, st_);
   launch_insert(L_, 0, st_);
-  mark(1);
+  mark(1);  // [1] vertex offsets
   launch_scan(L_, 0, st_);
   launch_chain_bases(L_, st_);
   CK(cudaMemsetAsync(s_.openmark, 0, 4 * nw, st_));
   CK(cudaMemsetAsync(s_.openroot, 0, 4 * nw, st_));
   CK(cudaMemsetAsync(s_.flipbits, 0, 4 * nw, st_));
+  mark(2);  // [2] labeling write
   launch_insert(L_, 1, st_);
+  mark(3);  // [3] linking + union-find
   launch_cut(L_, st_);
-  mark(2);
   launch_link(L_, st_);
-  mark(3);
+  mark(4);  // [4] loop ids
   launch_compress(L_, st_);
-  mark(4);
+  mark(5);  // [5] loop properties, new flags
   launch_est(L_, st_);
-  mark(5);
+  mark(6);  // [6] operator rewrite
   launch_scan(L_, 1, st_);
   launch_compact(L_, st_);
-  mark(6);
+  mark(7);  // [7] spin rewrite + record
   launch_sites(L_, st_);
   launch_final(L_, st_);
-  mark(7);
+  mark(8);
   CK(cudaGetLastError());
   return LCQMC_OK;
 }
@@ -556,7 +576,14 @@ int Engine::sync() {
         set_error("configuration violates the world-line constraint at tau=0");
         return LCQMC_E_STATE;
       }
-      set_error("internal consistency check failed on the device");
+      long long dbg[8] = {0};
+      cudaMemcpy(dbg, s_.dbg, sizeof(dbg), cudaMemcpyDeviceToHost);
+      cudaMemset(s_.dbg, 0, sizeof(dbg));
+      char msg[256];
+      std::snprintf(msg, sizeof msg,
+                    "internal consistency check %lld failed on the device (%lld %lld %lld %lld %lld)",
+                    dbg[0], dbg[1], dbg[2], dbg[3], dbg[4], dbg[5]);
+      set_error(msg);
       return LCQMC_E_CUDA;
     }
     if (status & ST_VTX_OVERFLOW) {

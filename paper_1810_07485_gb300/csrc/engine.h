@@ -21,7 +21,8 @@ struct ChainBuf {
   int32_t *op_ptr[2] = {nullptr, nullptr};
   double *op_tau[2] = {nullptr, nullptr};
   uint64_t *T_last = nullptr;
-  double *cosx = nullptr, *sinx = nullptr;
+  long long *cosq = nullptr, *sinq = nullptr;
+  uint64_t *win = nullptr;
   lcqmc_record *ring = nullptr;
 };
 

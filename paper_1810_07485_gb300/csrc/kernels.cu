@@ -114,6 +114,22 @@ __device__ int uf_find(int32_t *par, int x, int *status) {
   return p;
 }
 
+// Read-only walk to the root.  Compression uses it so that the only store to
+// parent[v] in that phase is v's own root: a path-halving store from another
+// thread landing after it would leave a non-root ancestor behind.
+__device__ int uf_root(const int32_t *par, int x, int *status) {
+  int p = __ldcg(par + x);
+  for (int it = 0; p != x; ++it) {
+    x = p;
+    p = __ldcg(par + x);
+    if (it > UF_MAX_ITERS) {
+      atomicOr(status, ST_TIMEOUT);
+      break;
+    }
+  }
+  return x;
+}
+
 __device__ void uf_union(int32_t *par, int a, int b, int *status) {
   a = uf_find(par, a, status);
   b = uf_find(par, b, status);
@@ -155,6 +171,9 @@ __global__ void k_bond_parity(const DevChain *__restrict__ ch, const int2 *__res
 }
 
 // ---- insertion (labeling, rules i-iii) --------------------------------------
+// Imaginary times are handled as the int64 bit patterns of non-negative doubles
+// (same order as the values); a candidate's time is the exact integer form of
+// fma(t_end - t0, u, t0).  No fp64 instruction is issued.
 template <int Q>
 struct NbOps {
   static constexpr int N = 4 * Q - 2;
@@ -164,13 +183,13 @@ struct NbOps {
 
 // Parity of the operators on the neighbour bonds ahead of (tau, b).
 template <int Q>
-__device__ __forceinline__ int nb_parity(const NbOps<Q> &X, const double *__restrict__ tau_arr,
-                                         double tau, int b) {
+__device__ __forceinline__ int nb_parity(const NbOps<Q> &X, const long long *__restrict__ tau_arr,
+                                         long long tau, int b) {
   int p = 0;
 #pragma unroll
   for (int k = 0; k < NbOps<Q>::N; ++k) {
     for (int q = X.o0[k]; q < X.o1[k]; ++q) {
-      double t = tau_arr[q];
+      const long long t = tau_arr[q];
       if (t < tau || (t == tau && X.bond[k] < b))
         p ^= 1;
       else
@@ -178,6 +197,19 @@ __device__ __forceinline__ int nb_parity(const NbOps<Q> &X, const double *__rest
     }
   }
   return p;
+}
+
+// Candidate k of the cell: 53 uniform bits.  Call 0 of the cell's Philox stream
+// gives the count (words x, y) and candidate 0 (z, w); call m >= 1 gives
+// candidates 2m-1 (x, y) and 2m (z, w).
+__device__ __forceinline__ uint64_t cand_bits(int k, const U4 &o0, U4 &o2, uint32_t b, uint32_t j,
+                                              uint32_t sweep, uint32_t k0, uint32_t k1) {
+  if (k == 0) return ((uint64_t)o0.z | ((uint64_t)o0.w << 32)) >> 11;
+  if (k & 1) {
+    o2 = philox((TAG_INSERT << 24) | (uint32_t)((k + 1) >> 1), b, j, sweep, k0, k1);
+    return ((uint64_t)o2.x | ((uint64_t)o2.y << 32)) >> 11;
+  }
+  return ((uint64_t)o2.z | ((uint64_t)o2.w << 32)) >> 11;
 }
 
 template <int Q, int WRITE>
@@ -193,14 +225,14 @@ __global__ void __launch_bounds__(TILE) k_insert(const DevChain *__restrict__ ch
   const bool valid = cell < C.ncell;
   const int cur = C.cur;
   const int32_t *op = C.op_ptr[cur];
-  const double *otau = C.op_tau[cur];
+  const long long *otau = (const long long *)C.op_tau[cur];
   const uint8_t *s0 = C.s0[cur];
   int32_t *vp = s.vptr + C.cell_off;
 
   int cnt = 0;
   int b = 0, j = 0;
   int q0 = 0, q1 = 0, K = 0, par0 = 0;
-  double t0 = 0, t_end = 0, d = 0;
+  uint64_t t0b = 0, teb = 0, db = 0;
   NbOps<Q> X;
   U4 o0 = {0, 0, 0, 0};
   const uint32_t k0 = (uint32_t)C.seed, k1 = (uint32_t)(C.seed >> 32);
@@ -228,13 +260,14 @@ __global__ void __launch_bounds__(TILE) k_insert(const DevChain *__restrict__ ch
     }
     q0 = op[cell];
     q1 = op[cell + 1];
-    t0 = (double)j * C.w;
-    t_end = (j == C.nwin - 1) ? C.beta : (double)(j + 1) * C.w;
-    d = t_end - t0;
+    t0b = C.win[3 * j];
+    teb = C.win[3 * j + 1];
+    db = C.win[3 * j + 2];
     o0 = philox(TAG_INSERT << 24, (uint32_t)b, (uint32_t)j, C.sweep, k0, k1);
     const uint64_t U = (uint64_t)o0.x | ((uint64_t)o0.y << 32);
     const uint64_t *T = (j == C.nwin - 1) ? C.T_last : c_T_full;
     while (K < KMAX - 1 && U >= T[K]) ++K;
+    if ((long long)db <= 0) K = 0;  // empty last window
   }
 
   if (!WRITE) {
@@ -242,19 +275,9 @@ __global__ void __launch_bounds__(TILE) k_insert(const DevChain *__restrict__ ch
       U4 o2 = {0, 0, 0, 0};
       int kept = 0;
       for (int k = 0; k < K; ++k) {
-        uint64_t bits;
-        if (k == 0) {
-          bits = (uint64_t)o0.z | ((uint64_t)o0.w << 32);
-        } else if (k & 1) {
-          o2 = philox((TAG_INSERT << 24) | (uint32_t)((k + 1) >> 1), (uint32_t)b, (uint32_t)j,
-                      C.sweep, k0, k1);
-          bits = (uint64_t)o2.x | ((uint64_t)o2.y << 32);
-        } else {
-          bits = (uint64_t)o2.z | ((uint64_t)o2.w << 32);
-        }
-        const double u = __dmul_rn((double)(bits >> 11), 0x1p-53);
-        const double tau = __fma_rn(d, u, t0);
-        if (!(tau < t_end)) continue;
+        const uint64_t u53 = cand_bits(k, o0, o2, (uint32_t)b, (uint32_t)j, C.sweep, k0, k1);
+        const long long tau = (long long)tau_fma_bits(db, t0b, u53);
+        if (!(tau < (long long)teb)) continue;
         if ((par0 ^ nb_parity<Q>(X, otau, tau, b)) & 1) ++kept;
       }
       cnt = (q1 - q0) + kept;
@@ -276,23 +299,13 @@ __global__ void __launch_bounds__(TILE) k_insert(const DevChain *__restrict__ ch
   if (cnt == 0) return;
 
   uint64_t cu[KMAX];
-  double ct[KMAX];
+  long long ct[KMAX];
   int nk = 0;
   U4 o2 = {0, 0, 0, 0};
   for (int k = 0; k < K; ++k) {
-    uint64_t bits;
-    if (k == 0) {
-      bits = (uint64_t)o0.z | ((uint64_t)o0.w << 32);
-    } else if (k & 1) {
-      o2 = philox((TAG_INSERT << 24) | (uint32_t)((k + 1) >> 1), (uint32_t)b, (uint32_t)j,
-                  C.sweep, k0, k1);
-      bits = (uint64_t)o2.x | ((uint64_t)o2.y << 32);
-    } else {
-      bits = (uint64_t)o2.z | ((uint64_t)o2.w << 32);
-    }
-    const uint64_t u53 = bits >> 11;
-    const double tau = __fma_rn(d, __dmul_rn((double)u53, 0x1p-53), t0);
-    if (!(tau < t_end)) continue;
+    const uint64_t u53 = cand_bits(k, o0, o2, (uint32_t)b, (uint32_t)j, C.sweep, k0, k1);
+    const long long tau = (long long)tau_fma_bits(db, t0b, u53);
+    if (!(tau < (long long)teb)) continue;
     if (!((par0 ^ nb_parity<Q>(X, otau, tau, b)) & 1)) continue;
     // insertion sort by u53 (stable: equal keys keep draw order)
     int p = nk;
@@ -306,9 +319,10 @@ __global__ void __launch_bounds__(TILE) k_insert(const DevChain *__restrict__ ch
     ++nk;
   }
   const int64_t vb = C.vtx_base;
+  long long *vt = (long long *)s.vtau + vb;
   int q = q0, ki = 0, r = off;
   while (q < q1 || ki < nk) {
-    double tau;
+    long long tau;
     uint8_t f;
     if (q < q1 && (ki >= nk || otau[q] <= ct[ki])) {
       tau = otau[q++];
@@ -317,12 +331,12 @@ __global__ void __launch_bounds__(TILE) k_insert(const DevChain *__restrict__ ch
       tau = ct[ki++];
       f = 0;
     }
-    s.vtau[vb + r] = tau;
+    vt[r] = tau;
     s.vflag[vb + r] = f;
     s.parent[vb + r] = r;
     ++r;
   }
-  if (r - off != cnt) atomicOr(s.status, ST_INTERNAL);
+  if (r - off != cnt) fail_check(s, 1, cell, cnt, r - off, nk, q1 - q0);
 }
 
 // ---- per-chain scans of tile totals ------------------------------------------
@@ -382,11 +396,11 @@ __global__ void __launch_bounds__(1024) k_chain_bases(DevChain *__restrict__ ch,
 
 // ---- tau = 0: last leg per subsite, subspin permutation, cut predecessors -----
 template <int Q>
-__device__ void last_leg(const DevChain &C, const int32_t *vp, const double *vtau, int64_t vb,
-                         int bond, int &id, int &cellc, double &tau) {
+__device__ void last_leg(const DevChain &C, const int32_t *vp, const long long *vtau, int64_t vb,
+                         int bond, int &id, int &cellc, long long &tau) {
   id = -1;
   cellc = -1;
-  tau = 0.0;
+  tau = 0;
   for (int j = C.nwin - 1; j >= 0; --j) {
     const int c = cell_of(C, bond, j);
     const int a = vp[c], e = vp[c + 1];
@@ -417,15 +431,15 @@ __global__ void __launch_bounds__(SITE_BLOCK) k_cut(const DevChain *__restrict__
   for (int a = 0; a < Q; ++a) {
     const int u = i * Q + a;
     int best = -1, bestc = -1;
-    double bt = 0.0;
+    long long bt = 0;
     int par = 0;
 #pragma unroll
     for (int m = 0; m < 2 * Q; ++m) {
       const int bb = inc_bond<Q>(u, m, C.L);
       par ^= ptot[bb];
       int id, cc;
-      double tt;
-      last_leg<Q>(C, vp, s.vtau, vb, bb, id, cc, tt);
+      long long tt;
+      last_leg<Q>(C, vp, (const long long *)s.vtau, vb, bb, id, cc, tt);
       if (id >= 0 && (best < 0 || tt > bt || (tt == bt && id > best))) {
         best = id;
         bt = tt;
@@ -519,7 +533,7 @@ __global__ void __launch_bounds__(TILE) k_link(const DevChain *__restrict__ ch,
   int b, j;
   cell_bj(C, cell, b, j);
   const int64_t vb = C.vtx_base, wb = vb >> 5;
-  const double *__restrict__ vt = s.vtau + vb;
+  const long long *__restrict__ vt = (const long long *)s.vtau + vb;
   int32_t *par = s.parent + vb;
   const int sub[2] = {left_sub<Q>(b), right_sub<Q>(b, C.L)};
   constexpr int NO = 2 * Q - 1;
@@ -547,13 +561,13 @@ __global__ void __launch_bounds__(TILE) k_link(const DevChain *__restrict__ ch,
   const int mytile = cell / TILE;
 
   for (int w = v0; w < v1; ++w) {
-    const double tw = vt[w];
+    const long long tw = vt[w];
     int P[2], Pc[2];
     uint8_t wrapbits = 0;
 #pragma unroll
     for (int sd = 0; sd < 2; ++sd) {
       int best = -1, bestc = -1;
-      double bt = 0.0;
+      long long bt = 0;
       if (w > v0) {
         best = w - 1;
         bestc = cell;
@@ -567,7 +581,7 @@ __global__ void __launch_bounds__(TILE) k_link(const DevChain *__restrict__ ch,
       for (int k = 0; k < NO; ++k) {
         int q = wq[sd][k];
         while (q < we[sd][k]) {
-          const double tq = vt[q];
+          const long long tq = vt[q];
           if (tq < tw || (tq == tw && q < w))
             ++q;
           else
@@ -583,7 +597,7 @@ __global__ void __launch_bounds__(TILE) k_link(const DevChain *__restrict__ ch,
           candc = bjc[sd][k];
         }
         if (cand >= 0) {
-          const double tc = vt[cand];
+          const long long tc = vt[cand];
           if (best < 0 || tc > bt || (tc == bt && cand > best)) {
             best = cand;
             bt = tc;
@@ -596,7 +610,7 @@ __global__ void __launch_bounds__(TILE) k_link(const DevChain *__restrict__ ch,
         bestc = sd ? cutc1 : cutc0;
         wrapbits |= sd ? VF_WRAP_R : VF_WRAP_L;
         if (best < 0) {
-          atomicOr(s.status, ST_INTERNAL);
+          fail_check(s, 2, cell, w, sd, sub[sd], 0);
           best = w;
           bestc = cell;
         }
@@ -636,8 +650,8 @@ __global__ void __launch_bounds__(TILE) k_compress(const DevChain *__restrict__ 
   __syncthreads();
   int64_t roots = 0;
   for (int v = a + threadIdx.x; v < e; v += blockDim.x) {
-    const int r = uf_find(par, v, s.status);
-    par[v] = r;
+    const int r = uf_root(par, v, s.status);
+    if (r != v) par[v] = r;
     if (r == v) {
       ++roots;
       const int g = (v >> 7) - g0;
@@ -708,10 +722,12 @@ __global__ void __launch_bounds__(TILE) k_est(const DevChain *__restrict__ ch,
     cell_bj(C, cell, b, j);
     const int ul = left_sub<Q>(b), ur = right_sub<Q>(b, C.L);
     const int xl = ul / Q, xr = ur / Q;
-    const double cl = C.cosx[xl], sl = C.sinx[xl], cr = C.cosx[xr], sr = C.sinx[xr];
-    const double crossl = __dmul_rn((double)s.cut_cross[C.sub_off + ul], C.beta);
-    const double crossr = __dmul_rn((double)s.cut_cross[C.sub_off + ur], C.beta);
-    const double scale = ldexp(1.0, C.F);
+    const long long cl = C.cosq[xl], sl = C.sinq[xl], cr = C.cosq[xr], sr = C.sinq[xr];
+    // a fragment through the tau=0 cut gains (crossings) x beta, in ticks
+    const long long crossl = (long long)s.cut_cross[C.sub_off + ul] * C.qbeta;
+    const long long crossr = (long long)s.cut_cross[C.sub_off + ur] * C.qbeta;
+    const uint64_t *vt = (const uint64_t *)s.vtau + vb;
+    const int F = C.F;
     for (int w = v0; w < v1; ++w) {
       const int P = s.pl[vb + w], R = s.pr[vb + w];
       const uint8_t f = s.vflag[vb + w];
@@ -719,20 +735,21 @@ __global__ void __launch_bounds__(TILE) k_est(const DevChain *__restrict__ ch,
       const int nf = (f & VF_OLD) ^ get_bit(s.flipbits, wb, rb) ^ get_bit(s.flipbits, wb, ra);
       s.vflag[vb + w] = (uint8_t)(f | (nf ? VF_NEW : 0));
       newcnt += nf;
-      const double tw = s.vtau[vb + w];
-      double dl = __dsub_rn(tw, s.vtau[vb + P]);
-      if (f & VF_WRAP_L) dl = __dadd_rn(dl, crossl);
-      double dr = __dsub_rn(tw, s.vtau[vb + R]);
-      if (f & VF_WRAP_R) dr = __dadd_rn(dr, crossr);
-      const long long W = fixq(dl, scale) + fixq(dr, scale);
-      const long long Cc = fixq(__dmul_rn(dl, cl), scale) + fixq(__dmul_rn(dr, cr), scale);
-      const long long Ss = fixq(__dmul_rn(dl, sl), scale) + fixq(__dmul_rn(dr, sr), scale);
+      // fragment lengths in ticks of 2^-F: q(tau_top) - q(tau_bottom) (+ crossings)
+      const long long qw = q_time(vt[w], F);
+      long long dl = qw - q_time(vt[P], F);
+      if (f & VF_WRAP_L) dl += crossl;
+      long long dr = qw - q_time(vt[R], F);
+      if (f & VF_WRAP_R) dr += crossr;
+      const long long W = dl + dr;
+      const long long Cc = mul_q32(dl, cl) + mul_q32(dr, cr);
+      const long long Ss = mul_q32(dl, sl) + mul_q32(dr, sr);
       if (get_bit(s.openroot, wb, rb)) {
         open_add(okeys, ovals, rb, W, Cc, Ss, s, vb);
       } else {
         const int li = rb - a;
         if (li < 0 || li >= nv) {
-          atomicOr(s.status, ST_INTERNAL);
+          fail_check(s, 3, cell, w, rb, a, ((long long)nv << 32) | (unsigned)P);
         } else {
           atomicAdd(cW + li, (unsigned long long)W);
           atomicAdd(cC + li, (unsigned long long)Cc);
@@ -841,7 +858,6 @@ __global__ void __launch_bounds__(SITE_BLOCK) k_sites(const DevChain *__restrict
   if (i < C.L) {
     const uint8_t *s0 = C.s0[C.cur];
     uint8_t *s1 = C.s0[C.cur ^ 1];
-    const double scale = ldexp(1.0, C.F);
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
       const int u = i * Q + a;
@@ -854,11 +870,10 @@ __global__ void __launch_bounds__(SITE_BLOCK) k_sites(const DevChain *__restrict
         f = coin(C, TAG_FREE, (uint32_t)mn);
         if (mn == u) {
           ++nfree;
-          const double len = __dmul_rn((double)s.free_len[C.sub_off + u], C.beta);
+          const long long len = (long long)s.free_len[C.sub_off + u] * C.qbeta;
           const int x = u / Q;
-          w2 += sq_abs(fixq(len, scale));
-          f2 += sq_abs(fixq(__dmul_rn(len, C.cosx[x]), scale)) +
-                sq_abs(fixq(__dmul_rn(len, C.sinx[x]), scale));
+          w2 += sq_abs(len);
+          f2 += sq_abs(mul_q32(len, C.cosq[x])) + sq_abs(mul_q32(len, C.sinq[x]));
         }
       }
       s1[u] = (uint8_t)(s0[u] ^ f);

@@ -17,8 +17,9 @@ PENDING = 1
 ERRORS = {-1: "E_INVAL", -2: "E_NOMEM", -3: "E_TOO_LARGE", -4: "E_ID_OVERFLOW",
           -5: "E_DEVICE_TIMEOUT", -6: "E_CUDA", -7: "E_STATE", -8: "E_NOT_FOUND",
           -9: "E_CANCELLED", -10: "E_CAPACITY"}
-NPHASE = 7
-PHASES = ["insert", "scan", "link_union", "loop_ids", "loop_props", "op_rewrite", "spin_rewrite"]
+NPHASE = 8
+PHASES = ["insert_count", "offsets", "insert_write", "link_union", "loop_ids", "loop_props", "op_rewrite",
+          "spin_rewrite"]
 
 
 class LcqmcError(RuntimeError):

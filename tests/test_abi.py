@@ -53,3 +53,15 @@ def test_invalid_arguments_rejected_on_host(built_lib):
                  (8, 0.5, 1.0, 0.0), (8, 1.5, 1.0, 1.0)]:
         rc = L.lcqmc_create(args[0], args[1], args[2], args[3], 1, ctypes.byref(h))
         assert rc == -1, args
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_integer_rounding_forms_match_libm(built_lib, which):
+    # The kernels evaluate fma(t_end - t0, u, t0) and rint(x 2^F) with integer
+    # arithmetic; the same code, run on the host, must agree bit for bit with
+    # the C library on a million random inputs.
+    so = ctypes.CDLL(built_lib)
+    bad = ctypes.c_int64(-1)
+    rc = so.lcqmc_selftest(ctypes.c_int(which), ctypes.c_int64(1_000_000), ctypes.c_uint64(12345),
+                           ctypes.byref(bad))
+    assert rc == 0 and bad.value == 0

@@ -71,8 +71,8 @@ def _check_partition_sampled(g, rng, m=2_000_000):
     assert np.all(root[w] <= w)
 
 
-@pytest.mark.parametrize("L,beta,warm,full", [(1 << 16, float(1 << 12), 8, True),
-                                              (1 << 20, float(1 << 10), 4, False)])
+@pytest.mark.parametrize("L,beta,warm,full", [(1 << 16, float(1 << 12), 12, True),
+                                              (1 << 20, float(1 << 10), 30, False)])
 def test_fullsize(L, beta, warm, full):
     from paper_1810_07485_gb300 import lcqmc
     ch = lcqmc.Chain(L, beta, seed=1)

@@ -144,8 +144,9 @@ def test_keyed_invariants(orc, L, beta, Q):
 
 def test_keyed_estimator_sums_exact(orc):
     """The 128-bit sum of squared loop lengths equals a brute-force recomputation
-    from the exported graph (S=1/2: fragment below w has length tau_w - tau_P,
-    plus beta when it wraps through tau=0)."""
+    from the exported graph (S=1/2: in ticks q(t) = rint(t 2^F), the fragment
+    below w has length q(tau_w) - q(tau_P), plus q(beta) when it wraps through
+    tau=0)."""
     L, beta = 8, 6.0
     p = orc.params(L, beta, seed=77)
     st = orc.neel(p)
@@ -161,11 +162,11 @@ def test_keyed_estimator_sums_exact(orc):
             for P in (int(gr["pl"][w]), int(gr["pr"][w])):
                 tw, tp = gr["tau"][w], gr["tau"][P]
                 wrapped = (tp > tw) or (tp == tw and P >= w)
-                ln = tw - tp
+                ln = int(np.rint(np.ldexp(tw, F))) - int(np.rint(np.ldexp(tp, F)))
                 if wrapped:
-                    ln = ln + beta
+                    ln += int(np.rint(np.ldexp(beta, F)))
                 r = int(gr["root"][P])
-                W[r] = W.get(r, 0) + int(np.rint(np.ldexp(ln, F)))
+                W[r] = W.get(r, 0) + ln
         sw2 = sum(v * v for v in W.values())
         sw2 += int((~touched).sum()) * int(np.rint(np.ldexp(beta, F))) ** 2
         assert sw2 == orc.u128(rec["sw2_lo"], rec["sw2_hi"])
