@@ -230,6 +230,25 @@ int lcqmc_poll(lcqmc_server_t s, uint64_t ticket, lcqmc_result *out);
 int lcqmc_cancel(lcqmc_server_t s, uint64_t ticket);
 int lcqmc_server_destroy(lcqmc_server_t s);
 
+/* Loop labelling with no device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not call cudaMalloc (it
+ * synchronizes the device, is refused on a thread that is capturing a CUDA
+ * graph, and may break a memory budget fixed in advance, e.g. inside another
+ * framework's pool).  Input: n graph vertices, pl[n] / pr[n] = node of the
+ * fragment below each vertex on its left / right subsite (device pointers,
+ * node ids in [0, n), as lcqmc_export_graph returns them).  Output: root[n]
+ * (device pointer) = smallest node id of each node's loop.  The union-find
+ * forest lives in a fixed device array of 2^22 int32 parents compiled into
+ * the library (reserved on every GPU that loads it, until exit); n above
+ * 2^22 returns LCQMC_E_TOO_LARGE.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress): make it before any stream
+ * capture.  Work runs on cuda_stream (NULL = legacy default) and the call
+ * waits for it.  All calls share the array and each call resets what it
+ * uses; calls that overlap on the GPU race and must be serialized by the
+ * caller.  LCQMC_E_INVAL if an id is outside [0, n). */
+int lcqmc_loops_noalloc(const int32_t *pl, const int32_t *pr, int64_t n, int32_t *root,
+                        void *cuda_stream);
+
 /* Host-side self-test of the integer forms of the update's two rounding steps
  * (which = 0: the candidate time fma(t_end - t0, u, t0) over random window
  * geometries; which = 1: rint(x 2^F)) against the C library, on n random
