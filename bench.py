@@ -35,7 +35,7 @@ WORKLOADS = {
 DEFAULT_WORKLOAD = "L65536_beta4096"
 # Oracle sample of the same workload: same beta, fewer sites.
 ORACLE_SAMPLE_L = 1024
-KERNELS_PER_UPDATE = 13
+KERNELS_PER_UPDATE = 11
 RECORD_BYTES = 104
 
 
@@ -53,17 +53,17 @@ def phase_bytes(rec, ncell, L):
     n = float(rec["n"])
     no, nn = float(rec["n_off_old"]), float(rec["n_off_new"])
     return {
-        # read old operator times (neighbour bonds come from cache), cell counts
-        "insert_count": 8 * no + 8 * ncell,
-        "offsets": 16 * (ncell / 128.0) + 3 * n / 8,
-        # read old operator times again, write vertex time/flag/parent, offsets
-        "insert_write": 8 * no + 13 * n + 8 * ncell,
+        # read old operator times, write vertex time/flag/parent, cell offsets,
+        # clear three bitmaps
+        "insert": 8 * no + 13 * n + 8 * ncell + 3 * n / 8,
+        "cut": 16.0 * L,
         # vertex times once, predecessor links out, flag RMW, two parent reads per edge
         "link_union": 26 * n + 4 * ncell,
         # parent read + root write + three bitmaps
         "loop_ids": 8.375 * n,
         # links, flags, two roots, three times per vertex, new flag
         "loop_props": 42 * n + 4 * ncell,
+        "op_offsets": 16 * (ncell / 128.0),
         # flags, new operator times read + written, cell offsets
         "op_rewrite": n + 16 * nn + 8 * ncell,
         "spin_rewrite": 2.0 * L + 64.0,

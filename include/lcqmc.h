@@ -171,10 +171,10 @@ int lcqmc_checkpoint(lcqmc_handle h, void *buf, size_t *len);
 int lcqmc_restore(lcqmc_handle h, const void *buf, size_t len);
 
 /* Per-phase device time (ms) accumulated over updates while enabled, in the
- * spirit of the cost table of Sec. 4.3: 0 random numbers and labeling count,
- * 1 vertex offsets, 2 labeling write, 3 linking and union-find, 4 loop ids
- * (compression, coins), 5 loop properties and new flags, 6 operator rewrite,
- * 7 spin rewrite and record. */
+ * spirit of the cost table of Sec. 4.3: 0 random numbers and labeling
+ * (insertion with vertex offsets), 1 tau=0 cut, 2 linking and union-find,
+ * 3 loop ids (compression, coins), 4 loop properties and new flags,
+ * 5 operator offsets, 6 operator rewrite, 7 spin rewrite and record. */
 #define LCQMC_NPHASE 8
 int lcqmc_set_phase_timing(lcqmc_handle h, int enable);
 int lcqmc_get_phase_times(lcqmc_handle h, double *ms, int nphase);
@@ -221,11 +221,19 @@ typedef struct {
   int64_t vertices_edges;           /* total V+E processed for this request */
 } lcqmc_result;
 
+/* Device bytes one served chain holds (persistent state + its share of the
+ * update's scratch), as used for admission.  Host-only; needs no GPU. */
+int lcqmc_footprint(int64_t L, double S, double J, double beta, size_t *bytes);
+
 /* A server keeps up to max_slots chains resident on the device within
  * hbm_budget bytes, admits queued requests as slots and memory free up, and
  * advances all resident chains together in ticks of updates. */
 int lcqmc_server_create(size_t hbm_budget, int max_slots, lcqmc_server_t *out);
+/* Queues a request; LCQMC_E_TOO_LARGE if its footprint alone exceeds the
+ * budget, LCQMC_E_ID_OVERFLOW if it needs more than 2^31 graph vertices. */
 int lcqmc_submit(lcqmc_server_t s, const lcqmc_request *req, uint64_t *ticket);
+/* LCQMC_PENDING while queued or running; LCQMC_OK once out->status holds the
+ * outcome (LCQMC_OK with obs filled, or an error / LCQMC_E_CANCELLED). */
 int lcqmc_poll(lcqmc_server_t s, uint64_t ticket, lcqmc_result *out);
 int lcqmc_cancel(lcqmc_server_t s, uint64_t ticket);
 int lcqmc_server_destroy(lcqmc_server_t s);

@@ -60,6 +60,7 @@ struct DevChain {
   int32_t cur;
   uint32_t sweep;
   int64_t vtx_base;  // first vertex of the chain in the vertex arrays (multiple of 128)
+  int64_t vcap;      // vertices reserved for the chain from vtx_base on
   int64_t n;         // graph vertices of the current update
   int64_t n_off_new; // off-diagonal operators after the current update
   // measurements
@@ -84,6 +85,8 @@ struct Scratch {
   unsigned long long *accW, *accC, *accS;
   uint32_t *openmark, *openroot, *flipbits;
   int64_t vcap;
+  unsigned long long *tile_state;  // per tile: insertion look-back word (flag << 62 | count)
+  unsigned int *tickets;           // per Q group: next tile of the insertion launch
   int *status;
   int64_t *need;  // [0] vertex capacity needed by the last update
   long long *dbg; // first failed consistency check: code, then 7 details

@@ -195,23 +195,28 @@ int Engine::alloc_vertex(int64_t vcap) {
   return LCQMC_OK;
 }
 
+void Engine::destroy_state(ChainState *c) {
+  if (!c) return;
+  ChainBuf &b = c->buf;
+  for (int k = 0; k < 2; ++k) {
+    dfree(b.s0[k]);
+    dfree(b.op_ptr[k]);
+    dfree(b.op_tau[k]);
+  }
+  dfree(b.T_last);
+  dfree(b.cosq);
+  dfree(b.sinq);
+  dfree(b.win);
+  dfree(b.ring);
+  b = ChainBuf{};
+}
+
 Engine::~Engine() {
   if (st_) cudaStreamSynchronize(st_);
   if (gexec_) cudaGraphExecDestroy(gexec_);
   for (auto e : ev_) cudaEventDestroy(e);
   free_vertex();
-  for (auto &b : buf_) {
-    for (int k = 0; k < 2; ++k) {
-      dfree(b.s0[k]);
-      dfree(b.op_ptr[k]);
-      dfree(b.op_tau[k]);
-    }
-    dfree(b.T_last);
-    dfree(b.cosq);
-    dfree(b.sinq);
-    dfree(b.win);
-    dfree(b.ring);
-  }
+  for (auto &c : owned_) destroy_state(c.get());
   dfree(dch_);
   dfree(tile_tab_);
   dfree(site_tab_);
@@ -234,17 +239,14 @@ Engine::~Engine() {
   dfree(s_.cut_cross);
   dfree(s_.free_len);
   dfree(s_.status);
+  dfree(s_.tickets);
+  dfree(s_.tile_state);
   dfree(s_.need);
   dfree(s_.dbg);
   if (own_stream_ && st_) cudaStreamDestroy(st_);
 }
 
-int Engine::init(const std::vector<ChainSpec> &specs, void *stream, const lcqmc_allocator *alloc,
-                 int ring_cap) {
-  if (specs.empty()) {
-    set_error("empty batch");
-    return LCQMC_E_INVAL;
-  }
+int Engine::open(void *stream, const lcqmc_allocator *alloc, int ring_cap) {
   CK(cudaGetDevice(&device_));
   if (init_kernel_attributes() != 0) {
     set_error("cudaFuncSetAttribute failed");
@@ -261,168 +263,262 @@ int Engine::init(const std::vector<ChainSpec> &specs, void *stream, const lcqmc_
     own_stream_ = true;
   }
   ring_cap_ = ring_cap;
-  // Order chains: Q=1 group first (tables), but keep the caller's chain index.
-  spec_ = specs;
-  const int nc = (int)specs.size();
+  std::vector<uint64_t> T(KMAX);
+  poisson_table(CELL_MEAN, T.data());
+  set_full_table(T.data(), st_);
+  DALLOC(s_.status, int, 1);
+  DALLOC(s_.tickets, unsigned int, 2);
+  DALLOC(s_.need, int64_t, 4);
+  DALLOC(s_.dbg, long long, 8);
+  CK(cudaMemsetAsync(s_.status, 0, sizeof(int), st_));
+  CK(cudaMemsetAsync(s_.dbg, 0, 8 * sizeof(long long), st_));
+  CK(cudaStreamSynchronize(st_));
+  return LCQMC_OK;
+}
+
+// Persistent state of one chain: Neel start, no operators, sweep 0.
+int Engine::create_state(const ChainSpec &spec, ChainState *out) {
+  out->spec = spec;
+  out->rec_read = 0;
+  const Geo g = geo_of(spec);
+  DevChain &d = out->dev;
+  d = DevChain{};
+  d.L = (int32_t)spec.L;
+  d.Q = spec.Q;
+  d.nsub = (int32_t)g.nsub;
+  d.nbond = (int32_t)g.nbond;
+  d.nwin = (int32_t)g.nwin;
+  d.nblk = (int32_t)g.nblk;
+  d.ncell = (int32_t)g.ncell;
+  d.ntile = (int32_t)g.ntile;
+  d.nsiteblk = (int32_t)g.nsiteblk;
+  d.F = fixed_exponent(spec);
+  d.ring_cap = ring_cap_;
+  d.beta = spec.beta;
+  d.J = spec.J;
+  d.w = g.w;
+  d.seed = spec.seed;
+  d.op_cap = op_estimate(spec);
+  ChainBuf &b = out->buf;
+  for (int k = 0; k < 2; ++k) {
+    DALLOC(b.s0[k], uint8_t, d.nsub);
+    DALLOC(b.op_ptr[k], int32_t, (int64_t)d.ncell + 1);
+    DALLOC(b.op_tau[k], double, d.op_cap);
+    d.s0[k] = b.s0[k];
+    d.op_ptr[k] = b.op_ptr[k];
+    d.op_tau[k] = b.op_tau[k];
+  }
+  std::vector<uint8_t> s0(d.nsub);
+  for (int u = 0; u < d.nsub; ++u) s0[u] = (uint8_t)((u / d.Q) & 1);
+  CK(cudaMemcpyAsync(b.s0[0], s0.data(), d.nsub, cudaMemcpyHostToDevice, st_));
+  CK(cudaMemsetAsync(b.op_ptr[0], 0, sizeof(int32_t) * ((size_t)d.ncell + 1), st_));
+  std::vector<uint64_t> T(KMAX);
+  const double t0 = (double)(d.nwin - 1) * d.w;
+  const double dl = d.beta - t0;
+  poisson_table(dl > 0.0 ? d.J * dl * 0.5 : 0.0, T.data());
+  DALLOC(b.T_last, uint64_t, KMAX);
+  CK(cudaMemcpyAsync(b.T_last, T.data(), 8 * KMAX, cudaMemcpyHostToDevice, st_));
+  // 2^32 cos(k x), 2^32 sin(k x), k = 2 pi / L, rounded to integers.
+  std::vector<long long> cs(d.L), sn(d.L);
+  for (int x = 0; x < d.L; ++x) {
+    const double ang = (2.0 * M_PI * (double)x) / (double)d.L;
+    cs[x] = std::llrint(std::ldexp(std::cos(ang), 32));
+    sn[x] = std::llrint(std::ldexp(std::sin(ang), 32));
+  }
+  DALLOC(b.cosq, long long, d.L);
+  DALLOC(b.sinq, long long, d.L);
+  CK(cudaMemcpyAsync(b.cosq, cs.data(), 8 * (size_t)d.L, cudaMemcpyHostToDevice, st_));
+  CK(cudaMemcpyAsync(b.sinq, sn.data(), 8 * (size_t)d.L, cudaMemcpyHostToDevice, st_));
+  // Window j covers [t0, t_end): t0 = j w, t_end = (j+1) w or beta for the last.
+  std::vector<uint64_t> win(3 * (size_t)d.nwin);
+  for (int j = 0; j < d.nwin; ++j) {
+    const double a = (double)j * d.w;
+    const double te = (j == d.nwin - 1) ? d.beta : (double)(j + 1) * d.w;
+    const double dd = te - a;
+    std::memcpy(&win[3 * (size_t)j], &a, 8);
+    std::memcpy(&win[3 * (size_t)j + 1], &te, 8);
+    std::memcpy(&win[3 * (size_t)j + 2], &dd, 8);
+  }
+  DALLOC(b.win, uint64_t, 3 * (size_t)d.nwin);
+  CK(cudaMemcpyAsync(b.win, win.data(), 8 * win.size(), cudaMemcpyHostToDevice, st_));
+  DALLOC(b.ring, lcqmc_record, ring_cap_);
+  d.T_last = b.T_last;
+  d.cosq = b.cosq;
+  d.sinq = b.sinq;
+  d.win = b.win;
+  d.ring = b.ring;
+  d.qbeta = std::llrint(std::ldexp(d.beta, d.F));
+  CK(cudaStreamSynchronize(st_));  // host staging vectors go out of scope
+  return LCQMC_OK;
+}
+
+size_t Engine::state_bytes(const ChainSpec &c, int ring_cap) {
+  const Geo g = geo_of(c);
+  return 2 * ((size_t)g.nsub + 4 * ((size_t)g.ncell + 1) + 8 * (size_t)op_estimate(c)) + 8 * KMAX +
+         16 * (size_t)c.L + 24 * (size_t)g.nwin + sizeof(lcqmc_record) * (size_t)ring_cap;
+}
+
+size_t Engine::scratch_bytes(const ChainSpec &c) {
+  const Geo g = geo_of(c);
+  const size_t v = (size_t)((vertex_estimate(c) + 127) / 128 * 128);
+  return v * 45 + 4 * (size_t)(g.ncell + 1) + 96 * (size_t)g.ntile + 48 * (size_t)g.nsiteblk +
+         (size_t)(g.nblk + 1) * g.nbond + 14 * (size_t)g.nsub + sizeof(DevChain);
+}
+
+int Engine::grow_array(void **p, int64_t *cap, int64_t need, size_t elem) {
+  if (need <= *cap && *p) return LCQMC_OK;
+  const int64_t nc = std::max<int64_t>(need, 1);
+  void *q = dalloc(elem * (size_t)nc);
+  if (!q) {
+    set_error("device allocation of scratch failed");
+    return LCQMC_E_NOMEM;
+  }
+  dfree(*p);
+  *p = q;
+  *cap = nc;
+  return LCQMC_OK;
+}
+
+// Makes `chains` the resident set: per-chain offsets into the batch scratch,
+// block tables (Q=1 chains' blocks before Q=2 chains'), scratch sized to the
+// set (grown, never shrunk).  The chains' persistent state is untouched.
+int Engine::set_chains(const std::vector<ChainState *> &chains) {
+  if (!cs_.empty()) {
+    int rc = sync();
+    if (rc) return rc;
+  }
+  cs_ = chains;
+  return layout();
+}
+
+// Offsets of the resident chains in the batch scratch.  Each chain owns a fixed
+// vertex region [vtx_base, vtx_base + vcap) (128-aligned), so the single-pass
+// insertion of one chain never waits for another chain's vertex count.
+int Engine::layout() {
+  const int nc = (int)cs_.size();
   hch.assign(nc, DevChain{});
-  buf_.assign(nc, ChainBuf{});
-  rec_read_.assign(nc, 0);
   std::vector<int2> ttab, stab, btab;
-  int64_t cell_off = 0, bpar_off = 0, sub_off = 0, vest = 4096;
+  int64_t cell_off = 0, bpar_off = 0, sub_off = 0, vest = 0;
   for (int q = 0; q < 2; ++q) {
     L_.tile0[q] = (int64_t)ttab.size();
     L_.site0[q] = (int64_t)stab.size();
     L_.bond0[q] = (int64_t)btab.size();
     for (int c = 0; c < nc; ++c) {
-      if (specs[c].Q != q + 1) continue;
-      const Geo g = geo_of(specs[c]);
+      if (cs_[c]->spec.Q != q + 1) continue;
+      const Geo g = geo_of(cs_[c]->spec);
       DevChain &d = hch[c];
-      d.L = (int32_t)specs[c].L;
-      d.Q = specs[c].Q;
-      d.nsub = (int32_t)g.nsub;
-      d.nbond = (int32_t)g.nbond;
-      d.nwin = (int32_t)g.nwin;
-      d.nblk = (int32_t)g.nblk;
-      d.ncell = (int32_t)g.ncell;
-      d.ntile = (int32_t)g.ntile;
-      d.nsiteblk = (int32_t)g.nsiteblk;
-      d.F = fixed_exponent(specs[c]);
-      d.ring_cap = ring_cap;
-      d.beta = specs[c].beta;
-      d.J = specs[c].J;
-      d.w = g.w;
-      d.seed = specs[c].seed;
+      d = cs_[c]->dev;
       d.cell_off = cell_off;
       d.tile0 = (int64_t)ttab.size();
       d.site0 = (int64_t)stab.size();
       d.bpar_off = bpar_off;
       d.sub_off = sub_off;
-      d.op_cap = op_estimate(specs[c]);
+      if (cs_[c]->vcap <= 0) cs_[c]->vcap = (vertex_estimate(cs_[c]->spec) + 127) / 128 * 128;
+      d.vcap = cs_[c]->vcap;
       cell_off += g.ncell + 1;
       bpar_off += (g.nblk + 1) * g.nbond;
       sub_off += g.nsub;
       for (int64_t t = 0; t < g.ntile; ++t) ttab.push_back(make_int2(c, (int)t));
       for (int64_t t = 0; t < g.nsiteblk; ++t) stab.push_back(make_int2(c, (int)t));
       for (int64_t t = 0; t < g.nbondblk; ++t) btab.push_back(make_int2(c, (int)t));
-      vest += (vertex_estimate(specs[c]) + 127) / 128 * 128;
     }
     L_.ntile[q] = (int64_t)ttab.size() - L_.tile0[q];
     L_.nsiteblk[q] = (int64_t)stab.size() - L_.site0[q];
     L_.nbondblk[q] = (int64_t)btab.size() - L_.bond0[q];
   }
-  ncell_tot_ = cell_off;
-  bpar_tot_ = bpar_off;
-  nsub_tot_ = sub_off;
-  ntile_tot_ = (int64_t)ttab.size();
-  nsiteblk_tot_ = (int64_t)stab.size();
-  nbondblk_tot_ = (int64_t)btab.size();
-
-  // Per-chain persistent buffers and tables; Neel start, no operators.
-  std::vector<uint64_t> T(KMAX);
-  for (int c = 0; c < nc; ++c) {
-    DevChain &d = hch[c];
-    ChainBuf &b = buf_[c];
-    for (int k = 0; k < 2; ++k) {
-      DALLOC(b.s0[k], uint8_t, d.nsub);
-      DALLOC(b.op_ptr[k], int32_t, (int64_t)d.ncell + 1);
-      DALLOC(b.op_tau[k], double, d.op_cap);
-      d.s0[k] = b.s0[k];
-      d.op_ptr[k] = b.op_ptr[k];
-      d.op_tau[k] = b.op_tau[k];
-    }
-    std::vector<uint8_t> s0(d.nsub);
-    for (int u = 0; u < d.nsub; ++u) s0[u] = (uint8_t)((u / d.Q) & 1);
-    CK(cudaMemcpyAsync(b.s0[0], s0.data(), d.nsub, cudaMemcpyHostToDevice, st_));
-    CK(cudaMemsetAsync(b.op_ptr[0], 0, sizeof(int32_t) * ((size_t)d.ncell + 1), st_));
-    const double t0 = (double)(d.nwin - 1) * d.w;
-    const double dl = d.beta - t0;
-    poisson_table(dl > 0.0 ? d.J * dl * 0.5 : 0.0, T.data());
-    DALLOC(b.T_last, uint64_t, KMAX);
-    CK(cudaMemcpyAsync(b.T_last, T.data(), 8 * KMAX, cudaMemcpyHostToDevice, st_));
-    // 2^32 cos(k x), 2^32 sin(k x), k = 2 pi / L, rounded to integers.
-    std::vector<long long> cs(d.L), sn(d.L);
-    for (int x = 0; x < d.L; ++x) {
-      const double ang = (2.0 * M_PI * (double)x) / (double)d.L;
-      cs[x] = std::llrint(std::ldexp(std::cos(ang), 32));
-      sn[x] = std::llrint(std::ldexp(std::sin(ang), 32));
-    }
-    DALLOC(b.cosq, long long, d.L);
-    DALLOC(b.sinq, long long, d.L);
-    CK(cudaMemcpyAsync(b.cosq, cs.data(), 8 * (size_t)d.L, cudaMemcpyHostToDevice, st_));
-    CK(cudaMemcpyAsync(b.sinq, sn.data(), 8 * (size_t)d.L, cudaMemcpyHostToDevice, st_));
-    // Window j covers [t0, t_end): t0 = j w, t_end = (j+1) w or beta for the last.
-    std::vector<uint64_t> win(3 * (size_t)d.nwin);
-    for (int j = 0; j < d.nwin; ++j) {
-      const double t0 = (double)j * d.w;
-      const double te = (j == d.nwin - 1) ? d.beta : (double)(j + 1) * d.w;
-      const double dd = te - t0;
-      std::memcpy(&win[3 * (size_t)j], &t0, 8);
-      std::memcpy(&win[3 * (size_t)j + 1], &te, 8);
-      std::memcpy(&win[3 * (size_t)j + 2], &dd, 8);
-    }
-    DALLOC(b.win, uint64_t, 3 * (size_t)d.nwin);
-    CK(cudaMemcpyAsync(b.win, win.data(), 8 * win.size(), cudaMemcpyHostToDevice, st_));
-    DALLOC(b.ring, lcqmc_record, ring_cap);
-    d.T_last = b.T_last;
-    d.cosq = b.cosq;
-    d.sinq = b.sinq;
-    d.win = b.win;
-    d.qbeta = std::llrint(std::ldexp(d.beta, d.F));
-    d.ring = b.ring;
-    op_bytes_ += 2 * (8 * (size_t)d.op_cap);
-    CK(cudaStreamSynchronize(st_));  // host vectors above go out of scope
+  for (int c = 0; c < nc; ++c) {  // vertex regions in chain order
+    hch[c].vtx_base = vest;
+    vest += (hch[c].vcap + 127) / 128 * 128;
   }
-  poisson_table(CELL_MEAN, T.data());
-  set_full_table(T.data(), st_);
-
-  DALLOC(dch_, DevChain, nc);
-  DALLOC(tile_tab_, int2, std::max<int64_t>(1, ntile_tot_));
-  DALLOC(site_tab_, int2, std::max<int64_t>(1, nsiteblk_tot_));
-  DALLOC(bond_tab_, int2, std::max<int64_t>(1, nbondblk_tot_));
-  CK(cudaMemcpyAsync(dch_, hch.data(), sizeof(DevChain) * nc, cudaMemcpyHostToDevice, st_));
-  CK(cudaMemcpyAsync(tile_tab_, ttab.data(), sizeof(int2) * ttab.size(), cudaMemcpyHostToDevice, st_));
-  CK(cudaMemcpyAsync(site_tab_, stab.data(), sizeof(int2) * stab.size(), cudaMemcpyHostToDevice, st_));
-  CK(cudaMemcpyAsync(bond_tab_, btab.data(), sizeof(int2) * btab.size(), cudaMemcpyHostToDevice, st_));
-
-  const int64_t nt = std::max<int64_t>(1, ntile_tot_), ns = std::max<int64_t>(1, nsiteblk_tot_);
-  DALLOC(s_.vptr, int32_t, ncell_tot_);
-  DALLOC(s_.tile_sum, int64_t, nt);
-  DALLOC(s_.tile_pref, int64_t, nt);
-  DALLOC(s_.tile_sum2, int64_t, nt);
-  DALLOC(s_.tile_pref2, int64_t, nt);
-  DALLOC(s_.tile_roots, int64_t, nt);
-  DALLOC(s_.tile_sw2, unsigned long long, 2 * nt);
-  DALLOC(s_.tile_sf2, unsigned long long, 2 * nt);
-  DALLOC(s_.site_free, int64_t, ns);
-  DALLOC(s_.site_sw2, unsigned long long, 2 * ns);
-  DALLOC(s_.site_sf2, unsigned long long, 2 * ns);
-  DALLOC(s_.bpar, uint8_t, bpar_tot_);
-  DALLOC(s_.cut_node, int32_t, nsub_tot_);
-  DALLOC(s_.cut_cell, int32_t, nsub_tot_);
-  DALLOC(s_.free_min, int32_t, nsub_tot_);
-  DALLOC(s_.cut_cross, int8_t, nsub_tot_);
-  DALLOC(s_.free_len, int8_t, nsub_tot_);
-  DALLOC(s_.status, int, 1);
-  DALLOC(s_.need, int64_t, 4);
-  DALLOC(s_.dbg, long long, 8);
-  CK(cudaMemsetAsync(s_.dbg, 0, 8 * sizeof(long long), st_));
-  CK(cudaMemsetAsync(s_.status, 0, sizeof(int), st_));
-  fixed_bytes_ = 4 * (size_t)ncell_tot_ + 64 * (size_t)nt + 48 * (size_t)ns + bpar_tot_ +
-                 14 * (size_t)nsub_tot_ + sizeof(DevChain) * nc;
-  for (auto &d : hch)
-    fixed_bytes_ += 2 * ((size_t)d.nsub + 4 * ((size_t)d.ncell + 1)) + 8 * KMAX + 16 * (size_t)d.L +
-                    sizeof(lcqmc_record) * ring_cap;
-
+  const int64_t nt = std::max<int64_t>(1, (int64_t)ttab.size());
+  const int64_t ns = std::max<int64_t>(1, (int64_t)stab.size());
+  const int64_t nb = std::max<int64_t>(1, (int64_t)btab.size());
+  int rc = 0;
+#define GROW(ptr, cap, need, T)                                                     \
+  if ((rc = grow_array((void **)&(ptr), &(cap), (need), sizeof(T))) != 0) return rc
+  GROW(dch_, cap_chains_, std::max(nc, 1), DevChain);
+  GROW(tile_tab_, cap_tt_, nt, int2);
+  GROW(site_tab_, cap_st_, ns, int2);
+  GROW(bond_tab_, cap_bt_, nb, int2);
+  GROW(s_.vptr, cap_cells_, std::max<int64_t>(1, cell_off), int32_t);
+  int64_t c1 = cap_tiles_, c2 = cap_tiles_, c3 = cap_tiles_, c4 = cap_tiles_, c5 = cap_tiles_,
+          c6 = cap_tiles_, c7 = cap_tiles_;
+  if (nt > cap_tiles_) {
+    GROW(s_.tile_sum, c1, nt, int64_t);
+    GROW(s_.tile_pref, c2, nt, int64_t);
+    GROW(s_.tile_sum2, c3, nt, int64_t);
+    GROW(s_.tile_pref2, c4, nt, int64_t);
+    GROW(s_.tile_roots, c5, nt, int64_t);
+    GROW(s_.tile_sw2, c6, 2 * nt, unsigned long long);
+    GROW(s_.tile_sf2, c7, 2 * nt, unsigned long long);
+    int64_t c8 = cap_tiles_;
+    GROW(s_.tile_state, c8, nt, unsigned long long);
+    cap_tiles_ = nt;
+  }
+  if (ns > cap_sites_) {
+    int64_t a1 = cap_sites_, a2 = cap_sites_, a3 = cap_sites_;
+    GROW(s_.site_free, a1, ns, int64_t);
+    GROW(s_.site_sw2, a2, 2 * ns, unsigned long long);
+    GROW(s_.site_sf2, a3, 2 * ns, unsigned long long);
+    cap_sites_ = ns;
+  }
+  GROW(s_.bpar, cap_bpar_, std::max<int64_t>(1, bpar_off), uint8_t);
+  if (sub_off > cap_subs_ || !s_.cut_node) {
+    int64_t a1 = cap_subs_, a2 = cap_subs_, a3 = cap_subs_, a4 = cap_subs_, a5 = cap_subs_;
+    const int64_t need = std::max<int64_t>(1, sub_off);
+    GROW(s_.cut_node, a1, need, int32_t);
+    GROW(s_.cut_cell, a2, need, int32_t);
+    GROW(s_.free_min, a3, need, int32_t);
+    GROW(s_.cut_cross, a4, need, int8_t);
+    GROW(s_.free_len, a5, need, int8_t);
+    cap_subs_ = need;
+  }
+#undef GROW
+  if (nc > 0) {
+    CK(cudaMemcpyAsync(dch_, hch.data(), sizeof(DevChain) * nc, cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync(tile_tab_, ttab.data(), sizeof(int2) * ttab.size(), cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync(site_tab_, stab.data(), sizeof(int2) * stab.size(), cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync(bond_tab_, btab.data(), sizeof(int2) * btab.size(), cudaMemcpyHostToDevice, st_));
+  }
+  fixed_bytes_ = 4 * (size_t)cap_cells_ + 96 * (size_t)cap_tiles_ + 48 * (size_t)cap_sites_ +
+                 (size_t)cap_bpar_ + 14 * (size_t)cap_subs_ + sizeof(DevChain) * (size_t)cap_chains_;
   L_.ch = dch_;
   L_.nchains = nc;
   L_.tile_tab = tile_tab_;
   L_.site_tab = site_tab_;
   L_.bond_tab = bond_tab_;
   L_.s = s_;
-  int rc = alloc_vertex(vest);
-  if (rc) return rc;
+  if (gexec_) {
+    cudaGraphExecDestroy(gexec_);
+    gexec_ = nullptr;
+  }
+  if (vest > vcap_) {
+    rc = alloc_vertex(vest);
+    if (rc) return rc;
+  } else {
+    L_.s = s_;
+  }
+  L_.s = s_;
   CK(cudaStreamSynchronize(st_));
   return LCQMC_OK;
+}
+
+int Engine::init(const std::vector<ChainSpec> &specs, void *stream, const lcqmc_allocator *alloc,
+                 int ring_cap) {
+  if (specs.empty()) {
+    set_error("empty batch");
+    return LCQMC_E_INVAL;
+  }
+  int rc = open(stream, alloc, ring_cap);
+  if (rc) return rc;
+  std::vector<ChainState *> v;
+  for (const auto &sp : specs) {
+    owned_.push_back(std::make_unique<ChainState>());
+    rc = create_state(sp, owned_.back().get());
+    if (rc) return rc;
+    v.push_back(owned_.back().get());
+  }
+  return set_chains(v);
 }
 
 // ---- update sequence ---------------------------------------------------------------------
@@ -431,26 +527,25 @@ int Engine::enqueue_one(bool timed, int slot) {
   auto mark = [&](int k) {
     if (timed) cudaEventRecord(ev_[slot * (LCQMC_NPHASE + 1) + k], st_);
   };
-  mark(0);  // [0] random numbers + labeling count
+  mark(0);  // [0] labeling: random numbers, insertion, vertex offsets (one pass)
   launch_bond_parity(L_, st_);
-  launch_insert(L_, 0, st_);
-  mark(1);  // [1] vertex offsets
-  launch_scan(L_, 0, st_);
-  launch_chain_bases(L_, st_);
+  CK(cudaMemsetAsync(s_.tile_state, 0, 8 * (size_t)cap_tiles_, st_));
+  CK(cudaMemsetAsync(s_.tickets, 0, 2 * sizeof(unsigned int), st_));
   CK(cudaMemsetAsync(s_.openmark, 0, 4 * nw, st_));
   CK(cudaMemsetAsync(s_.openroot, 0, 4 * nw, st_));
   CK(cudaMemsetAsync(s_.flipbits, 0, 4 * nw, st_));
-  mark(2);  // [2] labeling write
-  launch_insert(L_, 1, st_);
-  mark(3);  // [3] linking + union-find
+  launch_insert(L_, st_);
+  mark(1);  // [1] tau = 0 cut
   launch_cut(L_, st_);
+  mark(2);  // [2] linking + union-find
   launch_link(L_, st_);
-  mark(4);  // [4] loop ids
+  mark(3);  // [3] loop ids (compression, coins)
   launch_compress(L_, st_);
-  mark(5);  // [5] loop properties, new flags
+  mark(4);  // [4] loop properties, new flags
   launch_est(L_, st_);
+  mark(5);  // [5] operator offsets
+  launch_scan_ops(L_, st_);
   mark(6);  // [6] operator rewrite
-  launch_scan(L_, 1, st_);
   launch_compact(L_, st_);
   mark(7);  // [7] spin rewrite + record
   launch_sites(L_, st_);
@@ -501,20 +596,24 @@ int Engine::update(int64_t n) {
 }
 
 int Engine::pull_chains() {
+  if (hch.empty()) return LCQMC_OK;
   CK(cudaMemcpyAsync(hch.data(), dch_, sizeof(DevChain) * hch.size(), cudaMemcpyDeviceToHost, st_));
   CK(cudaStreamSynchronize(st_));
+  for (size_t c = 0; c < hch.size(); ++c) cs_[c]->dev = hch[c];
   return LCQMC_OK;
 }
 
 int Engine::push_chains() {
+  if (hch.empty()) return LCQMC_OK;
   CK(cudaMemcpyAsync(dch_, hch.data(), sizeof(DevChain) * hch.size(), cudaMemcpyHostToDevice, st_));
   CK(cudaStreamSynchronize(st_));
+  for (size_t c = 0; c < hch.size(); ++c) cs_[c]->dev = hch[c];
   return LCQMC_OK;
 }
 
 int Engine::grow_ops(int64_t c, int64_t need) {
   DevChain &d = hch[c];
-  ChainBuf &b = buf_[c];
+  ChainBuf &b = cs_[c]->buf;
   const int64_t cap = need + need / 4 + 1024;
   const int64_t nold = 0;
   (void)nold;
@@ -587,9 +686,9 @@ int Engine::sync() {
       return LCQMC_E_CUDA;
     }
     if (status & ST_VTX_OVERFLOW) {
-      int64_t need = 0;
-      CK(cudaMemcpy(&need, s_.need, 8, cudaMemcpyDeviceToHost));
-      rc = alloc_vertex(need + need / 8 + 4096);
+      for (size_t c = 0; c < cs_.size(); ++c)
+        if (hch[c].n > cs_[c]->vcap) cs_[c]->vcap = (hch[c].n + hch[c].n / 8 + 4096 + 127) / 128 * 128;
+      rc = layout();
       if (rc) return rc;
     }
     if (status & ST_OP_OVERFLOW) {
@@ -647,13 +746,13 @@ int Engine::records(int64_t c, lcqmc_record *out, int64_t max, int64_t *count) {
   int rc = sync();
   if (rc) return rc;
   const DevChain &d = hch[c];
-  int64_t &rd = rec_read_[c];
+  int64_t &rd = cs_[c]->rec_read;
   if (d.n_rec - rd > d.ring_cap) rd = d.n_rec - d.ring_cap;
   int64_t avail = d.n_rec - rd;
   const int64_t m = std::min<int64_t>(avail, std::max<int64_t>(0, max));
   for (int64_t i = 0; i < m; ++i) {
     const int64_t slot = (rd + i) % d.ring_cap;
-    CK(cudaMemcpyAsync(out + i, buf_[c].ring + slot, sizeof(lcqmc_record), cudaMemcpyDeviceToHost, st_));
+    CK(cudaMemcpyAsync(out + i, cs_[c]->buf.ring + slot, sizeof(lcqmc_record), cudaMemcpyDeviceToHost, st_));
   }
   CK(cudaStreamSynchronize(st_));
   rd += m;
@@ -686,7 +785,7 @@ int Engine::export_config(int64_t c, uint8_t *s0, int32_t *op_ptr, double *op_ta
   int rc = sync();
   if (rc) return rc;
   const DevChain &d = hch[c];
-  const ChainBuf &b = buf_[c];
+  const ChainBuf &b = cs_[c]->buf;
   int32_t n = 0;
   CK(cudaMemcpy(&n, b.op_ptr[d.cur] + d.ncell, 4, cudaMemcpyDeviceToHost));
   if (n_off) *n_off = n;
@@ -775,7 +874,7 @@ int Engine::import_config(int64_t c, const uint8_t *s0, const int32_t *op_ptr, c
       gexec_ = nullptr;
     }
   }
-  const ChainBuf &b = buf_[c];
+  const ChainBuf &b = cs_[c]->buf;
   CK(cudaMemcpy(b.s0[d.cur], s0, d.nsub, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(b.op_ptr[d.cur], op_ptr, 4 * ((size_t)d.ncell + 1), cudaMemcpyHostToDevice));
   if (n_off > 0) CK(cudaMemcpy(b.op_tau[d.cur], op_tau, 8 * (size_t)n_off, cudaMemcpyHostToDevice));

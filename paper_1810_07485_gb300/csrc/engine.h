@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -26,6 +27,15 @@ struct ChainBuf {
   lcqmc_record *ring = nullptr;
 };
 
+// Persistent state of one chain (device buffers + last known descriptor).
+struct ChainState {
+  ChainSpec spec{};
+  ChainBuf buf{};
+  DevChain dev{};
+  int64_t rec_read = 0;
+  int64_t vcap = 0;  // vertices reserved per update (grown on overflow)
+};
+
 void set_error(const std::string &msg);
 int validate_spec(int64_t L, double S, double J, double beta, ChainSpec &out);
 
@@ -38,6 +48,14 @@ class Engine {
 
   int init(const std::vector<ChainSpec> &specs, void *stream, const lcqmc_allocator *alloc,
            int ring_cap);
+  // Served form: open an engine with no chains, create / destroy chain states
+  // it does not own, and change the resident set between ticks.
+  int open(void *stream, const lcqmc_allocator *alloc, int ring_cap);
+  int create_state(const ChainSpec &spec, ChainState *out);
+  void destroy_state(ChainState *c);
+  int set_chains(const std::vector<ChainState *> &chains);
+  static size_t state_bytes(const ChainSpec &c, int ring_cap);
+  static size_t scratch_bytes(const ChainSpec &c);
   int update(int64_t n);
   int sync();
   int pull_chains();  // device descriptors -> hch (after sync)
@@ -59,8 +77,9 @@ class Engine {
   static size_t estimate_footprint(const std::vector<ChainSpec> &specs, int ring_cap);
 
   cudaStream_t stream() const { return st_; }
-  int nchains() const { return (int)spec_.size(); }
-  const ChainSpec &spec(int64_t i) const { return spec_[i]; }
+  int nchains() const { return (int)cs_.size(); }
+  const ChainSpec &spec(int64_t i) const { return cs_[i]->spec; }
+  int64_t vertex_capacity() const { return vcap_; }
   std::vector<DevChain> hch;
 
  private:
@@ -77,15 +96,16 @@ class Engine {
   bool own_stream_ = false;
   lcqmc_allocator alloc_{};
   bool has_alloc_ = false;
-  std::vector<ChainSpec> spec_;
-  std::vector<ChainBuf> buf_;
-  std::vector<int64_t> rec_read_;
+  std::vector<ChainState *> cs_;
+  std::vector<std::unique_ptr<ChainState>> owned_;
+  int64_t cap_chains_ = 0, cap_tt_ = 0, cap_st_ = 0, cap_bt_ = 0, cap_cells_ = 0, cap_tiles_ = 0,
+          cap_sites_ = 0, cap_bpar_ = 0, cap_subs_ = 0;
+  int grow_array(void **p, int64_t *cap, int64_t need, size_t elem);
+  int layout();
   DevChain *dch_ = nullptr;
   int2 *tile_tab_ = nullptr, *site_tab_ = nullptr, *bond_tab_ = nullptr;
   Launch L_{};
   Scratch s_{};
-  int64_t ncell_tot_ = 0, nsub_tot_ = 0, bpar_tot_ = 0;
-  int64_t ntile_tot_ = 0, nsiteblk_tot_ = 0, nbondblk_tot_ = 0;
   int64_t vcap_ = 0;
   int ring_cap_ = 0;
   size_t fixed_bytes_ = 0, vertex_bytes_ = 0, op_bytes_ = 0;

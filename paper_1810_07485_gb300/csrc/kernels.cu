@@ -4,17 +4,16 @@
 //
 // Phase order per update (the Sec. 4.3 cost table's rows in brackets):
 //   k_bond_parity    spin parity of every bond at each time-block start
-//   k_insert<0>      per cell: Poisson candidates, keep the antiparallel ones,
-//                    count vertices                                  [1, 2]
-//   k_scan_tiles<0>, k_chain_bases   vertex offsets per tile / chain
-//   k_insert<1>      regenerate, merge with old operators, write vertices [2]
+//   k_insert         per cell: Poisson candidates, keep the antiparallel ones,
+//                    merge with old operators, write vertices; offsets by
+//                    decoupled look-back over the tiles          [1, 2]
 //   k_cut            last leg per subsite, tau=0 subspin permutation
 //   k_link           predecessor of each leg on both subsites; union of the two
 //                    fragments below each vertex (lock-free, min root)    [2]
 //   k_compress       root of every node, one coin per loop              [3]
 //   k_est            new operator flags, loop lengths (tile-local loops in
 //                    shared memory, others in global accumulators)      [4]
-//   k_scan_tiles<1>  operator offsets
+//   k_scan_ops       operator offsets per tile
 //   k_compact        next operator list, squared lengths of open loops  [8]
 //   k_sites          spins at tau = 0, vertex-free loops                [8]
 //   k_final          per-chain record, running sums, buffer swap
@@ -92,6 +91,24 @@ __device__ u128 block_sum_u128(u128 v) {
 
 __device__ __forceinline__ bool halted(const Scratch &s) { return __ldcg(s.status) != 0; }
 
+// Tile blocks of the vertex-parallel kernels: TPB threads walk the tile's
+// vertices in id order (coalesced); a vertex's cell comes from a binary search
+// in the tile's cell offsets staged in shared memory.
+constexpr int TPB = 256;
+
+__device__ __forceinline__ int tile_cell_of(const int *cvp, int ncl, int w) {
+  // largest i in [0, ncl) with cvp[i] <= w
+  int lo = 0, hi = ncl - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cvp[mid] <= w)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
 // ---- bond parity at time-block starts ---------------------------------------
 // bpar[(blk) * nbond + b] = parity of the operators of bond b in time blocks
 // before blk; row nblk is the parity over the whole period.
@@ -157,15 +174,52 @@ __device__ __forceinline__ uint64_t cand_bits(int k, const U4 &o0, U4 &o2, uint3
   return ((uint64_t)o2.z | ((uint64_t)o2.w << 32)) >> 11;
 }
 
-template <int Q, int WRITE>
-__global__ void __launch_bounds__(TILE) k_insert(const DevChain *__restrict__ ch,
+// Single pass: every tile counts its cells' vertices, publishes the count, and
+// gets the chain-local offset of its first vertex by decoupled look-back over
+// the tiles before it (tile order = order in which blocks took their ticket,
+// so every tile waited on has started and publishes its count without
+// waiting).  Each wait is bounded; it also gives up when the update halts.
+constexpr unsigned long long LB_AGG = 1ull, LB_INC = 2ull, LB_MASK = (1ull << 62) - 1;
+constexpr int LB_MAX_SPINS = 1 << 24;
+
+__device__ __forceinline__ void lb_publish(unsigned long long *st, int64_t g, unsigned long long flag,
+                                           int64_t v) {
+  atomicExch(st + g, (flag << 62) | ((unsigned long long)v & LB_MASK));
+}
+
+__device__ int64_t lb_lookback(unsigned long long *st, int64_t g, const Scratch &s) {
+  int64_t excl = 0;
+  int spins = 0;
+  for (int64_t p = g - 1;;) {
+    const unsigned long long x = *((volatile unsigned long long *)(st + p));
+    const unsigned long long f = x >> 62;
+    if (f == 0) {
+      if (++spins > LB_MAX_SPINS) {
+        atomicOr(s.status, ST_TIMEOUT);
+        return 0;
+      }
+      if ((spins & 255) == 0 && halted(s)) return 0;
+      __nanosleep(32);
+      continue;
+    }
+    excl += (int64_t)(x & LB_MASK);
+    if (f == LB_INC) return excl;
+    --p;
+  }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(TILE) k_insert(DevChain *__restrict__ ch,
                                                  const int2 *__restrict__ tab, int64_t blk0,
-                                                 Scratch s) {
+                                                 int group, Scratch s) {
   __shared__ int64_t sm[33];
+  __shared__ int64_t s_gt, s_excl;
   if (halted(s)) return;
-  const int64_t gt = blk0 + blockIdx.x;
+  if (threadIdx.x == 0) s_gt = blk0 + (int64_t)atomicAdd(s.tickets + group, 1u);
+  __syncthreads();
+  const int64_t gt = s_gt;
   const int2 t = tab[gt];
-  const DevChain &C = ch[t.x];
+  DevChain &C = ch[t.x];
   const int cell = t.y * TILE + threadIdx.x;
   const bool valid = cell < C.ncell;
   const int cur = C.cur;
@@ -174,19 +228,17 @@ __global__ void __launch_bounds__(TILE) k_insert(const DevChain *__restrict__ ch
   const uint8_t *s0 = C.s0[cur];
   int32_t *vp = s.vptr + C.cell_off;
 
-  int cnt = 0;
-  int b = 0, j = 0;
-  int q0 = 0, q1 = 0, K = 0, par0 = 0;
-  uint64_t t0b = 0, teb = 0, db = 0;
-  NbOps<Q> X;
-  U4 o0 = {0, 0, 0, 0};
-  const uint32_t k0 = (uint32_t)C.seed, k1 = (uint32_t)(C.seed >> 32);
+  uint64_t cu[KMAX];
+  long long ct[KMAX];
+  int nk = 0, cnt = 0, q0 = 0, q1 = 0;
   if (valid) {
+    int b, j;
     cell_bj(C, cell, b, j);
     const int ul = left_sub<Q>(b), ur = right_sub<Q>(b, C.L);
     const int blk = j / TW, jb = blk * TW;
     const uint8_t *prow = s.bpar + C.bpar_off + (int64_t)blk * C.nbond;
-    par0 = (s0[ul] ^ s0[ur]) & 1;
+    int par0 = (s0[ul] ^ s0[ur]) & 1;
+    NbOps<Q> X;
     int k = 0;
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
@@ -205,64 +257,59 @@ __global__ void __launch_bounds__(TILE) k_insert(const DevChain *__restrict__ ch
     }
     q0 = op[cell];
     q1 = op[cell + 1];
-    t0b = C.win[3 * j];
-    teb = C.win[3 * j + 1];
-    db = C.win[3 * j + 2];
-    o0 = philox(TAG_INSERT << 24, (uint32_t)b, (uint32_t)j, C.sweep, k0, k1);
+    const uint64_t t0b = C.win[3 * j], teb = C.win[3 * j + 1], db = C.win[3 * j + 2];
+    const uint32_t k0 = (uint32_t)C.seed, k1 = (uint32_t)(C.seed >> 32);
+    const U4 o0 = philox(TAG_INSERT << 24, (uint32_t)b, (uint32_t)j, C.sweep, k0, k1);
     const uint64_t U = (uint64_t)o0.x | ((uint64_t)o0.y << 32);
     const uint64_t *T = (j == C.nwin - 1) ? C.T_last : c_T_full;
+    int K = 0;
     while (K < KMAX - 1 && U >= T[K]) ++K;
     if ((long long)db <= 0) K = 0;  // empty last window
-  }
-
-  if (!WRITE) {
-    if (valid) {
-      U4 o2 = {0, 0, 0, 0};
-      int kept = 0;
-      for (int k = 0; k < K; ++k) {
-        const uint64_t u53 = cand_bits(k, o0, o2, (uint32_t)b, (uint32_t)j, C.sweep, k0, k1);
-        const long long tau = (long long)tau_fma_bits(db, t0b, u53);
-        if (!(tau < (long long)teb)) continue;
-        if ((par0 ^ nb_parity<Q>(X, otau, tau, b)) & 1) ++kept;
+    U4 o2 = {0, 0, 0, 0};
+    for (int kk = 0; kk < K; ++kk) {
+      const uint64_t u53 = cand_bits(kk, o0, o2, (uint32_t)b, (uint32_t)j, C.sweep, k0, k1);
+      const long long tau = (long long)tau_fma_bits(db, t0b, u53);
+      if (!(tau < (long long)teb)) continue;
+      if (!((par0 ^ nb_parity<Q>(X, otau, tau, b)) & 1)) continue;
+      // insertion sort by u53 (stable: equal keys keep draw order)
+      int p = nk;
+      while (p > 0 && cu[p - 1] > u53) {
+        cu[p] = cu[p - 1];
+        ct[p] = ct[p - 1];
+        --p;
       }
-      cnt = (q1 - q0) + kept;
-      vp[cell] = cnt;
+      cu[p] = u53;
+      ct[p] = tau;
+      ++nk;
     }
-    const int64_t tot = block_sum<int64_t>((int64_t)cnt, sm);
-    if (threadIdx.x == 0) s.tile_sum[gt] = tot;
-    return;
+    cnt = (q1 - q0) + nk;
   }
-
-  // WRITE: offsets, then the merged vertex list of the cell.
-  if (valid) cnt = vp[cell];
   int64_t tot;
   const int64_t ex = block_excl_scan<int64_t>((int64_t)cnt, sm, tot);
-  if (!valid) return;
-  const int32_t off = (int32_t)(s.tile_pref[gt] + ex);
-  vp[cell] = off;
-  if (cell == C.ncell - 1) vp[C.ncell] = (int32_t)C.n;
-  if (cnt == 0) return;
-
-  uint64_t cu[KMAX];
-  long long ct[KMAX];
-  int nk = 0;
-  U4 o2 = {0, 0, 0, 0};
-  for (int k = 0; k < K; ++k) {
-    const uint64_t u53 = cand_bits(k, o0, o2, (uint32_t)b, (uint32_t)j, C.sweep, k0, k1);
-    const long long tau = (long long)tau_fma_bits(db, t0b, u53);
-    if (!(tau < (long long)teb)) continue;
-    if (!((par0 ^ nb_parity<Q>(X, otau, tau, b)) & 1)) continue;
-    // insertion sort by u53 (stable: equal keys keep draw order)
-    int p = nk;
-    while (p > 0 && cu[p - 1] > u53) {
-      cu[p] = cu[p - 1];
-      ct[p] = ct[p - 1];
-      --p;
+  if (threadIdx.x == 0) {
+    int64_t excl = 0;
+    if (t.y == 0) {
+      lb_publish(s.tile_state, gt, LB_INC, tot);
+    } else {
+      lb_publish(s.tile_state, gt, LB_AGG, tot);
+      excl = lb_lookback(s.tile_state, gt, s);
+      lb_publish(s.tile_state, gt, LB_INC, excl + tot);
     }
-    cu[p] = u53;
-    ct[p] = tau;
-    ++nk;
+    s_excl = excl;
+    if (t.y == C.ntile - 1) {
+      C.n = excl + tot;
+      if (excl + tot > C.vcap) atomicOr(s.status, ST_VTX_OVERFLOW);
+      if (excl + tot > (int64_t)0x7fffff00) atomicOr(s.status, ST_ID_OVERFLOW);
+    }
   }
+  __syncthreads();
+  if (!valid) return;
+  const int64_t off64 = s_excl + ex;
+  if (off64 + cnt > C.vcap) return;  // overflow: the host grows the chain and replays
+  const int32_t off = (int32_t)off64;
+  vp[cell] = off;
+  if (cell == C.ncell - 1) vp[C.ncell] = off + cnt;
+  if (cnt == 0) return;
   const int64_t vb = C.vtx_base;
   long long *vt = (long long *)s.vtau + vb;
   int q = q0, ki = 0, r = off;
@@ -281,61 +328,27 @@ __global__ void __launch_bounds__(TILE) k_insert(const DevChain *__restrict__ ch
     s.parent[vb + r] = r;
     ++r;
   }
-  if (r - off != cnt) fail_check(s, 1, cell, cnt, r - off, nk, q1 - q0);
 }
 
-// ---- per-chain scans of tile totals ------------------------------------------
-template <int MODE>
-__global__ void __launch_bounds__(1024) k_scan_tiles(DevChain *__restrict__ ch, Scratch s) {
+// ---- per-chain scan of the tiles' new-operator counts ------------------------------
+__global__ void __launch_bounds__(1024) k_scan_ops(DevChain *__restrict__ ch, Scratch s) {
   __shared__ int64_t sm[33];
   if (halted(s)) return;
   DevChain &C = ch[blockIdx.x];
-  const int64_t *in = MODE == 0 ? s.tile_sum : s.tile_sum2;
-  int64_t *out = MODE == 0 ? s.tile_pref : s.tile_pref2;
   const int nt = C.ntile;
   const int per = (nt + blockDim.x - 1) / blockDim.x;
   const int lo = min(nt, (int)threadIdx.x * per), hi = min(nt, lo + per);
   int64_t sum = 0;
-  for (int i = lo; i < hi; ++i) sum += in[C.tile0 + i];
+  for (int i = lo; i < hi; ++i) sum += s.tile_sum2[C.tile0 + i];
   int64_t total;
   int64_t run = block_excl_scan<int64_t>(sum, sm, total);
   for (int i = lo; i < hi; ++i) {
-    out[C.tile0 + i] = run;
-    run += in[C.tile0 + i];
+    s.tile_pref2[C.tile0 + i] = run;
+    run += s.tile_sum2[C.tile0 + i];
   }
   if (threadIdx.x == 0) {
-    if (MODE == 0) {
-      C.n = total;
-    } else {
-      C.n_off_new = total;
-      if (total > C.op_cap) atomicOr(s.status, ST_OP_OVERFLOW);
-    }
-  }
-}
-
-__global__ void __launch_bounds__(1024) k_chain_bases(DevChain *__restrict__ ch, int nchains,
-                                                      Scratch s) {
-  __shared__ int64_t sm[33];
-  if (halted(s)) return;
-  int64_t base = 0;
-  bool bad = false;
-  for (int c0 = 0; c0 < nchains; c0 += blockDim.x) {
-    const int c = c0 + threadIdx.x;
-    int64_t sz = 0;
-    if (c < nchains) {
-      const int64_t n = ch[c].n;
-      if (n > (int64_t)0x7fffff00) bad = true;
-      sz = (n + 127) & ~(int64_t)127;
-    }
-    int64_t total;
-    const int64_t ex = block_excl_scan<int64_t>(sz, sm, total);
-    if (c < nchains) ch[c].vtx_base = base + ex;
-    base += total;
-  }
-  if (bad) atomicOr(s.status, ST_ID_OVERFLOW);
-  if (threadIdx.x == 0) {
-    s.need[0] = base;
-    if (base > s.vcap) atomicOr(s.status, ST_VTX_OVERFLOW);
+    C.n_off_new = total;
+    if (total > C.op_cap) atomicOr(s.status, ST_OP_OVERFLOW);
   }
 }
 
@@ -463,49 +476,74 @@ __device__ __forceinline__ void before_window(const DevChain &C, const int32_t *
   }
 }
 
+// Per-cell linking context, staged in shared memory by one thread per cell.
 template <int Q>
-__global__ void __launch_bounds__(TILE) k_link(const DevChain *__restrict__ ch,
-                                               const int2 *__restrict__ tab, int64_t blk0,
-                                               Scratch s) {
+struct LinkCell {
+  static constexpr int NO = 2 * Q - 1;  // other bonds touching each of the two subsites
+  int wa[2][NO], we[2][NO], wc[2][NO], bj[2][NO], bjc[2][NO];
+  int own_bj, own_bjc, cut[2], cutc[2];
+};
+
+// First index q in [lo, hi) whose key (tau, id) is not below (tw, w).
+__device__ __forceinline__ int key_lower_bound(const long long *vt, int lo, int hi, long long tw,
+                                               int w) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const long long tq = vt[mid];
+    if (tq < tw || (tq == tw && mid < w))
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+template <int Q>
+__global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
+                                              const int2 *__restrict__ tab, int64_t blk0,
+                                              Scratch s) {
+  __shared__ LinkCell<Q> lc[TILE];
+  __shared__ int cvp[TILE + 1];
   if (halted(s)) return;
   const int2 t = tab[blk0 + blockIdx.x];
   const DevChain &C = ch[t.x];
-  const int cell = t.y * TILE + threadIdx.x;
-  if (cell >= C.ncell) return;
+  const int c0 = t.y * TILE, c1 = min(C.ncell, c0 + TILE), ncl = c1 - c0;
   const int32_t *vp = s.vptr + C.cell_off;
-  const int v0 = vp[cell], v1 = vp[cell + 1];
-  if (v0 == v1) return;
-  int b, j;
-  cell_bj(C, cell, b, j);
+  for (int i = threadIdx.x; i <= ncl; i += blockDim.x) cvp[i] = vp[c0 + i];
+  if (threadIdx.x < ncl) {
+    LinkCell<Q> &L = lc[threadIdx.x];
+    int b, j;
+    cell_bj(C, c0 + threadIdx.x, b, j);
+    const int sub[2] = {left_sub<Q>(b), right_sub<Q>(b, C.L)};
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+      int k = 0;
+#pragma unroll
+      for (int m = 0; m < 2 * Q; ++m) {
+        const int bb = inc_bond<Q>(sub[sd], m, C.L);
+        if (bb == b) continue;
+        const int cj = cell_of(C, bb, j);
+        L.wa[sd][k] = vp[cj];
+        L.we[sd][k] = vp[cj + 1];
+        L.wc[sd][k] = cj;
+        before_window(C, vp, bb, j, L.bj[sd][k], L.bjc[sd][k]);
+        ++k;
+      }
+      L.cut[sd] = s.cut_node[C.sub_off + sub[sd]];
+      L.cutc[sd] = s.cut_cell[C.sub_off + sub[sd]];
+    }
+    before_window(C, vp, b, j, L.own_bj, L.own_bjc);
+  }
+  __syncthreads();
+  const int a = cvp[0], e = cvp[ncl];
   const int64_t vb = C.vtx_base, wb = vb >> 5;
   const long long *__restrict__ vt = (const long long *)s.vtau + vb;
   int32_t *par = s.parent + vb;
-  const int sub[2] = {left_sub<Q>(b), right_sub<Q>(b, C.L)};
-  constexpr int NO = 2 * Q - 1;
-  int wa[2][NO], we[2][NO], wq[2][NO], wc[2][NO], bj[2][NO], bjc[2][NO];
-#pragma unroll
-  for (int sd = 0; sd < 2; ++sd) {
-    int k = 0;
-#pragma unroll
-    for (int m = 0; m < 2 * Q; ++m) {
-      const int bb = inc_bond<Q>(sub[sd], m, C.L);
-      if (bb == b) continue;
-      const int cj = cell_of(C, bb, j);
-      wa[sd][k] = vp[cj];
-      we[sd][k] = vp[cj + 1];
-      wq[sd][k] = wa[sd][k];
-      wc[sd][k] = cj;
-      before_window(C, vp, bb, j, bj[sd][k], bjc[sd][k]);
-      ++k;
-    }
-  }
-  int own_bj, own_bjc;
-  before_window(C, vp, b, j, own_bj, own_bjc);
-  const int cut0 = s.cut_node[C.sub_off + sub[0]], cut1 = s.cut_node[C.sub_off + sub[1]];
-  const int cutc0 = s.cut_cell[C.sub_off + sub[0]], cutc1 = s.cut_cell[C.sub_off + sub[1]];
-  const int mytile = cell / TILE;
-
-  for (int w = v0; w < v1; ++w) {
+  const int mytile = t.y;
+  for (int w = a + threadIdx.x; w < e; w += blockDim.x) {
+    const int ci = tile_cell_of(cvp, ncl, w);
+    const LinkCell<Q> &L = lc[ci];
+    const int cell = c0 + ci, v0 = cvp[ci];
     const long long tw = vt[w];
     int P[2], Pc[2];
     uint8_t wrapbits = 0;
@@ -517,29 +555,21 @@ __global__ void __launch_bounds__(TILE) k_link(const DevChain *__restrict__ ch,
         best = w - 1;
         bestc = cell;
         bt = vt[w - 1];
-      } else if (own_bj >= 0) {
-        best = own_bj;
-        bestc = own_bjc;
-        bt = vt[own_bj];
+      } else if (L.own_bj >= 0) {
+        best = L.own_bj;
+        bestc = L.own_bjc;
+        bt = vt[best];
       }
 #pragma unroll
-      for (int k = 0; k < NO; ++k) {
-        int q = wq[sd][k];
-        while (q < we[sd][k]) {
-          const long long tq = vt[q];
-          if (tq < tw || (tq == tw && q < w))
-            ++q;
-          else
-            break;
-        }
-        wq[sd][k] = q;
+      for (int k = 0; k < LinkCell<Q>::NO; ++k) {
+        const int q = key_lower_bound(vt, L.wa[sd][k], L.we[sd][k], tw, w);
         int cand, candc;
-        if (q > wa[sd][k]) {
+        if (q > L.wa[sd][k]) {
           cand = q - 1;
-          candc = wc[sd][k];
+          candc = L.wc[sd][k];
         } else {
-          cand = bj[sd][k];
-          candc = bjc[sd][k];
+          cand = L.bj[sd][k];
+          candc = L.bjc[sd][k];
         }
         if (cand >= 0) {
           const long long tc = vt[cand];
@@ -551,11 +581,11 @@ __global__ void __launch_bounds__(TILE) k_link(const DevChain *__restrict__ ch,
         }
       }
       if (best < 0) {
-        best = sd ? cut1 : cut0;
-        bestc = sd ? cutc1 : cutc0;
+        best = L.cut[sd];
+        bestc = L.cutc[sd];
         wrapbits |= sd ? VF_WRAP_R : VF_WRAP_L;
         if (best < 0) {
-          fail_check(s, 2, cell, w, sd, sub[sd], 0);
+          fail_check(s, 2, cell, w, sd, 0, 0);
           best = w;
           bestc = cell;
         }
@@ -635,21 +665,40 @@ __device__ __forceinline__ void open_add(int *keys, unsigned long long *vals, in
 }
 
 template <int Q>
-__global__ void __launch_bounds__(TILE) k_est(const DevChain *__restrict__ ch,
-                                              const int2 *__restrict__ tab, int64_t blk0,
-                                              Scratch s) {
+__global__ void __launch_bounds__(TPB) k_est(const DevChain *__restrict__ ch,
+                                             const int2 *__restrict__ tab, int64_t blk0,
+                                             Scratch s) {
   extern __shared__ unsigned long long est_dyn[];
   unsigned long long *cW = est_dyn, *cC = est_dyn + SMEM_CAP, *cS = est_dyn + 2 * SMEM_CAP;
   __shared__ int okeys[OPEN_SLOTS];
   __shared__ unsigned long long ovals[3 * OPEN_SLOTS];
+  __shared__ int cvp[TILE + 1];
+  __shared__ int cnew[TILE];
+  __shared__ long long ccl[TILE], csl[TILE], ccr[TILE], csr[TILE], cxl[TILE], cxr[TILE];
   __shared__ int64_t sm[33];
   if (halted(s)) return;
   const int64_t gt = blk0 + blockIdx.x;
   const int2 t = tab[gt];
   const DevChain &C = ch[t.x];
-  const int c0 = t.y * TILE, c1 = min(C.ncell, c0 + TILE);
+  const int c0 = t.y * TILE, c1 = min(C.ncell, c0 + TILE), ncl = c1 - c0;
   const int32_t *vp = s.vptr + C.cell_off;
-  const int a = vp[c0], e = vp[c1];
+  for (int i = threadIdx.x; i <= ncl; i += blockDim.x) cvp[i] = vp[c0 + i];
+  if (threadIdx.x < ncl) {
+    // per cell: Fourier weights of its two sites, cut crossings (in ticks)
+    int b, j;
+    cell_bj(C, c0 + threadIdx.x, b, j);
+    const int ul = left_sub<Q>(b), ur = right_sub<Q>(b, C.L);
+    const int xl = ul / Q, xr = ur / Q;
+    ccl[threadIdx.x] = C.cosq[xl];
+    csl[threadIdx.x] = C.sinq[xl];
+    ccr[threadIdx.x] = C.cosq[xr];
+    csr[threadIdx.x] = C.sinq[xr];
+    cxl[threadIdx.x] = (long long)s.cut_cross[C.sub_off + ul] * C.qbeta;
+    cxr[threadIdx.x] = (long long)s.cut_cross[C.sub_off + ur] * C.qbeta;
+    cnew[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  const int a = cvp[0], e = cvp[ncl];
   const int nv = min(e - a, SMEM_CAP);
   for (int i = threadIdx.x; i < nv; i += blockDim.x) cW[i] = cC[i] = cS[i] = 0ull;
   for (int i = threadIdx.x; i < OPEN_SLOTS; i += blockDim.x) {
@@ -659,54 +708,46 @@ __global__ void __launch_bounds__(TILE) k_est(const DevChain *__restrict__ ch,
   __syncthreads();
   const int64_t vb = C.vtx_base, wb = vb >> 5;
   const int32_t *par = s.parent + vb;
-  const int cell = c0 + threadIdx.x;
-  int newcnt = 0;
-  if (cell < c1) {
-    const int v0 = vp[cell], v1 = vp[cell + 1];
-    int b, j;
-    cell_bj(C, cell, b, j);
-    const int ul = left_sub<Q>(b), ur = right_sub<Q>(b, C.L);
-    const int xl = ul / Q, xr = ur / Q;
-    const long long cl = C.cosq[xl], sl = C.sinq[xl], cr = C.cosq[xr], sr = C.sinq[xr];
-    // a fragment through the tau=0 cut gains (crossings) x beta, in ticks
-    const long long crossl = (long long)s.cut_cross[C.sub_off + ul] * C.qbeta;
-    const long long crossr = (long long)s.cut_cross[C.sub_off + ur] * C.qbeta;
-    const uint64_t *vt = (const uint64_t *)s.vtau + vb;
-    const int F = C.F;
-    for (int w = v0; w < v1; ++w) {
-      const int P = s.pl[vb + w], R = s.pr[vb + w];
-      const uint8_t f = s.vflag[vb + w];
-      const int rb = __ldcg(par + P), ra = __ldcg(par + w);
-      const int nf = (f & VF_OLD) ^ get_bit(s.flipbits, wb, rb) ^ get_bit(s.flipbits, wb, ra);
-      s.vflag[vb + w] = (uint8_t)(f | (nf ? VF_NEW : 0));
-      newcnt += nf;
-      // fragment lengths in ticks of 2^-F: q(tau_top) - q(tau_bottom) (+ crossings)
-      const long long qw = q_time(vt[w], F);
-      long long dl = qw - q_time(vt[P], F);
-      if (f & VF_WRAP_L) dl += crossl;
-      long long dr = qw - q_time(vt[R], F);
-      if (f & VF_WRAP_R) dr += crossr;
-      const long long W = dl + dr;
-      const long long Cc = mul_q32(dl, cl) + mul_q32(dr, cr);
-      const long long Ss = mul_q32(dl, sl) + mul_q32(dr, sr);
-      if (get_bit(s.openroot, wb, rb)) {
-        open_add(okeys, ovals, rb, W, Cc, Ss, s, vb);
+  const uint64_t *vt = (const uint64_t *)s.vtau + vb;
+  const int F = C.F;
+  for (int w = a + threadIdx.x; w < e; w += blockDim.x) {
+    const int ci = tile_cell_of(cvp, ncl, w);
+    const int P = s.pl[vb + w], R = s.pr[vb + w];
+    const uint8_t f = s.vflag[vb + w];
+    const int rb = __ldcg(par + P), ra = __ldcg(par + w);
+    const int nf = (f & VF_OLD) ^ get_bit(s.flipbits, wb, rb) ^ get_bit(s.flipbits, wb, ra);
+    s.vflag[vb + w] = (uint8_t)(f | (nf ? VF_NEW : 0));
+    if (nf) atomicAdd(cnew + ci, 1);
+    // fragment lengths in ticks of 2^-F: q(tau_top) - q(tau_bottom) (+ crossings)
+    const long long qw = q_time(vt[w], F);
+    long long dl = qw - q_time(vt[P], F);
+    if (f & VF_WRAP_L) dl += cxl[ci];
+    long long dr = qw - q_time(vt[R], F);
+    if (f & VF_WRAP_R) dr += cxr[ci];
+    const long long W = dl + dr;
+    const long long Cc = mul_q32(dl, ccl[ci]) + mul_q32(dr, ccr[ci]);
+    const long long Ss = mul_q32(dl, csl[ci]) + mul_q32(dr, csr[ci]);
+    if (get_bit(s.openroot, wb, rb)) {
+      open_add(okeys, ovals, rb, W, Cc, Ss, s, vb);
+    } else {
+      const int li = rb - a;
+      if (li < 0 || li >= nv) {
+        fail_check(s, 3, c0 + ci, w, rb, a, ((long long)nv << 32) | (unsigned)P);
       } else {
-        const int li = rb - a;
-        if (li < 0 || li >= nv) {
-          fail_check(s, 3, cell, w, rb, a, ((long long)nv << 32) | (unsigned)P);
-        } else {
-          atomicAdd(cW + li, (unsigned long long)W);
-          atomicAdd(cC + li, (unsigned long long)Cc);
-          atomicAdd(cS + li, (unsigned long long)Ss);
-        }
+        atomicAdd(cW + li, (unsigned long long)W);
+        atomicAdd(cC + li, (unsigned long long)Cc);
+        atomicAdd(cS + li, (unsigned long long)Ss);
       }
     }
-    C.op_ptr[C.cur ^ 1][cell] = newcnt;
+  }
+  __syncthreads();
+  int newcnt = 0;
+  if (threadIdx.x < ncl) {
+    newcnt = cnew[threadIdx.x];
+    C.op_ptr[C.cur ^ 1][c0 + threadIdx.x] = newcnt;
   }
   const int64_t tot = block_sum<int64_t>((int64_t)newcnt, sm);
   if (threadIdx.x == 0) s.tile_sum2[gt] = tot;
-  __syncthreads();
   u128 w2 = 0, f2 = 0;
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
     const int v = a + i;
@@ -716,11 +757,11 @@ __global__ void __launch_bounds__(TILE) k_est(const DevChain *__restrict__ ch,
     }
   }
   for (int h = threadIdx.x; h < OPEN_SLOTS; h += blockDim.x) {
-    const int k = okeys[h];
-    if (k >= 0) {
-      atomicAdd(s.accW + vb + k, ovals[3 * h]);
-      atomicAdd(s.accC + vb + k, ovals[3 * h + 1]);
-      atomicAdd(s.accS + vb + k, ovals[3 * h + 2]);
+    const int kk = okeys[h];
+    if (kk >= 0) {
+      atomicAdd(s.accW + vb + kk, ovals[3 * h]);
+      atomicAdd(s.accC + vb + kk, ovals[3 * h + 1]);
+      atomicAdd(s.accS + vb + kk, ovals[3 * h + 2]);
     }
   }
   w2 = block_sum_u128(w2);
@@ -734,32 +775,41 @@ __global__ void __launch_bounds__(TILE) k_est(const DevChain *__restrict__ ch,
 }
 
 // ---- next operator list + open loops -------------------------------------------------
-__global__ void __launch_bounds__(TILE) k_compact(const DevChain *__restrict__ ch,
-                                                  const int2 *__restrict__ tab, int64_t blk0,
-                                                  Scratch s) {
+// Cell offsets from a block scan of the per-cell counts; vertex positions from
+// a chunked block scan of the new-operator flags in id order (the same order).
+__global__ void __launch_bounds__(TPB) k_compact(const DevChain *__restrict__ ch,
+                                                 const int2 *__restrict__ tab, int64_t blk0,
+                                                 Scratch s) {
   __shared__ int64_t sm[33];
   if (halted(s)) return;
   const int64_t gt = blk0 + blockIdx.x;
   const int2 t = tab[gt];
   const DevChain &C = ch[t.x];
-  const int c0 = t.y * TILE, c1 = min(C.ncell, c0 + TILE);
-  const int cell = c0 + threadIdx.x;
+  const int c0 = t.y * TILE, c1 = min(C.ncell, c0 + TILE), ncl = c1 - c0;
   int32_t *nptr = C.op_ptr[C.cur ^ 1];
   double *ntau = C.op_tau[C.cur ^ 1];
   const int32_t *vp = s.vptr + C.cell_off;
   const int64_t vb = C.vtx_base, wb = vb >> 5;
-  int cnt = (cell < c1) ? nptr[cell] : 0;
-  int64_t tot;
-  const int64_t ex = block_excl_scan<int64_t>((int64_t)cnt, sm, tot);
-  if (cell < c1) {
-    int off = (int)(s.tile_pref2[gt] + ex);
-    nptr[cell] = off;
-    if (cell == C.ncell - 1) nptr[C.ncell] = (int32_t)C.n_off_new;
-    const int v0 = vp[cell], v1 = vp[cell + 1];
-    for (int w = v0; w < v1; ++w)
-      if (s.vflag[vb + w] & VF_NEW) ntau[off++] = s.vtau[vb + w];
+  const int64_t base = s.tile_pref2[gt];
+  {
+    const int cnt = (threadIdx.x < ncl) ? nptr[c0 + threadIdx.x] : 0;
+    int64_t tot;
+    const int64_t ex = block_excl_scan<int64_t>((int64_t)cnt, sm, tot);
+    if (threadIdx.x < ncl) {
+      nptr[c0 + threadIdx.x] = (int32_t)(base + ex);
+      if (c0 + (int)threadIdx.x == C.ncell - 1) nptr[C.ncell] = (int32_t)C.n_off_new;
+    }
   }
   const int a = vp[c0], e = vp[c1];
+  int64_t run = base;
+  for (int w0 = a; w0 < e; w0 += blockDim.x) {
+    const int w = w0 + threadIdx.x;
+    const int f = (w < e) ? ((s.vflag[vb + w] & VF_NEW) ? 1 : 0) : 0;
+    int64_t tot;
+    const int64_t ex = block_excl_scan<int64_t>((int64_t)f, sm, tot);
+    if (f) ntau[run + ex] = s.vtau[vb + w];
+    run += tot;
+  }
   u128 w2 = 0, f2 = 0;
   for (int v = a + threadIdx.x; v < e; v += blockDim.x) {
     if (get_bit(s.openroot, wb, v)) {
@@ -913,30 +963,13 @@ void launch_bond_parity(const Launch &L, cudaStream_t st) {
       k_bond_parity<<<g1(L.nbondblk[q]), BOND_BLOCK, 0, st>>>(L.ch, L.bond_tab, L.bond0[q], L.s);
 }
 
-void launch_insert(const Launch &L, int write, cudaStream_t st) {
-  if (L.ntile[0]) {
-    if (write)
-      k_insert<1, 1><<<g1(L.ntile[0]), TILE, 0, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
-    else
-      k_insert<1, 0><<<g1(L.ntile[0]), TILE, 0, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
-  }
-  if (L.ntile[1]) {
-    if (write)
-      k_insert<2, 1><<<g1(L.ntile[1]), TILE, 0, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
-    else
-      k_insert<2, 0><<<g1(L.ntile[1]), TILE, 0, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
-  }
+void launch_insert(const Launch &L, cudaStream_t st) {
+  if (L.ntile[0]) k_insert<1><<<g1(L.ntile[0]), TILE, 0, st>>>(L.ch, L.tile_tab, L.tile0[0], 0, L.s);
+  if (L.ntile[1]) k_insert<2><<<g1(L.ntile[1]), TILE, 0, st>>>(L.ch, L.tile_tab, L.tile0[1], 1, L.s);
 }
 
-void launch_scan(const Launch &L, int mode, cudaStream_t st) {
-  if (mode == 0)
-    k_scan_tiles<0><<<L.nchains, 1024, 0, st>>>(L.ch, L.s);
-  else
-    k_scan_tiles<1><<<L.nchains, 1024, 0, st>>>(L.ch, L.s);
-}
-
-void launch_chain_bases(const Launch &L, cudaStream_t st) {
-  k_chain_bases<<<1, 1024, 0, st>>>(L.ch, L.nchains, L.s);
+void launch_scan_ops(const Launch &L, cudaStream_t st) {
+  k_scan_ops<<<L.nchains, 1024, 0, st>>>(L.ch, L.s);
 }
 
 void launch_cut(const Launch &L, cudaStream_t st) {
@@ -945,8 +978,8 @@ void launch_cut(const Launch &L, cudaStream_t st) {
 }
 
 void launch_link(const Launch &L, cudaStream_t st) {
-  if (L.ntile[0]) k_link<1><<<g1(L.ntile[0]), TILE, 0, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
-  if (L.ntile[1]) k_link<2><<<g1(L.ntile[1]), TILE, 0, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
+  if (L.ntile[0]) k_link<1><<<g1(L.ntile[0]), TPB, 0, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
+  if (L.ntile[1]) k_link<2><<<g1(L.ntile[1]), TPB, 0, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
 }
 
 void launch_compress(const Launch &L, cudaStream_t st) {
@@ -967,13 +1000,13 @@ int init_kernel_attributes() {
 }
 
 void launch_est(const Launch &L, cudaStream_t st) {
-  if (L.ntile[0]) k_est<1><<<g1(L.ntile[0]), TILE, EST_DYN_SMEM, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
-  if (L.ntile[1]) k_est<2><<<g1(L.ntile[1]), TILE, EST_DYN_SMEM, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
+  if (L.ntile[0]) k_est<1><<<g1(L.ntile[0]), TPB, EST_DYN_SMEM, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
+  if (L.ntile[1]) k_est<2><<<g1(L.ntile[1]), TPB, EST_DYN_SMEM, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
 }
 
 void launch_compact(const Launch &L, cudaStream_t st) {
   const int64_t n = L.ntile[0] + L.ntile[1];
-  if (n) k_compact<<<g1(n), TILE, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
+  if (n) k_compact<<<g1(n), TPB, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
 }
 
 void launch_sites(const Launch &L, cudaStream_t st) {

@@ -20,9 +20,8 @@ struct Launch {
 void set_full_table(const uint64_t *T, cudaStream_t st);
 int init_kernel_attributes();
 void launch_bond_parity(const Launch &L, cudaStream_t st);
-void launch_insert(const Launch &L, int write, cudaStream_t st);
-void launch_scan(const Launch &L, int mode, cudaStream_t st);
-void launch_chain_bases(const Launch &L, cudaStream_t st);
+void launch_insert(const Launch &L, cudaStream_t st);
+void launch_scan_ops(const Launch &L, cudaStream_t st);
 void launch_cut(const Launch &L, cudaStream_t st);
 void launch_link(const Launch &L, cudaStream_t st);
 void launch_compress(const Launch &L, cudaStream_t st);

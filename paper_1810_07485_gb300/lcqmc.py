@@ -18,8 +18,7 @@ ERRORS = {-1: "E_INVAL", -2: "E_NOMEM", -3: "E_TOO_LARGE", -4: "E_ID_OVERFLOW",
           -5: "E_DEVICE_TIMEOUT", -6: "E_CUDA", -7: "E_STATE", -8: "E_NOT_FOUND",
           -9: "E_CANCELLED", -10: "E_CAPACITY"}
 NPHASE = 8
-PHASES = ["insert_count", "offsets", "insert_write", "link_union", "loop_ids", "loop_props", "op_rewrite",
-          "spin_rewrite"]
+PHASES = ["insert", "cut", "link_union", "loop_ids", "loop_props", "op_offsets", "op_rewrite", "spin_rewrite"]
 
 
 class LcqmcError(RuntimeError):
@@ -118,6 +117,9 @@ def lib():
         "lcqmc_poll": [vp, u64, P(Result)],
         "lcqmc_cancel": [vp, u64],
         "lcqmc_server_destroy": [vp],
+        "lcqmc_footprint": [i64, dbl, dbl, dbl, P(ctypes.c_size_t)],
+        "lcqmc_selftest": [i32, i64, u64, P(i64)],
+        "lcqmc_loops_noalloc": [vp, vp, i64, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -304,3 +306,46 @@ class Batch:
         cnt = ctypes.c_int64()
         _check(lib().lcqmc_batch_get_records(self.h, int(i), buf, int(max_n), ctypes.byref(cnt)))
         return records_to_numpy(buf, cnt.value)
+
+
+def footprint(L, beta, S=0.5, J=1.0):
+    """Device bytes one served chain holds (host-only computation)."""
+    b = ctypes.c_size_t()
+    _check(lib().lcqmc_footprint(int(L), float(S), float(J), float(beta), ctypes.byref(b)))
+    return b.value
+
+
+class Server:
+    """Served form: continuous batching of simulation requests (lcqmc_server_*)."""
+
+    def __init__(self, hbm_budget, max_slots):
+        h = ctypes.c_void_p()
+        _check(lib().lcqmc_server_create(int(hbm_budget), int(max_slots), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().lcqmc_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, L, beta, n_updates, S=0.5, J=1.0, seed=1):
+        """Returns a ticket, or raises LcqmcError (E_TOO_LARGE, E_ID_OVERFLOW, ...)."""
+        r = Request(int(L), float(S), float(J), float(beta), int(seed) & (2**64 - 1), int(n_updates))
+        t = ctypes.c_uint64()
+        _check(lib().lcqmc_submit(self.h, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else the Result (status, obs, timestamps)."""
+        res = Result()
+        rc = _check(lib().lcqmc_poll(self.h, int(ticket), ctypes.byref(res)))
+        return None if rc == PENDING else res
+
+    def cancel(self, ticket):
+        _check(lib().lcqmc_cancel(self.h, int(ticket)))
