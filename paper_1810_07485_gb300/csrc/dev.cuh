@@ -82,7 +82,7 @@ struct Scratch {
   double *vtau;
   uint8_t *vflag;
   int32_t *pl, *pr, *parent;
-  unsigned long long *accW, *accC, *accS;
+  unsigned long long *acc;  // per vertex: W, C, S, pad (32-byte record), open loops only
   uint32_t *openmark, *openroot, *flipbits;
   int64_t vcap;
   unsigned long long *tile_state;  // per tile: insertion look-back word (flag << 62 | count)

@@ -152,16 +152,14 @@ void Engine::free_vertex() {
   dfree(s_.pl);
   dfree(s_.pr);
   dfree(s_.parent);
-  dfree(s_.accW);
-  dfree(s_.accC);
-  dfree(s_.accS);
+  dfree(s_.acc);
   dfree(s_.openmark);
   dfree(s_.openroot);
   dfree(s_.flipbits);
   s_.vtau = nullptr;
   s_.vflag = nullptr;
   s_.pl = s_.pr = s_.parent = nullptr;
-  s_.accW = s_.accC = s_.accS = nullptr;
+  s_.acc = nullptr;
   s_.openmark = s_.openroot = s_.flipbits = nullptr;
   vertex_bytes_ = 0;
 }
@@ -174,19 +172,15 @@ int Engine::alloc_vertex(int64_t vcap) {
   DALLOC(s_.pl, int32_t, vcap);
   DALLOC(s_.pr, int32_t, vcap);
   DALLOC(s_.parent, int32_t, vcap);
-  DALLOC(s_.accW, unsigned long long, vcap);
-  DALLOC(s_.accC, unsigned long long, vcap);
-  DALLOC(s_.accS, unsigned long long, vcap);
+  DALLOC(s_.acc, unsigned long long, 4 * vcap);
   const int64_t nw = vcap / 32 + 1;
   DALLOC(s_.openmark, uint32_t, nw);
   DALLOC(s_.openroot, uint32_t, nw);
   DALLOC(s_.flipbits, uint32_t, nw);
-  CK(cudaMemsetAsync(s_.accW, 0, sizeof(unsigned long long) * vcap, st_));
-  CK(cudaMemsetAsync(s_.accC, 0, sizeof(unsigned long long) * vcap, st_));
-  CK(cudaMemsetAsync(s_.accS, 0, sizeof(unsigned long long) * vcap, st_));
+  CK(cudaMemsetAsync(s_.acc, 0, 4 * sizeof(unsigned long long) * vcap, st_));
   s_.vcap = vcap;
   vcap_ = vcap;
-  vertex_bytes_ = (size_t)vcap * (8 + 1 + 12 + 24) + 3 * (size_t)nw * 4;
+  vertex_bytes_ = (size_t)vcap * (8 + 1 + 12 + 32) + 3 * (size_t)nw * 4;
   L_.s = s_;
   if (gexec_) {
     cudaGraphExecDestroy(gexec_);

@@ -187,24 +187,37 @@ __device__ __forceinline__ void lb_publish(unsigned long long *st, int64_t g, un
   atomicExch(st + g, (flag << 62) | ((unsigned long long)v & LB_MASK));
 }
 
-__device__ int64_t lb_lookback(unsigned long long *st, int64_t g, const Scratch &s) {
+// Warp-cooperative look-back (run by warp 0): lane l inspects tile g-1-l of a
+// window of 32 predecessors; the window moves down until it holds a tile with
+// an inclusive prefix.  first = the chain's first tile, which publishes its
+// inclusive prefix at once, so the walk never leaves the chain.
+__device__ int64_t lb_lookback(unsigned long long *st, int64_t g, int64_t first, const Scratch &s) {
+  const int lane = threadIdx.x & 31;
   int64_t excl = 0;
   int spins = 0;
   for (int64_t p = g - 1;;) {
-    const unsigned long long x = *((volatile unsigned long long *)(st + p));
+    const int64_t idx = p - lane;
+    unsigned long long x = (LB_INC << 62);  // below the chain: inclusive 0
+    if (idx >= first) x = *((volatile unsigned long long *)(st + idx));
     const unsigned long long f = x >> 62;
-    if (f == 0) {
+    const unsigned inc = __ballot_sync(0xffffffffu, f == LB_INC);
+    const unsigned none = __ballot_sync(0xffffffffu, f == 0);
+    const int k = inc ? __ffs(inc) - 1 : 31;  // lanes 0..k are summed
+    if (none & (k == 31 ? 0xffffffffu : ((2u << k) - 1u))) {  // a tile up to lane k not ready
       if (++spins > LB_MAX_SPINS) {
-        atomicOr(s.status, ST_TIMEOUT);
+        if (lane == 0) atomicOr(s.status, ST_TIMEOUT);
         return 0;
       }
       if ((spins & 255) == 0 && halted(s)) return 0;
       __nanosleep(32);
       continue;
     }
-    excl += (int64_t)(x & LB_MASK);
-    if (f == LB_INC) return excl;
-    --p;
+    long long v = (lane <= k) ? (long long)(x & LB_MASK) : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    excl += v;
+    if (inc) return excl;
+    p -= 32;
   }
 }
 
@@ -286,16 +299,20 @@ __global__ void __launch_bounds__(TILE) k_insert(DevChain *__restrict__ ch,
   }
   int64_t tot;
   const int64_t ex = block_excl_scan<int64_t>((int64_t)cnt, sm, tot);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     int64_t excl = 0;
     if (t.y == 0) {
-      lb_publish(s.tile_state, gt, LB_INC, tot);
+      if (threadIdx.x == 0) lb_publish(s.tile_state, gt, LB_INC, tot);
     } else {
-      lb_publish(s.tile_state, gt, LB_AGG, tot);
-      excl = lb_lookback(s.tile_state, gt, s);
-      lb_publish(s.tile_state, gt, LB_INC, excl + tot);
+      if (threadIdx.x == 0) lb_publish(s.tile_state, gt, LB_AGG, tot);
+      __syncwarp();
+      excl = lb_lookback(s.tile_state, gt, gt - t.y, s);
+      if (threadIdx.x == 0) lb_publish(s.tile_state, gt, LB_INC, excl + tot);
     }
-    s_excl = excl;
+    if (threadIdx.x == 0) s_excl = excl;
+  }
+  if (threadIdx.x == 0) {
+    const int64_t excl = s_excl;
     if (t.y == C.ntile - 1) {
       C.n = excl + tot;
       if (excl + tot > C.vcap) atomicOr(s.status, ST_VTX_OVERFLOW);
@@ -659,13 +676,16 @@ __device__ __forceinline__ void open_add(int *keys, unsigned long long *vals, in
     }
     h = (h + 1) & (OPEN_SLOTS - 1);
   }
-  atomicAdd(s.accW + vb + key, (unsigned long long)W);
-  atomicAdd(s.accC + vb + key, (unsigned long long)Cc);
-  atomicAdd(s.accS + vb + key, (unsigned long long)Ss);
+  unsigned long long *r = s.acc + 4 * (vb + key);
+  atomicAdd(r, (unsigned long long)W);
+  atomicAdd(r + 1, (unsigned long long)Cc);
+  atomicAdd(r + 2, (unsigned long long)Ss);
 }
 
+constexpr int TPB_EST = 512;
+
 template <int Q>
-__global__ void __launch_bounds__(TPB) k_est(const DevChain *__restrict__ ch,
+__global__ void __launch_bounds__(TPB_EST) k_est(const DevChain *__restrict__ ch,
                                              const int2 *__restrict__ tab, int64_t blk0,
                                              Scratch s) {
   extern __shared__ unsigned long long est_dyn[];
@@ -759,9 +779,10 @@ __global__ void __launch_bounds__(TPB) k_est(const DevChain *__restrict__ ch,
   for (int h = threadIdx.x; h < OPEN_SLOTS; h += blockDim.x) {
     const int kk = okeys[h];
     if (kk >= 0) {
-      atomicAdd(s.accW + vb + kk, ovals[3 * h]);
-      atomicAdd(s.accC + vb + kk, ovals[3 * h + 1]);
-      atomicAdd(s.accS + vb + kk, ovals[3 * h + 2]);
+      unsigned long long *r = s.acc + 4 * (vb + kk);
+      atomicAdd(r, ovals[3 * h]);
+      atomicAdd(r + 1, ovals[3 * h + 1]);
+      atomicAdd(r + 2, ovals[3 * h + 2]);
     }
   }
   w2 = block_sum_u128(w2);
@@ -801,25 +822,45 @@ __global__ void __launch_bounds__(TPB) k_compact(const DevChain *__restrict__ ch
     }
   }
   const int a = vp[c0], e = vp[c1];
+  // New operators in vertex order: four flags per thread per step (one aligned
+  // 32-bit load), one block scan per 4*TPB vertices.
+  const uint8_t *vf = s.vflag + vb;
   int64_t run = base;
-  for (int w0 = a; w0 < e; w0 += blockDim.x) {
-    const int w = w0 + threadIdx.x;
-    const int f = (w < e) ? ((s.vflag[vb + w] & VF_NEW) ? 1 : 0) : 0;
+  for (int g0 = a & ~3; g0 < e; g0 += 4 * (int)blockDim.x) {
+    const int w0 = g0 + 4 * (int)threadIdx.x;
+    uint32_t fl = 0;
+    if (w0 < e) fl = *(const uint32_t *)(vf + w0);  // vb and w0 are multiples of 4
+    int m = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int w = w0 + i;
+      if (w >= a && w < e && ((fl >> (8 * i)) & VF_NEW)) m |= 1 << i;
+    }
     int64_t tot;
-    const int64_t ex = block_excl_scan<int64_t>((int64_t)f, sm, tot);
-    if (f) ntau[run + ex] = s.vtau[vb + w];
+    const int64_t ex = block_excl_scan<int64_t>((int64_t)__popc(m), sm, tot);
+    int64_t pos = run + ex;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (m & (1 << i)) ntau[pos++] = s.vtau[vb + w0 + i];
     run += tot;
   }
+  // Loops that left their tile: one 32-byte accumulator record per root, read
+  // and cleared; a thread takes one 32-vertex word of the open-root bitmap.
   u128 w2 = 0, f2 = 0;
-  for (int v = a + threadIdx.x; v < e; v += blockDim.x) {
-    if (get_bit(s.openroot, wb, v)) {
-      const long long W = (long long)s.accW[vb + v], Cc = (long long)s.accC[vb + v],
-                      Ss = (long long)s.accS[vb + v];
-      s.accW[vb + v] = 0ull;
-      s.accC[vb + v] = 0ull;
-      s.accS[vb + v] = 0ull;
-      w2 += sq_abs(W);
-      f2 += sq_abs(Cc) + sq_abs(Ss);
+  const int64_t wfirst = (vb + a) >> 5, wlast = (vb + e - 1) >> 5;
+  for (int64_t wd = wfirst + threadIdx.x; e > a && wd <= wlast; wd += blockDim.x) {
+    uint32_t bits = __ldcg(s.openroot + wd);
+    const int64_t v0 = (wd << 5) - vb;
+    if (v0 < a) bits &= ~0u << (a - v0);
+    if (v0 + 32 > e) bits &= (e - v0 >= 32) ? ~0u : ((1u << (e - v0)) - 1u);
+    while (bits) {
+      const int i = __ffs(bits) - 1;
+      bits &= bits - 1;
+      ulonglong4 *r = (ulonglong4 *)(s.acc + 4 * (vb + v0 + i));
+      const ulonglong4 x = *r;
+      *r = make_ulonglong4(0ull, 0ull, 0ull, 0ull);
+      w2 += sq_abs((long long)x.x);
+      f2 += sq_abs((long long)x.y) + sq_abs((long long)x.z);
     }
   }
   w2 = block_sum_u128(w2);
@@ -1000,8 +1041,8 @@ int init_kernel_attributes() {
 }
 
 void launch_est(const Launch &L, cudaStream_t st) {
-  if (L.ntile[0]) k_est<1><<<g1(L.ntile[0]), TPB, EST_DYN_SMEM, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
-  if (L.ntile[1]) k_est<2><<<g1(L.ntile[1]), TPB, EST_DYN_SMEM, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
+  if (L.ntile[0]) k_est<1><<<g1(L.ntile[0]), TPB_EST, EST_DYN_SMEM, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
+  if (L.ntile[1]) k_est<2><<<g1(L.ntile[1]), TPB_EST, EST_DYN_SMEM, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
 }
 
 void launch_compact(const Launch &L, cudaStream_t st) {
