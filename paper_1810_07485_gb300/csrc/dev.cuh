@@ -81,6 +81,7 @@ struct Scratch {
   int8_t *cut_cross, *free_len;
   double *vtau;
   uint8_t *vflag;
+  uint8_t *vcell;  // per vertex: its cell's index inside the tile (0..127)
   int32_t *pl, *pr, *parent;
   unsigned long long *acc;  // per vertex: W, C, S, pad (32-byte record), open loops only
   uint32_t *openmark, *openroot, *flipbits;

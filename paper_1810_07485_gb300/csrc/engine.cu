@@ -149,6 +149,7 @@ void Engine::dfree(void *p) {
 void Engine::free_vertex() {
   dfree(s_.vtau);
   dfree(s_.vflag);
+  dfree(s_.vcell);
   dfree(s_.pl);
   dfree(s_.pr);
   dfree(s_.parent);
@@ -158,6 +159,7 @@ void Engine::free_vertex() {
   dfree(s_.flipbits);
   s_.vtau = nullptr;
   s_.vflag = nullptr;
+  s_.vcell = nullptr;
   s_.pl = s_.pr = s_.parent = nullptr;
   s_.acc = nullptr;
   s_.openmark = s_.openroot = s_.flipbits = nullptr;
@@ -169,6 +171,7 @@ int Engine::alloc_vertex(int64_t vcap) {
   vcap = (vcap + 127) / 128 * 128;
   DALLOC(s_.vtau, double, vcap);
   DALLOC(s_.vflag, uint8_t, vcap);
+  DALLOC(s_.vcell, uint8_t, vcap);
   DALLOC(s_.pl, int32_t, vcap);
   DALLOC(s_.pr, int32_t, vcap);
   DALLOC(s_.parent, int32_t, vcap);
@@ -180,7 +183,7 @@ int Engine::alloc_vertex(int64_t vcap) {
   CK(cudaMemsetAsync(s_.acc, 0, 4 * sizeof(unsigned long long) * vcap, st_));
   s_.vcap = vcap;
   vcap_ = vcap;
-  vertex_bytes_ = (size_t)vcap * (8 + 1 + 12 + 32) + 3 * (size_t)nw * 4;
+  vertex_bytes_ = (size_t)vcap * (8 + 2 + 12 + 32) + 3 * (size_t)nw * 4;
   L_.s = s_;
   if (gexec_) {
     cudaGraphExecDestroy(gexec_);

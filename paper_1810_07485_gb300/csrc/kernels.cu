@@ -342,6 +342,7 @@ __global__ void __launch_bounds__(TILE) k_insert(DevChain *__restrict__ ch,
     }
     vt[r] = tau;
     s.vflag[vb + r] = f;
+    s.vcell[vb + r] = (uint8_t)threadIdx.x;  // cell within the tile
     s.parent[vb + r] = r;
     ++r;
   }
@@ -558,7 +559,7 @@ __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
   int32_t *par = s.parent + vb;
   const int mytile = t.y;
   for (int w = a + threadIdx.x; w < e; w += blockDim.x) {
-    const int ci = tile_cell_of(cvp, ncl, w);
+    const int ci = s.vcell[vb + w];
     const LinkCell<Q> &L = lc[ci];
     const int cell = c0 + ci, v0 = cvp[ci];
     const long long tw = vt[w];
@@ -695,6 +696,7 @@ __global__ void __launch_bounds__(TPB_EST) k_est(const DevChain *__restrict__ ch
   __shared__ int cvp[TILE + 1];
   __shared__ int cnew[TILE];
   __shared__ long long ccl[TILE], csl[TILE], ccr[TILE], csr[TILE], cxl[TILE], cxr[TILE];
+  __shared__ long long wbuf[TPB_EST / 32][32][3];
   __shared__ int64_t sm[33];
   if (halted(s)) return;
   const int64_t gt = blk0 + blockIdx.x;
@@ -730,35 +732,62 @@ __global__ void __launch_bounds__(TPB_EST) k_est(const DevChain *__restrict__ ch
   const int32_t *par = s.parent + vb;
   const uint64_t *vt = (const uint64_t *)s.vtau + vb;
   const int F = C.F;
-  for (int w = a + threadIdx.x; w < e; w += blockDim.x) {
-    const int ci = tile_cell_of(cvp, ncl, w);
-    const int P = s.pl[vb + w], R = s.pr[vb + w];
-    const uint8_t f = s.vflag[vb + w];
-    const int rb = __ldcg(par + P), ra = __ldcg(par + w);
-    const int nf = (f & VF_OLD) ^ get_bit(s.flipbits, wb, rb) ^ get_bit(s.flipbits, wb, ra);
-    s.vflag[vb + w] = (uint8_t)(f | (nf ? VF_NEW : 0));
-    if (nf) atomicAdd(cnew + ci, 1);
-    // fragment lengths in ticks of 2^-F: q(tau_top) - q(tau_bottom) (+ crossings)
-    const long long qw = q_time(vt[w], F);
-    long long dl = qw - q_time(vt[P], F);
-    if (f & VF_WRAP_L) dl += cxl[ci];
-    long long dr = qw - q_time(vt[R], F);
-    if (f & VF_WRAP_R) dr += cxr[ci];
-    const long long W = dl + dr;
-    const long long Cc = mul_q32(dl, ccl[ci]) + mul_q32(dr, ccr[ci]);
-    const long long Ss = mul_q32(dl, csl[ci]) + mul_q32(dr, csr[ci]);
-    if (get_bit(s.openroot, wb, rb)) {
-      open_add(okeys, ovals, rb, W, Cc, Ss, s, vb);
-    } else {
-      const int li = rb - a;
-      if (li < 0 || li >= nv) {
-        fail_check(s, 3, c0 + ci, w, rb, a, ((long long)nv << 32) | (unsigned)P);
+  // Whole warps walk the tile (trip count rounded up) so that the warp-wide
+  // key reduction below has every lane present.
+  const int lane = threadIdx.x & 31;
+  for (int w0 = a; w0 < e; w0 += blockDim.x) {
+    const int w = w0 + threadIdx.x;
+    int key = -1;  // root of the loop the two fragments below w belong to
+    long long W = 0, Cc = 0, Ss = 0;
+    if (w < e) {
+      const int ci = s.vcell[vb + w];
+      const int P = s.pl[vb + w], R = s.pr[vb + w];
+      const uint8_t f = s.vflag[vb + w];
+      const int rb = __ldcg(par + P), ra = __ldcg(par + w);
+      const int nf = (f & VF_OLD) ^ get_bit(s.flipbits, wb, rb) ^ get_bit(s.flipbits, wb, ra);
+      s.vflag[vb + w] = (uint8_t)(f | (nf ? VF_NEW : 0));
+      if (nf) atomicAdd(cnew + ci, 1);
+      // fragment lengths in ticks of 2^-F: q(tau_top) - q(tau_bottom) (+ crossings)
+      const long long qw = q_time(vt[w], F);
+      long long dl = qw - q_time(vt[P], F);
+      if (f & VF_WRAP_L) dl += cxl[ci];
+      long long dr = qw - q_time(vt[R], F);
+      if (f & VF_WRAP_R) dr += cxr[ci];
+      W = dl + dr;
+      Cc = mul_q32(dl, ccl[ci]) + mul_q32(dr, ccr[ci]);
+      Ss = mul_q32(dl, csl[ci]) + mul_q32(dr, csr[ci]);
+      key = rb;
+    }
+    // Lanes holding the same loop root (mostly the giant loop) are summed by
+    // the group's lowest lane from a per-warp buffer; one set of atomics per
+    // distinct root and warp.
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    const int wid = threadIdx.x >> 5;
+    wbuf[wid][lane][0] = W;
+    wbuf[wid][lane][1] = Cc;
+    wbuf[wid][lane][2] = Ss;
+    __syncwarp();
+    if (key >= 0 && lane == __ffs(grp) - 1) {
+      for (unsigned mm = grp & (grp - 1); mm; mm &= mm - 1) {
+        const int j = __ffs(mm) - 1;
+        W += wbuf[wid][j][0];
+        Cc += wbuf[wid][j][1];
+        Ss += wbuf[wid][j][2];
+      }
+      if (get_bit(s.openroot, wb, key)) {
+        open_add(okeys, ovals, key, W, Cc, Ss, s, vb);
       } else {
-        atomicAdd(cW + li, (unsigned long long)W);
-        atomicAdd(cC + li, (unsigned long long)Cc);
-        atomicAdd(cS + li, (unsigned long long)Ss);
+        const int li = key - a;
+        if (li < 0 || li >= nv) {
+          fail_check(s, 3, c0, w, key, a, nv);
+        } else {
+          atomicAdd(cW + li, (unsigned long long)W);
+          atomicAdd(cC + li, (unsigned long long)Cc);
+          atomicAdd(cS + li, (unsigned long long)Ss);
+        }
       }
     }
+    __syncwarp();
   }
   __syncthreads();
   int newcnt = 0;
