@@ -8,6 +8,8 @@ measurement) of a single chain with L = 2^16 sites at beta = 2^12 (about
 paper's graph: fragments + 2 x vertices (Sec. 4.4).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --mode batched [--chains C --updates U]   (many uneven chains)
+  python bench.py --mode served [--requests R --rate Hz]    (request stream)
 
 Under torchrun each rank runs its own chain (seed 1 + rank): independent Markov
 chains, weak scaling, no collective on the data path.  `--impl reference`
@@ -120,6 +122,25 @@ def dist_setup(n_gpus):
     return world, rank, local
 
 
+def chain_seed(rank):
+    """Each rank runs its own independent chain: the seed keys every random
+    number of the update, so distinct seeds give distinct Markov chains."""
+    return 1 + rank
+
+
+def over_ranks(world, elapsed, units, device):
+    """Whole-job figures: the slowest rank's elapsed time (max) and the units
+    processed by all ranks (sum).  With one rank, the inputs unchanged."""
+    import torch
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    v = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(v, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(v.item())
+
+
 def oracle_sample(beta, steps, warmup, L=ORACLE_SAMPLE_L):
     """Times the keyed CPU oracle on L sites at the workload's beta."""
     from oracle import orc
@@ -165,7 +186,7 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     L, beta, therm = WORKLOADS[args.workload]
     stream = torch.cuda.Stream()
-    ch = lcqmc.Chain(L, beta, seed=1 + rank, stream=stream.cuda_stream)
+    ch = lcqmc.Chain(L, beta, seed=chain_seed(rank), stream=stream.cuda_stream)
     geo = ch.geometry()
     # thermalization from the Neel state, then W warm-up updates (untimed)
     ch.update(therm + args.warmup)
@@ -190,13 +211,7 @@ def run_ours(args, world, rank, local):
     ms = e0.elapsed_time(e1)
     recs = ch.records()
     ve_local = float((recs["n_seg"] + 2 * recs["n"]).sum())
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    v = torch.tensor([ve_local], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(v, op=dist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    ve_tot = float(v.item())
+    ms_max, ve_tot = over_ranks(world, ms, ve_local, "cuda")
     value = ve_tot / (ms_max * 1e-3)
 
     # -- end to end through the public API: update + record readback per step --
@@ -209,12 +224,8 @@ def run_ours(args, world, rank, local):
         ve_e2e += float((r["n_seg"] + 2 * r["n"]).sum())
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    ve2 = torch.tensor([ve_e2e], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        dist.all_reduce(ve2, op=dist.ReduceOp.SUM)
-    e2e_value = float(ve2.item()) / float(te.item())
+    e2e_max, ve2_tot = over_ranks(world, e2e_s, ve_e2e, "cuda")
+    e2e_value = ve2_tot / e2e_max
 
     # -- per-phase device times (CUDA events between phases, same stream) -------
     nph = min(10, max(3, args.steps))
@@ -265,6 +276,127 @@ def run_ours(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def _pct(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
+
+
+def run_batched(args):
+    """Many independent uneven chains (L log-uniform in [32, 4096], beta = L U,
+    U log-uniform in [1/4, 4]): batched launches (chains packed per phase,
+    CUDA-graph replay, memory-bounded waves in footprint order) vs the same
+    kernels launched chain by chain.  Per-chain results must be identical."""
+    import torch
+    from paper_1810_07485_gb300 import lcqmc, workloads
+    torch.cuda.set_device(0)
+    specs = workloads.batch_specs(args.chains, seed=0)
+    foot = [lcqmc.footprint(s["L"], s["beta"]) for s in specs]
+    order = sorted(range(len(specs)), key=lambda i: foot[i])
+    budget = args.budget_gb * 1e9
+    waves, cur, used = [], [], 0.0
+    for i in order:
+        if cur and used + foot[i] > budget:
+            waves.append(cur)
+            cur, used = [], 0.0
+        cur.append(i)
+        used += foot[i]
+    if cur:
+        waves.append(cur)
+    lcqmc.Chain(8, 1.0).close()  # context warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done_b, obs_b = {}, {}
+    for wave in waves:
+        bt = lcqmc.Batch([specs[i] for i in wave])
+        bt.update(args.updates)
+        bt.sync()
+        tw = time.perf_counter() - t0
+        for j, i in enumerate(wave):
+            obs_b[i] = bt.measure(j)
+            done_b[i] = tw
+        bt.close()
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    done_1, obs_1 = {}, {}
+    for i in order:
+        s = specs[i]
+        ch = lcqmc.Chain(s["L"], s["beta"], seed=s["seed"])
+        ch.update(args.updates)
+        obs_1[i] = ch.measure()
+        done_1[i] = time.perf_counter() - t0
+        ch.close()
+    t1 = time.perf_counter() - t0
+    same = sum(1 for i in obs_b if list(obs_b[i].sum) == list(obs_1[i].sum) and
+               list(obs_b[i].sumsq) == list(obs_1[i].sumsq))
+    ve = float(sum(o.sum[7] for o in obs_b.values()))
+    line = {
+        "metric": "batched chains: V+E/s and per-chain completion p50/p99 vs one-by-one", "mode": "batched",
+        "value": ve / tb, "unit": "V+E/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": f"{args.chains} S=1/2 chains, L log-uniform [32,4096], beta=L*U, U log-uniform "
+                               f"[1/4,4], seeds 0..{args.chains - 1}, {args.updates} updates each",
+                   "waves": len(waves), "budget_gb": args.budget_gb},
+        "batched": {"seconds": tb, "ve_per_s": ve / tb, "p50_s": _pct(list(done_b.values()), 50),
+                    "p99_s": _pct(list(done_b.values()), 99)},
+        "one_by_one": {"seconds": t1, "ve_per_s": ve / t1, "p50_s": _pct(list(done_1.values()), 50),
+                       "p99_s": _pct(list(done_1.values()), 99)},
+        "speedup": t1 / tb, "identical_results": f"{same}/{len(specs)}",
+    }
+    print(json.dumps(line))
+
+
+def run_served(args):
+    """Poisson stream of requests (S in {1/2, 1}, L log-uniform in [64, 65536],
+    beta = L U, U log-uniform in [1/4, 4], 50 updates + readout each) into the
+    continuous-batching server; bounded by --time-limit."""
+    import torch
+    from paper_1810_07485_gb300 import lcqmc, workloads
+    torch.cuda.set_device(0)
+    stream = workloads.request_stream(args.requests, args.rate, n_updates=args.req_updates, seed=0)
+    srv = lcqmc.Server(int(args.budget_gb * 1e9), args.slots)
+    rejected = {}
+    tickets = {}
+    t0 = time.perf_counter()
+    for k, (ta, s) in enumerate(stream):
+        dt = t0 + ta - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        try:
+            tickets[k] = srv.submit(s["L"], s["beta"], s["n_updates"], S=s["S"], seed=s["seed"])
+        except lcqmc.LcqmcError as e:
+            rejected[k] = e.code
+    res = {}
+    while time.perf_counter() - t0 < args.time_limit and len(res) < len(tickets):
+        for k, t in tickets.items():
+            if k not in res:
+                r = srv.poll(t)
+                if r is not None:
+                    res[k] = (r.status, r.t_done - r.t_submit, r.t_admit - r.t_submit, r.vertices_edges, r.t_done)
+        time.sleep(0.01)
+    wall = time.perf_counter() - t0
+    srv.close()
+    done = {k: v for k, v in res.items() if v[0] == 0}
+    lat = [v[1] for v in done.values()]
+    ve = float(sum(v[3] for v in done.values()))
+    last = max((v[4] for v in done.values()), default=wall)
+    rej_s = {0.5: 0, 1.0: 0}
+    for k in rejected:
+        rej_s[stream[k][1]["S"]] += 1
+    line = {
+        "metric": "served requests: latency p50/p99 and V+E/s", "mode": "served", "value": ve / last,
+        "unit": "V+E/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": f"{args.requests} requests, Poisson {args.rate}/s, S in {{1/2,1}}, L log-uniform "
+                               f"[64,65536], beta=L*U, U log-uniform [1/4,4], {args.req_updates} updates each",
+                   "hbm_budget_gb": args.budget_gb, "slots": args.slots, "time_limit_s": args.time_limit},
+        "submitted": len(stream), "rejected_at_admission": len(rejected),
+        "rejected_fraction": {"S=1/2": rej_s[0.5] / max(1, sum(1 for _, s in stream if s["S"] == 0.5)),
+                              "S=1": rej_s[1.0] / max(1, sum(1 for _, s in stream if s["S"] == 1.0))},
+        "completed": len(done), "unfinished_at_limit": len(tickets) - len(res),
+        "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
+        "queue_wait_p50_s": _pct([v[2] for v in done.values()], 50), "wall_s": wall,
+    }
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -272,8 +404,23 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default="single", choices=["single", "batched", "served"])
+    ap.add_argument("--chains", type=int, default=512)
+    ap.add_argument("--updates", type=int, default=20)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--requests", type=int, default=400)
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--req-updates", type=int, default=50)
+    ap.add_argument("--slots", type=int, default=512)
+    ap.add_argument("--time-limit", type=float, default=90.0)
     args = ap.parse_args()
     world, rank, local = dist_setup(args.gpus)
+    if args.mode == "batched":
+        run_batched(args)
+        return
+    if args.mode == "served":
+        run_served(args)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:
