@@ -172,7 +172,7 @@ def run_reference(args, world, rank):
                          "sample": f"keyed oracle, L={ORACLE_SAMPLE_L}, beta={beta:g}, {steps} updates after {warm}"},
         "e2e": {"value": value, "unit": "V+E/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line))
+    print(json.dumps(line), flush=True)
 
 
 def run_ours(args, world, rank, local):
@@ -270,10 +270,14 @@ def run_ours(args, world, rank, local):
         "clocks": clocks,
     }
     if rank == 0:
-        print(json.dumps(line))
+        print(json.dumps(line), flush=True)
     ch.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def log(msg):
+    print(msg, file=sys.stderr, flush=True)
 
 
 def _pct(xs, q):
@@ -341,17 +345,18 @@ def run_batched(args):
                        "p99_s": _pct(list(done_1.values()), 99)},
         "speedup": t1 / tb, "identical_results": f"{same}/{len(specs)}",
     }
-    print(json.dumps(line))
+    print(json.dumps(line), flush=True)
 
 
 def run_served(args):
-    """Poisson stream of requests (S in {1/2, 1}, L log-uniform in [64, 65536],
+    """Poisson stream of requests (S in {1/2, 1}, L log-uniform in [64, L_max],
     beta = L U, U log-uniform in [1/4, 4], 50 updates + readout each) into the
-    continuous-batching server; bounded by --time-limit."""
+    continuous-batching server; polling bounded by --time-limit."""
     import torch
     from paper_1810_07485_gb300 import lcqmc, workloads
     torch.cuda.set_device(0)
-    stream = workloads.request_stream(args.requests, args.rate, n_updates=args.req_updates, seed=0)
+    stream = workloads.request_stream(args.requests, args.rate, L_max=args.req_lmax,
+                                      n_updates=args.req_updates, seed=0)
     srv = lcqmc.Server(int(args.budget_gb * 1e9), args.slots)
     rejected = {}
     tickets = {}
@@ -364,16 +369,23 @@ def run_served(args):
             tickets[k] = srv.submit(s["L"], s["beta"], s["n_updates"], S=s["S"], seed=s["seed"])
         except lcqmc.LcqmcError as e:
             rejected[k] = e.code
+    log(f"served: {len(tickets)} submitted, {len(rejected)} rejected at submission")
     res = {}
+    t_log = time.perf_counter()
     while time.perf_counter() - t0 < args.time_limit and len(res) < len(tickets):
         for k, t in tickets.items():
             if k not in res:
                 r = srv.poll(t)
                 if r is not None:
                     res[k] = (r.status, r.t_done - r.t_submit, r.t_admit - r.t_submit, r.vertices_edges, r.t_done)
+        if time.perf_counter() - t_log > 5.0:
+            t_log = time.perf_counter()
+            log(f"served: t={t_log - t0:.1f}s finished {len(res)}/{len(tickets)}")
         time.sleep(0.01)
     wall = time.perf_counter() - t0
+    log(f"served: polling ended at t={wall:.1f}s, finished {len(res)}/{len(tickets)}; stopping the server")
     srv.close()
+    log(f"served: server stopped at t={time.perf_counter() - t0:.1f}s")
     done = {k: v for k, v in res.items() if v[0] == 0}
     lat = [v[1] for v in done.values()]
     ve = float(sum(v[3] for v in done.values()))
@@ -385,7 +397,7 @@ def run_served(args):
         "metric": "served requests: latency p50/p99 and V+E/s", "mode": "served", "value": ve / last,
         "unit": "V+E/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
         "config": {"workload": f"{args.requests} requests, Poisson {args.rate}/s, S in {{1/2,1}}, L log-uniform "
-                               f"[64,65536], beta=L*U, U log-uniform [1/4,4], {args.req_updates} updates each",
+                               f"[64,{args.req_lmax}], beta=L*U, U log-uniform [1/4,4], {args.req_updates} updates each",
                    "hbm_budget_gb": args.budget_gb, "slots": args.slots, "time_limit_s": args.time_limit},
         "submitted": len(stream), "rejected_at_admission": len(rejected),
         "rejected_fraction": {"S=1/2": rej_s[0.5] / max(1, sum(1 for _, s in stream if s["S"] == 0.5)),
@@ -394,7 +406,7 @@ def run_served(args):
         "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
         "queue_wait_p50_s": _pct([v[2] for v in done.values()], 50), "wall_s": wall,
     }
-    print(json.dumps(line))
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -408,11 +420,12 @@ def main():
     ap.add_argument("--chains", type=int, default=512)
     ap.add_argument("--updates", type=int, default=20)
     ap.add_argument("--budget-gb", type=float, default=150.0)
-    ap.add_argument("--requests", type=int, default=400)
-    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=10.0)
+    ap.add_argument("--req-lmax", type=int, default=4096)
     ap.add_argument("--req-updates", type=int, default=50)
     ap.add_argument("--slots", type=int, default=512)
-    ap.add_argument("--time-limit", type=float, default=90.0)
+    ap.add_argument("--time-limit", type=float, default=60.0)
     args = ap.parse_args()
     world, rank, local = dist_setup(args.gpus)
     if args.mode == "batched":

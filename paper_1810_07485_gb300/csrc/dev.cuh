@@ -84,7 +84,7 @@ struct Scratch {
   uint8_t *vcell;  // per vertex: its cell's index inside the tile (0..127)
   int32_t *pl, *pr, *parent;
   unsigned long long *acc;  // per vertex: W, C, S, pad (32-byte record), open loops only
-  uint32_t *openmark, *openroot, *flipbits;
+  uint32_t *openmark, *openroot, *flipbits, *xmark;
   int64_t vcap;
   unsigned long long *tile_state;  // per tile: insertion look-back word (flag << 62 | count)
   unsigned int *tickets;           // per Q group: next tile of the insertion launch

@@ -112,7 +112,7 @@ size_t Engine::estimate_footprint(const std::vector<ChainSpec> &specs, int ring_
              14 * g.nsub + sizeof(DevChain) + 8 * (g.ntile + g.nsiteblk + g.nbondblk);
     vc += (vertex_estimate(c) + 127) / 128 * 128;
   }
-  bytes += (size_t)vc * (8 + 1 + 12 + 24) + 3 * (size_t)(vc / 32 + 1) * 4;
+  bytes += (size_t)vc * (8 + 2 + 12 + 32) + 4 * (size_t)(vc / 32 + 1) * 4;
   return bytes;
 }
 
@@ -157,12 +157,13 @@ void Engine::free_vertex() {
   dfree(s_.openmark);
   dfree(s_.openroot);
   dfree(s_.flipbits);
+  dfree(s_.xmark);
   s_.vtau = nullptr;
   s_.vflag = nullptr;
   s_.vcell = nullptr;
   s_.pl = s_.pr = s_.parent = nullptr;
   s_.acc = nullptr;
-  s_.openmark = s_.openroot = s_.flipbits = nullptr;
+  s_.openmark = s_.openroot = s_.flipbits = s_.xmark = nullptr;
   vertex_bytes_ = 0;
 }
 
@@ -180,10 +181,11 @@ int Engine::alloc_vertex(int64_t vcap) {
   DALLOC(s_.openmark, uint32_t, nw);
   DALLOC(s_.openroot, uint32_t, nw);
   DALLOC(s_.flipbits, uint32_t, nw);
+  DALLOC(s_.xmark, uint32_t, nw);
   CK(cudaMemsetAsync(s_.acc, 0, 4 * sizeof(unsigned long long) * vcap, st_));
   s_.vcap = vcap;
   vcap_ = vcap;
-  vertex_bytes_ = (size_t)vcap * (8 + 2 + 12 + 32) + 3 * (size_t)nw * 4;
+  vertex_bytes_ = (size_t)vcap * (8 + 2 + 12 + 32) + 4 * (size_t)nw * 4;
   L_.s = s_;
   if (gexec_) {
     cudaGraphExecDestroy(gexec_);
@@ -531,6 +533,7 @@ int Engine::enqueue_one(bool timed, int slot) {
   CK(cudaMemsetAsync(s_.openmark, 0, 4 * nw, st_));
   CK(cudaMemsetAsync(s_.openroot, 0, 4 * nw, st_));
   CK(cudaMemsetAsync(s_.flipbits, 0, 4 * nw, st_));
+  CK(cudaMemsetAsync(s_.xmark, 0, 4 * nw, st_));
   launch_insert(L_, st_);
   mark(1);  // [1] tau = 0 cut
   launch_cut(L_, st_);

@@ -161,19 +161,6 @@ __device__ __forceinline__ int nb_parity(const NbOps<Q> &X, const long long *__r
   return p;
 }
 
-// Candidate k of the cell: 53 uniform bits.  Call 0 of the cell's Philox stream
-// gives the count (words x, y) and candidate 0 (z, w); call m >= 1 gives
-// candidates 2m-1 (x, y) and 2m (z, w).
-__device__ __forceinline__ uint64_t cand_bits(int k, const U4 &o0, U4 &o2, uint32_t b, uint32_t j,
-                                              uint32_t sweep, uint32_t k0, uint32_t k1) {
-  if (k == 0) return ((uint64_t)o0.z | ((uint64_t)o0.w << 32)) >> 11;
-  if (k & 1) {
-    o2 = philox((TAG_INSERT << 24) | (uint32_t)((k + 1) >> 1), b, j, sweep, k0, k1);
-    return ((uint64_t)o2.x | ((uint64_t)o2.y << 32)) >> 11;
-  }
-  return ((uint64_t)o2.z | ((uint64_t)o2.w << 32)) >> 11;
-}
-
 // Single pass: every tile counts its cells' vertices, publishes the count, and
 // gets the chain-local offset of its first vertex by decoupled look-back over
 // the tiles before it (tile order = order in which blocks took their ticket,
@@ -221,19 +208,151 @@ __device__ int64_t lb_lookback(unsigned long long *st, int64_t g, int64_t first,
   }
 }
 
+// Candidate-parallel insertion.  A tile's cells first set up in shared memory
+// (count K of Poisson candidates, parity at the window start, neighbour
+// operator ranges); then the tile's Philox calls are spread over all threads
+// (call 0 of a cell gives K and candidate 0, call m >= 1 candidates 2m-1 and
+// 2m), each candidate's time is formed and the antiparallel test taken; the
+// kept candidates' places inside their cell follow from ranks: among the
+// cell's kept candidates by (u53, draw index), and against its old operators
+// by time (an old operator goes first on a tie).  Every vertex is then written
+// by its own thread (time, flag, cell; the parent forest is set by the linking
+// kernels).  Candidates are staged INS_CAP at a time: a tile whose
+// candidates exceed that (the mean is 8 * TILE) runs its cells in groups,
+// counting in a first pass and drawing again in the writing pass.
+constexpr int INS_CAP = 1536;
+constexpr int INS_SPAN = INS_CAP - KMAX;  // a group's cells start within INS_SPAN slots
+constexpr int INS_UCAP = INS_CAP / 2 + TILE;
+constexpr int INS_MAXG = (TILE * (KMAX - 1)) / INS_SPAN + 2;
+
+template <int Q>
+struct InsSmem {
+  unsigned long long u53[INS_CAP];
+  long long tau[INS_CAP];  // -1: candidate not kept
+  uint8_t scell[INS_CAP];  // slot -> cell in tile
+  uint8_t ucell[INS_UCAP];  // Philox call -> cell in tile
+  NbOps<Q> X[TILE];
+  int kpre[TILE + 1], upre[TILE + 1], q[TILE + 1];
+  int K[TILE], nk[TILE], cex[TILE], b[TILE], j[TILE];
+  uint8_t par0[TILE];
+  int gfirst[INS_MAXG + 1];
+  int G;
+  int sm[33];
+  int64_t excl;
+  int64_t gt;
+};
+
+template <int Q>
+__device__ __forceinline__ void ins_decide(const DevChain &C, InsSmem<Q> &S, const long long *otau,
+                                           int c, int slot, uint64_t u53, uint64_t t0b,
+                                           uint64_t teb, uint64_t db, bool count) {
+  const long long tau = (long long)tau_fma_bits(db, t0b, u53);
+  bool keep = tau < (long long)teb;
+  if (keep) keep = (S.par0[c] ^ nb_parity<Q>(S.X[c], otau, tau, S.b[c])) & 1;
+  S.u53[slot] = u53;
+  S.tau[slot] = keep ? tau : -1;
+  S.scell[slot] = (uint8_t)c;
+  if (count && keep) atomicAdd(&S.nk[c], 1);
+}
+
+// Draw and decide the candidates of the cells of group g.
+template <int Q>
+__device__ void ins_draw(const DevChain &C, InsSmem<Q> &S, const long long *otau, int g, bool count) {
+  const int c0 = S.gfirst[g], c1 = S.gfirst[g + 1];
+  const int kb = S.kpre[c0], ub = S.upre[c0], nu = S.upre[c1] - ub;
+  {
+    const int c = threadIdx.x;
+    if (c >= c0 && c < c1)
+      for (int u = S.upre[c], e = S.upre[c + 1]; u < e; ++u) S.ucell[u - ub] = (uint8_t)c;
+  }
+  __syncthreads();
+  const uint32_t k0 = (uint32_t)C.seed, k1 = (uint32_t)(C.seed >> 32);
+  for (int u = threadIdx.x; u < nu; u += TILE) {
+    const int c = S.ucell[u];
+    const int m = u + ub - S.upre[c];
+    const int b = S.b[c], j = S.j[c], K = S.K[c], ks = S.kpre[c] - kb;
+    const uint64_t t0b = C.win[3 * j], teb = C.win[3 * j + 1], db = C.win[3 * j + 2];
+    const U4 o = philox((TAG_INSERT << 24) | (uint32_t)m, (uint32_t)b, (uint32_t)j, C.sweep, k0, k1);
+    const uint64_t lo = ((uint64_t)o.x | ((uint64_t)o.y << 32)) >> 11;
+    const uint64_t hi = ((uint64_t)o.z | ((uint64_t)o.w << 32)) >> 11;
+    if (m == 0) {
+      ins_decide<Q>(C, S, otau, c, ks, hi, t0b, teb, db, count);
+    } else {
+      ins_decide<Q>(C, S, otau, c, ks + 2 * m - 1, lo, t0b, teb, db, count);
+      if (2 * m < K) ins_decide<Q>(C, S, otau, c, ks + 2 * m, hi, t0b, teb, db, count);
+    }
+  }
+  __syncthreads();
+}
+
+// Place and write the vertices of the cells of group g (kept candidates, then
+// old operators); vertex ids are chain-local, base = the tile's first id.
+template <int Q>
+__device__ void ins_write(const DevChain &C, InsSmem<Q> &S, const long long *otau, int g,
+                          int64_t base, const Scratch &s) {
+  const int c0 = S.gfirst[g], c1 = S.gfirst[g + 1];
+  const int kb = S.kpre[c0], ns = S.kpre[c1] - kb;
+  const int64_t vb = C.vtx_base;
+  long long *vt = (long long *)s.vtau + vb;
+  uint8_t *vf = s.vflag + vb, *vc = s.vcell + vb;
+  for (int i = threadIdx.x; i < ns; i += TILE) {
+    const long long tau = S.tau[i];
+    if (tau < 0) continue;
+    const int c = S.scell[i];
+    const int ks = S.kpre[c] - kb, K = S.K[c], k = i - ks;
+    const unsigned long long u = S.u53[i];
+    int r = 0;
+    for (int x = 0; x < K; ++x) {
+      const unsigned long long u2 = S.u53[ks + x];
+      r += (S.tau[ks + x] >= 0) & ((u2 < u) | ((u2 == u) & (x < k)));
+    }
+    for (int q = S.q[c], e = S.q[c + 1]; q < e; ++q) {
+      if (otau[q] > tau) break;
+      ++r;
+    }
+    const int64_t pos = base + S.cex[c] + r;
+    vt[pos] = tau;
+    vf[pos] = 0;
+    vc[pos] = (uint8_t)c;
+  }
+  const int qa = S.q[c0], qb = S.q[c1];
+  for (int q = qa + threadIdx.x; q < qb; q += TILE) {
+    int lo = c0, hi = c1 - 1;  // largest c in [c0, c1) with S.q[c] <= q
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (S.q[mid] <= q)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const int c = lo;
+    const long long ot = otau[q];
+    const int ks = S.kpre[c] - kb, K = S.K[c];
+    int r = q - S.q[c];
+    for (int x = 0; x < K; ++x) {
+      const long long t2 = S.tau[ks + x];
+      r += (t2 >= 0) & (t2 < ot);
+    }
+    const int64_t pos = base + S.cex[c] + r;
+    vt[pos] = ot;
+    vf[pos] = VF_OLD;
+    vc[pos] = (uint8_t)c;
+  }
+}
+
 template <int Q>
 __global__ void __launch_bounds__(TILE) k_insert(DevChain *__restrict__ ch,
                                                  const int2 *__restrict__ tab, int64_t blk0,
                                                  int group, Scratch s) {
-  __shared__ int64_t sm[33];
-  __shared__ int64_t s_gt, s_excl;
+  __shared__ InsSmem<Q> S;
   if (halted(s)) return;
-  if (threadIdx.x == 0) s_gt = blk0 + (int64_t)atomicAdd(s.tickets + group, 1u);
+  if (threadIdx.x == 0) S.gt = blk0 + (int64_t)atomicAdd(s.tickets + group, 1u);
   __syncthreads();
-  const int64_t gt = s_gt;
+  const int64_t gt = S.gt;
   const int2 t = tab[gt];
   DevChain &C = ch[t.x];
-  const int cell = t.y * TILE + threadIdx.x;
+  const int c = threadIdx.x;
+  const int cell = t.y * TILE + c;
   const bool valid = cell < C.ncell;
   const int cur = C.cur;
   const int32_t *op = C.op_ptr[cur];
@@ -241,9 +360,8 @@ __global__ void __launch_bounds__(TILE) k_insert(DevChain *__restrict__ ch,
   const uint8_t *s0 = C.s0[cur];
   int32_t *vp = s.vptr + C.cell_off;
 
-  uint64_t cu[KMAX];
-  long long ct[KMAX];
-  int nk = 0, cnt = 0, q0 = 0, q1 = 0;
+  // -- per-cell setup --------------------------------------------------------
+  int K = 0, P = 0, q0 = 0, q1 = 0;
   if (valid) {
     int b, j;
     cell_bj(C, cell, b, j);
@@ -268,83 +386,85 @@ __global__ void __launch_bounds__(TILE) k_insert(DevChain *__restrict__ ch,
         ++k;
       }
     }
+    S.X[c] = X;
+    S.par0[c] = (uint8_t)par0;
+    S.b[c] = b;
+    S.j[c] = j;
     q0 = op[cell];
     q1 = op[cell + 1];
-    const uint64_t t0b = C.win[3 * j], teb = C.win[3 * j + 1], db = C.win[3 * j + 2];
-    const uint32_t k0 = (uint32_t)C.seed, k1 = (uint32_t)(C.seed >> 32);
-    const U4 o0 = philox(TAG_INSERT << 24, (uint32_t)b, (uint32_t)j, C.sweep, k0, k1);
+    const uint64_t db = C.win[3 * j + 2];
+    const U4 o0 = philox(TAG_INSERT << 24, (uint32_t)b, (uint32_t)j, C.sweep, (uint32_t)C.seed,
+                         (uint32_t)(C.seed >> 32));
     const uint64_t U = (uint64_t)o0.x | ((uint64_t)o0.y << 32);
     const uint64_t *T = (j == C.nwin - 1) ? C.T_last : c_T_full;
-    int K = 0;
     while (K < KMAX - 1 && U >= T[K]) ++K;
     if ((long long)db <= 0) K = 0;  // empty last window
-    U4 o2 = {0, 0, 0, 0};
-    for (int kk = 0; kk < K; ++kk) {
-      const uint64_t u53 = cand_bits(kk, o0, o2, (uint32_t)b, (uint32_t)j, C.sweep, k0, k1);
-      const long long tau = (long long)tau_fma_bits(db, t0b, u53);
-      if (!(tau < (long long)teb)) continue;
-      if (!((par0 ^ nb_parity<Q>(X, otau, tau, b)) & 1)) continue;
-      // insertion sort by u53 (stable: equal keys keep draw order)
-      int p = nk;
-      while (p > 0 && cu[p - 1] > u53) {
-        cu[p] = cu[p - 1];
-        ct[p] = ct[p - 1];
-        --p;
-      }
-      cu[p] = u53;
-      ct[p] = tau;
-      ++nk;
-    }
-    cnt = (q1 - q0) + nk;
+    P = K ? K / 2 + 1 : 0;
   }
-  int64_t tot;
-  const int64_t ex = block_excl_scan<int64_t>((int64_t)cnt, sm, tot);
-  if (threadIdx.x < 32) {
-    int64_t excl = 0;
-    if (t.y == 0) {
-      if (threadIdx.x == 0) lb_publish(s.tile_state, gt, LB_INC, tot);
-    } else {
-      if (threadIdx.x == 0) lb_publish(s.tile_state, gt, LB_AGG, tot);
-      __syncwarp();
-      excl = lb_lookback(s.tile_state, gt, gt - t.y, s);
-      if (threadIdx.x == 0) lb_publish(s.tile_state, gt, LB_INC, excl + tot);
-    }
-    if (threadIdx.x == 0) s_excl = excl;
+  if (!valid) q0 = q1 = op[C.ncell];  // cells past the chain's end: empty ranges
+  S.K[c] = K;
+  S.nk[c] = 0;
+  S.q[c] = q0;
+  if (c == TILE - 1) S.q[TILE] = q1;
+  int tot;
+  const int ex = block_excl_scan<int>(K | (P << 16), S.sm, tot);
+  S.kpre[c] = ex & 0xffff;
+  S.upre[c] = ex >> 16;
+  if (c == TILE - 1) {
+    S.kpre[TILE] = tot & 0xffff;
+    S.upre[TILE] = tot >> 16;
   }
-  if (threadIdx.x == 0) {
-    const int64_t excl = s_excl;
-    if (t.y == C.ntile - 1) {
-      C.n = excl + tot;
-      if (excl + tot > C.vcap) atomicOr(s.status, ST_VTX_OVERFLOW);
-      if (excl + tot > (int64_t)0x7fffff00) atomicOr(s.status, ST_ID_OVERFLOW);
+  __syncthreads();
+  {
+    const int gc = S.kpre[c] / INS_SPAN;
+    if (c == 0 || gc != S.kpre[c - 1] / INS_SPAN) S.gfirst[gc] = c;
+    if (c == TILE - 1) {
+      S.G = gc + 1;
+      S.gfirst[gc + 1] = TILE;
     }
   }
   __syncthreads();
-  if (!valid) return;
-  const int64_t off64 = s_excl + ex;
-  if (off64 + cnt > C.vcap) return;  // overflow: the host grows the chain and replays
-  const int32_t off = (int32_t)off64;
-  vp[cell] = off;
-  if (cell == C.ncell - 1) vp[C.ncell] = off + cnt;
-  if (cnt == 0) return;
-  const int64_t vb = C.vtx_base;
-  long long *vt = (long long *)s.vtau + vb;
-  int q = q0, ki = 0, r = off;
-  while (q < q1 || ki < nk) {
-    long long tau;
-    uint8_t f;
-    if (q < q1 && (ki >= nk || otau[q] <= ct[ki])) {
-      tau = otau[q++];
-      f = VF_OLD;
+  const int G = S.G;
+
+  // -- draw, decide and count ------------------------------------------------
+  for (int g = 0; g < G; ++g) ins_draw<Q>(C, S, otau, g, true);
+  const int cnt = valid ? (q1 - q0) + S.nk[c] : 0;
+  int ctot;
+  S.cex[c] = block_excl_scan<int>(cnt, S.sm, ctot);
+
+  // -- chain-local offset of the tile: decoupled look-back --------------------
+  if (threadIdx.x < 32) {
+    int64_t excl = 0;
+    if (t.y == 0) {
+      if (threadIdx.x == 0) lb_publish(s.tile_state, gt, LB_INC, ctot);
     } else {
-      tau = ct[ki++];
-      f = 0;
+      if (threadIdx.x == 0) lb_publish(s.tile_state, gt, LB_AGG, ctot);
+      __syncwarp();
+      excl = lb_lookback(s.tile_state, gt, gt - t.y, s);
+      if (threadIdx.x == 0) lb_publish(s.tile_state, gt, LB_INC, excl + ctot);
     }
-    vt[r] = tau;
-    s.vflag[vb + r] = f;
-    s.vcell[vb + r] = (uint8_t)threadIdx.x;  // cell within the tile
-    s.parent[vb + r] = r;
-    ++r;
+    if (threadIdx.x == 0) {
+      S.excl = excl;
+      if (t.y == C.ntile - 1) {
+        C.n = excl + ctot;
+        if (excl + ctot > C.vcap) atomicOr(s.status, ST_VTX_OVERFLOW);
+        if (excl + ctot > (int64_t)0x7fffff00) atomicOr(s.status, ST_ID_OVERFLOW);
+      }
+    }
+  }
+  __syncthreads();
+  const int64_t base = S.excl;
+  if (base + ctot > C.vcap) return;  // overflow: the host grows the chain and replays
+  if (valid) {
+    vp[cell] = (int32_t)(base + S.cex[c]);
+    if (cell == C.ncell - 1) vp[C.ncell] = (int32_t)(base + S.cex[c] + cnt);
+  }
+
+  // -- write -----------------------------------------------------------------
+  for (int g = 0; g < G; ++g) {
+    if (G > 1) ins_draw<Q>(C, S, otau, g, false);
+    ins_write<Q>(C, S, otau, g, base, s);
+    __syncthreads();
   }
 }
 
@@ -479,28 +599,52 @@ __global__ void __launch_bounds__(SITE_BLOCK) k_cut(const DevChain *__restrict__
 }
 
 // ---- linking + union-find -----------------------------------------------------
-__device__ __forceinline__ void before_window(const DevChain &C, const int32_t *vp, int bond,
-                                              int j, int &id, int &cellc) {
-  id = -1;
-  cellc = -1;
+__device__ __forceinline__ int before_window(const DevChain &C, const int32_t *vp, int bond, int j) {
   for (int jj = j - 1; jj >= 0; --jj) {
     const int c = cell_of(C, bond, jj);
     const int a = vp[c], e = vp[c + 1];
-    if (e > a) {
-      id = e - 1;
-      cellc = c;
-      return;
-    }
+    if (e > a) return e - 1;
   }
+  return -1;
 }
 
 // Per-cell linking context, staged in shared memory by one thread per cell.
 template <int Q>
 struct LinkCell {
   static constexpr int NO = 2 * Q - 1;  // other bonds touching each of the two subsites
-  int wa[2][NO], we[2][NO], wc[2][NO], bj[2][NO], bjc[2][NO];
-  int own_bj, own_bjc, cut[2], cutc[2];
+  int wa[2][NO], we[2][NO], bj[2][NO];
+  int own_bj, cut[2];
 };
+
+// Union-find of one tile's nodes in shared memory (local ids), with the same
+// min-root rule as the global one: lp[x] <= x; a link is one CAS on the larger
+// root.  Walks are bounded by the tile's node count.
+__device__ __forceinline__ int suf_find(volatile int *lp, int x, int bound, int *status) {
+  for (int it = 0; it <= bound; ++it) {
+    const int p = lp[x];
+    if (p == x) return x;
+    const int g = lp[p];
+    if (g != p) lp[x] = g;  // path halving (g is an ancestor of x)
+    x = g;
+  }
+  atomicOr(status, ST_TIMEOUT);
+  return x;
+}
+
+__device__ __forceinline__ void suf_union(int *lp, int a, int b, int bound, int *status) {
+  for (int it = 0; it <= bound; ++it) {
+    a = suf_find(lp, a, bound, status);
+    b = suf_find(lp, b, bound, status);
+    if (a == b) return;
+    if (a > b) {
+      const int t = a;
+      a = b;
+      b = t;
+    }
+    if (atomicCAS(lp + b, b, a) == b) return;
+  }
+  atomicOr(status, ST_TIMEOUT);
+}
 
 // First index q in [lo, hi) whose key (tau, id) is not below (tw, w).
 __device__ __forceinline__ int key_lower_bound(const long long *vt, int lo, int hi, long long tw,
@@ -516,12 +660,19 @@ __device__ __forceinline__ int key_lower_bound(const long long *vt, int lo, int 
   return lo;
 }
 
+// Linking, then the union of the two fragments below every vertex.  Edges
+// with both nodes in the tile are united in shared memory, and the tile's
+// forest is then stored as each node's local root; edges that leave the tile
+// are marked and united in the global forest by k_link_x, after every tile has
+// stored its forest (a tile too large for shared memory leaves all of its
+// edges to k_link_x, with every node its own root).
 template <int Q>
 __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
                                               const int2 *__restrict__ tab, int64_t blk0,
                                               Scratch s) {
   __shared__ LinkCell<Q> lc[TILE];
   __shared__ int cvp[TILE + 1];
+  __shared__ int lp[SMEM_CAP];
   if (halted(s)) return;
   const int2 t = tab[blk0 + blockIdx.x];
   const DevChain &C = ch[t.x];
@@ -543,80 +694,97 @@ __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
         const int cj = cell_of(C, bb, j);
         L.wa[sd][k] = vp[cj];
         L.we[sd][k] = vp[cj + 1];
-        L.wc[sd][k] = cj;
-        before_window(C, vp, bb, j, L.bj[sd][k], L.bjc[sd][k]);
+        L.bj[sd][k] = before_window(C, vp, bb, j);
         ++k;
       }
       L.cut[sd] = s.cut_node[C.sub_off + sub[sd]];
-      L.cutc[sd] = s.cut_cell[C.sub_off + sub[sd]];
     }
-    before_window(C, vp, b, j, L.own_bj, L.own_bjc);
+    L.own_bj = before_window(C, vp, b, j);
   }
   __syncthreads();
-  const int a = cvp[0], e = cvp[ncl];
+  const int a = cvp[0], e = cvp[ncl], nv = e - a;
+  const bool local = nv <= SMEM_CAP;
+  if (local)
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) lp[i] = i;
+  __syncthreads();
   const int64_t vb = C.vtx_base, wb = vb >> 5;
   const long long *__restrict__ vt = (const long long *)s.vtau + vb;
   int32_t *par = s.parent + vb;
-  const int mytile = t.y;
   for (int w = a + threadIdx.x; w < e; w += blockDim.x) {
     const int ci = s.vcell[vb + w];
     const LinkCell<Q> &L = lc[ci];
-    const int cell = c0 + ci, v0 = cvp[ci];
+    const int v0 = cvp[ci];
     const long long tw = vt[w];
-    int P[2], Pc[2];
+    int P[2];
     uint8_t wrapbits = 0;
 #pragma unroll
     for (int sd = 0; sd < 2; ++sd) {
-      int best = -1, bestc = -1;
+      int best = -1;
       long long bt = 0;
       if (w > v0) {
         best = w - 1;
-        bestc = cell;
         bt = vt[w - 1];
       } else if (L.own_bj >= 0) {
         best = L.own_bj;
-        bestc = L.own_bjc;
         bt = vt[best];
       }
 #pragma unroll
       for (int k = 0; k < LinkCell<Q>::NO; ++k) {
         const int q = key_lower_bound(vt, L.wa[sd][k], L.we[sd][k], tw, w);
-        int cand, candc;
-        if (q > L.wa[sd][k]) {
-          cand = q - 1;
-          candc = L.wc[sd][k];
-        } else {
-          cand = L.bj[sd][k];
-          candc = L.bjc[sd][k];
-        }
+        const int cand = (q > L.wa[sd][k]) ? q - 1 : L.bj[sd][k];
         if (cand >= 0) {
           const long long tc = vt[cand];
           if (best < 0 || tc > bt || (tc == bt && cand > best)) {
             best = cand;
             bt = tc;
-            bestc = candc;
           }
         }
       }
       if (best < 0) {
         best = L.cut[sd];
-        bestc = L.cutc[sd];
         wrapbits |= sd ? VF_WRAP_R : VF_WRAP_L;
         if (best < 0) {
-          fail_check(s, 2, cell, w, sd, 0, 0);
+          fail_check(s, 2, c0 + ci, w, sd, 0, 0);
           best = w;
-          bestc = cell;
         }
       }
       P[sd] = best;
-      Pc[sd] = bestc;
     }
     s.pl[vb + w] = P[0];
     s.pr[vb + w] = P[1];
     if (wrapbits) s.vflag[vb + w] |= wrapbits;
-    if (Pc[0] / TILE != mytile || Pc[1] / TILE != mytile) set_bit(s.openmark, wb, P[0]);
-    uf_union(par, P[0], P[1], s.status);
+    const bool inside = P[0] >= a && P[0] < e && P[1] >= a && P[1] < e;
+    if (!inside) {
+      set_bit(s.openmark, wb, P[0]);
+      if (local) set_bit(s.xmark, wb, w);
+    } else if (local) {
+      suf_union(lp, P[0] - a, P[1] - a, nv, s.status);
+    }
   }
+  __syncthreads();
+  if (local) {
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) par[a + i] = a + suf_find(lp, i, nv, s.status);
+  } else {
+    for (int v = a + threadIdx.x; v < e; v += blockDim.x) par[v] = v;
+  }
+}
+
+// Global unions of the edges that leave their tile (all edges of a tile too
+// large for shared memory), on the forests the tiles stored.
+__global__ void __launch_bounds__(TPB) k_link_x(const DevChain *__restrict__ ch,
+                                                const int2 *__restrict__ tab, int64_t blk0,
+                                                Scratch s) {
+  if (halted(s)) return;
+  const int2 t = tab[blk0 + blockIdx.x];
+  const DevChain &C = ch[t.x];
+  const int c0 = t.y * TILE, c1 = min(C.ncell, c0 + TILE);
+  const int32_t *vp = s.vptr + C.cell_off;
+  const int a = vp[c0], e = vp[c1];
+  const bool local = e - a <= SMEM_CAP;
+  const int64_t vb = C.vtx_base, wb = vb >> 5;
+  int32_t *par = s.parent + vb;
+  for (int w = a + threadIdx.x; w < e; w += blockDim.x)
+    if (!local || get_bit(s.xmark, wb, w)) uf_union(par, s.pl[vb + w], s.pr[vb + w], s.status);
 }
 
 // ---- compression + coins --------------------------------------------------------
@@ -1050,6 +1218,8 @@ void launch_cut(const Launch &L, cudaStream_t st) {
 void launch_link(const Launch &L, cudaStream_t st) {
   if (L.ntile[0]) k_link<1><<<g1(L.ntile[0]), TPB, 0, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
   if (L.ntile[1]) k_link<2><<<g1(L.ntile[1]), TPB, 0, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
+  const int64_t n = L.ntile[0] + L.ntile[1];
+  if (n) k_link_x<<<g1(n), TPB, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
 }
 
 void launch_compress(const Launch &L, cudaStream_t st) {
