@@ -51,20 +51,24 @@ def load_peaks():
 
 
 def phase_bytes(rec, ncell, L):
-    """Algorithmic bytes per phase of one update from its counts."""
+    """Algorithmic bytes per phase of one update from its counts: every datum
+    the phase must read or write, counted once (re-reads served by caches are
+    not counted)."""
     n = float(rec["n"])
     no, nn = float(rec["n_off_old"]), float(rec["n_off_new"])
     return {
-        # read old operator times, write vertex time/flag/parent, cell offsets,
-        # clear three bitmaps
-        "insert": 8 * no + 13 * n + 8 * ncell + 3 * n / 8,
+        # old operator times and offsets in; vertex time/flag/cell and cell
+        # offsets out; four per-vertex bitmaps cleared
+        "insert": 8 * no + 10 * n + 8 * ncell + n / 2,
         "cut": 16.0 * L,
-        # vertex times once, predecessor links out, flag RMW, two parent reads per edge
-        "link_union": 26 * n + 4 * ncell,
-        # parent read + root write + three bitmaps
+        # vertex time and cell in, predecessor links and parent forest out,
+        # flag read-modify-write, cell offsets
+        "link_union": 23 * n + 4 * ncell,
+        # parent read, root written, open-mark / open-root / flip bitmaps
         "loop_ids": 8.375 * n,
-        # links, flags, two roots, three times per vertex, new flag
-        "loop_props": 42 * n + 4 * ncell,
+        # cell, links, flag read+write, parent, time, flip bits; new-operator
+        # counts per cell
+        "loop_props": 23.125 * n + 4 * ncell,
         "op_offsets": 16 * (ncell / 128.0),
         # flags, new operator times read + written, cell offsets
         "op_rewrite": n + 16 * nn + 8 * ncell,

@@ -257,10 +257,11 @@ int lcqmc_server_destroy(lcqmc_server_t s);
 int lcqmc_loops_noalloc(const int32_t *pl, const int32_t *pr, int64_t n, int32_t *root,
                         void *cuda_stream);
 
-/* Host-side self-test of the integer forms of the update's two rounding steps
- * (which = 0: the candidate time fma(t_end - t0, u, t0) over random window
- * geometries; which = 1: rint(x 2^F)) against the C library, on n random
- * inputs from seed.  *mismatches receives the count.  Needs no GPU. */
+/* Host-side self-test of the integer bit constructions the kernels use, against
+ * the C library, on n random inputs from seed (which = 0: the unit factor
+ * u53 2^-53 of a candidate time, Sec. 2 step 2; which = 1: the tick count
+ * rint(x 2^F) of a time, used by the loop-length sums).  *mismatches receives
+ * the count.  Needs no GPU. */
 int lcqmc_selftest(int which, int64_t n, uint64_t seed, int64_t *mismatches);
 
 /* Message of the calling thread's last failure ("" if none). */

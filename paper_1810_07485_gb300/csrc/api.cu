@@ -81,30 +81,13 @@ int lcqmc_selftest(int which, int64_t n, uint64_t seed, int64_t *mismatches) {
   int64_t bad = 0;
   for (int64_t i = 0; i < n; ++i) {
     if (which == 0) {
-      // window geometry as the update builds it, J and beta spread over decades
-      const double J = std::exp((unif() - 0.5) * 12.0);
-      const double w = 16.0 / J;
-      const int64_t nwin = 1 + (int64_t)(next() % 100000);
-      const double beta = ((double)(nwin - 1) + unif()) * w;
-      const int64_t j = (int64_t)(next() % (uint64_t)nwin);
-      const double t0 = (double)j * w;
-      const double te = (j == nwin - 1) ? beta : (double)(j + 1) * w;
-      const double d = te - t0;
-      if (!(d > 0.0)) continue;
+      // the unit factor u53 * 2^-53 of a candidate time, over all magnitudes
       uint64_t u53 = next() >> 11;
-      const int mode = (int)(next() % 4);
-      if (mode == 1) u53 &= 0xFFFF;                   // small u
-      if (mode == 2) u53 |= (1ull << 53) - (1ull << 20);  // u close to 1
-      double db, tb;
-      std::memcpy(&db, &d, 8);
-      std::memcpy(&tb, &t0, 8);
-      uint64_t dbits, tbits;
-      std::memcpy(&dbits, &d, 8);
-      std::memcpy(&tbits, &t0, 8);
-      const double ref = std::fma(d, std::ldexp((double)u53, -53), t0);
+      u53 >>= next() % 54;
+      const double ref = std::ldexp((double)u53, -53);
       uint64_t rbits;
       std::memcpy(&rbits, &ref, 8);
-      if (lcq::tau_fma_bits(dbits, tbits, u53) != rbits) ++bad;
+      if (lcq::unit_bits(u53) != rbits) ++bad;
     } else if (which == 1) {
       const int F = (int)(next() % 63);
       const double v = std::ldexp(unif() + 0.5, (int)(next() % 60) - 40);

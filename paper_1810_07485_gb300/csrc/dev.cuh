@@ -193,84 +193,26 @@ __device__ __forceinline__ u128 sq_abs(long long v) {
   return (u128)a * (u128)a;
 }
 
-// ---- exact integer forms of the few fp64 operations of the method ------------
+// ---- times as bit patterns ------------------------------------------------------
 // GB300 executes fp64 instructions on a handful of lanes per SM, so the hot
 // loops keep imaginary times as the bit patterns of non-negative doubles
-// (ordered like the doubles themselves when read as int64) and evaluate the
-// method's two rounding steps with integer arithmetic, exactly as IEEE 754
-// defines them (round to nearest, ties to even).
+// (ordered like the doubles themselves when read as int64).  The only fp64
+// instruction left is one fused multiply-add per insertion candidate; the
+// conversion of times to integer ticks is done with integer arithmetic,
+// exactly as IEEE 754 defines it (round to nearest, ties to even).
 
 constexpr uint64_t M52 = (1ull << 52) - 1;
 
-__host__ __device__ __forceinline__ int clz128(u128 x) {
-  const uint64_t hi = (uint64_t)(x >> 64), lo = (uint64_t)x;
+// Bits of the double u53 * 2^-53 for u53 < 2^53 (exact).
+__host__ __device__ __forceinline__ uint64_t unit_bits(uint64_t u53) {
+  if (u53 == 0) return 0;
 #ifdef __CUDA_ARCH__
-  return hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+  const int s = __clzll((long long)u53) - 11;
 #else
-  return hi ? __builtin_clzll(hi) : (lo ? 64 + __builtin_clzll(lo) : 128);
+  const int s = __builtin_clzll(u53) - 11;
 #endif
-}
-
-// Bits of the positive double nearest to S * 2^e (S > 0, S < 2^127; normal
-// range), ties to even.
-__host__ __device__ __forceinline__ uint64_t round_to_double_bits(u128 S, int e) {
-  const int nb = 128 - clz128(S);
-  uint64_t q;
-  if (nb <= 53) {
-    q = (uint64_t)S << (53 - nb);
-    e -= 53 - nb;
-  } else {
-    const int sh = nb - 53;
-    q = (uint64_t)(S >> sh);
-    const u128 rem = S - ((u128)q << sh);
-    const u128 half = (u128)1 << (sh - 1);
-    if (rem > half || (rem == half && (q & 1))) ++q;
-    e += sh;
-    if (q >> 53) {
-      q >>= 1;
-      ++e;
-    }
-  }
-  return ((uint64_t)(e + 1075) << 52) | (q & M52);
-}
-
-// Bits of fma(d, u53 * 2^-53, t0) for d > 0 and t0 >= 0 normal doubles given as
-// bit patterns and u53 < 2^53: the exact product plus t0, rounded once.
-__host__ __device__ __forceinline__ uint64_t tau_fma_bits(uint64_t d_bits, uint64_t t0_bits,
-                                                         uint64_t u53) {
-  if (u53 == 0) return t0_bits;
-  const int ed = (int)((d_bits >> 52) & 0x7ff);
-  const uint64_t md = (d_bits & M52) | (1ull << 52);
-  u128 X = (u128)md * (u128)u53;  // product, scale 2^eX, < 2^106
-  int eX = ed - 1075 - 53;
-  if (t0_bits == 0) return round_to_double_bits(X, eX);
-  const int et = (int)((t0_bits >> 52) & 0x7ff);
-  u128 Y = (u128)((t0_bits & M52) | (1ull << 52));
-  int eY = et - 1075;
-  // align: the operand with the larger exponent is shifted left as far as the
-  // sum stays below 2^127; the other one is shifted right with a sticky bit.
-  u128 hi = X, lo = Y;
-  int ehi = eX, elo = eY;
-  if (eY > eX) {
-    hi = Y;
-    lo = X;
-    ehi = eY;
-    elo = eX;
-  }
-  const int diff = ehi - elo;
-  const int room = 126 - (128 - clz128(hi));
-  const int s = diff < room ? diff : room;
-  hi <<= s;
-  const int r = diff - s;
-  if (r > 0) {
-    if (r >= 128) {
-      lo = lo ? 1 : 0;
-    } else {
-      const u128 out = lo & (((u128)1 << r) - 1);
-      lo = (lo >> r) | (out ? 1 : 0);
-    }
-  }
-  return round_to_double_bits(hi + lo, ehi - s);
+  // u53 in [2^(52-s), 2^(53-s)): value 1.f * 2^(-1-s)
+  return ((uint64_t)(1022 - s) << 52) | ((u53 << s) & M52);
 }
 
 // llrint(ldexp(x, F)) for a non-negative double x given as bits (x 2^F < 2^62).

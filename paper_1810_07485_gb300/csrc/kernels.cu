@@ -217,42 +217,75 @@ __device__ int64_t lb_lookback(unsigned long long *st, int64_t g, int64_t first,
 // cell's kept candidates by (u53, draw index), and against its old operators
 // by time (an old operator goes first on a tie).  Every vertex is then written
 // by its own thread (time, flag, cell; the parent forest is set by the linking
-// kernels).  Candidates are staged INS_CAP at a time: a tile whose
-// candidates exceed that (the mean is 8 * TILE) runs its cells in groups,
-// counting in a first pass and drawing again in the writing pass.
-constexpr int INS_CAP = 1536;
+// kernels).  Candidates are staged INS_CAP at a time: a tile whose candidates
+// exceed that (the mean is 8 * TILE) runs its cells in groups, counting in a
+// first pass and drawing again in the writing pass.
+constexpr int INS_CAP = 1280;
 constexpr int INS_SPAN = INS_CAP - KMAX;  // a group's cells start within INS_SPAN slots
 constexpr int INS_UCAP = INS_CAP / 2 + TILE;
 constexpr int INS_MAXG = (TILE * (KMAX - 1)) / INS_SPAN + 2;
+constexpr int INS_OPCAP = 2048;  // old operators of a group mapped to their cell
+constexpr unsigned long long KEY_DROP = 1ull << 63;
 
 template <int Q>
 struct InsSmem {
-  unsigned long long u53[INS_CAP];
-  long long tau[INS_CAP];  // -1: candidate not kept
-  uint8_t scell[INS_CAP];  // slot -> cell in tile
-  uint8_t ucell[INS_UCAP];  // Philox call -> cell in tile
+  unsigned long long key[INS_CAP];  // u53, with bit 63 set if the candidate is not kept
+  long long tau[INS_CAP];           // time bits; LLONG_MAX if not kept
+  short klist[INS_CAP];             // kept candidates' slots (any order)
+  uint8_t scell[INS_CAP];           // slot -> cell in tile
+  uint8_t ucell[INS_UCAP];          // Philox call -> cell in tile
+  uint8_t qcell[INS_OPCAP];         // old operator -> cell in tile
   NbOps<Q> X[TILE];
+  unsigned long long T[2][KMAX];    // Poisson thresholds: full windows, last window
   int kpre[TILE + 1], upre[TILE + 1], q[TILE + 1];
   int K[TILE], nk[TILE], cex[TILE], b[TILE], j[TILE];
   uint8_t par0[TILE];
   int gfirst[INS_MAXG + 1];
-  int G;
+  int G, nkept;
   int sm[33];
   int64_t excl;
   int64_t gt;
 };
 
+// Number of operators of one neighbour bond (times tq[lo..hi), ascending)
+// that act before a candidate at time tau on bond b: order (time, bond).
+__device__ __forceinline__ int ops_before(const long long *__restrict__ tq, int lo, int hi,
+                                          long long tau, int bb, int b) {
+  const long long thr = tau + (bb < b ? 1 : 0);  // t < thr  <=>  (t, bb) < (tau, b)
+  const int base = lo;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (tq[mid] < thr)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo - base;
+}
+
 template <int Q>
-__device__ __forceinline__ void ins_decide(const DevChain &C, InsSmem<Q> &S, const long long *otau,
-                                           int c, int slot, uint64_t u53, uint64_t t0b,
-                                           uint64_t teb, uint64_t db, bool count) {
-  const long long tau = (long long)tau_fma_bits(db, t0b, u53);
-  bool keep = tau < (long long)teb;
-  if (keep) keep = (S.par0[c] ^ nb_parity<Q>(S.X[c], otau, tau, S.b[c])) & 1;
-  S.u53[slot] = u53;
-  S.tau[slot] = keep ? tau : -1;
+__device__ __forceinline__ void ins_decide(InsSmem<Q> &S, const long long *otau, int c, int slot,
+                                           uint64_t u53, double t0, double d, long long teb,
+                                           bool count) {
+  // tau = fma(d, u53 2^-53, t0), one IEEE fused multiply-add
+  const long long tau =
+      __double_as_longlong(__fma_rn(d, __longlong_as_double((long long)unit_bits(u53)), t0));
+  bool keep = tau < teb;
+  if (keep) {
+    const NbOps<Q> &X = S.X[c];
+    const int b = S.b[c];
+    int p = S.par0[c];
+#pragma unroll
+    for (int k = 0; k < NbOps<Q>::N; ++k) p ^= ops_before(otau, X.o0[k], X.o1[k], tau, X.bond[k], b);
+    keep = p & 1;
+  }
+  S.key[slot] = keep ? u53 : (u53 | KEY_DROP);
+  S.tau[slot] = keep ? tau : LLONG_MAX;
   S.scell[slot] = (uint8_t)c;
-  if (count && keep) atomicAdd(&S.nk[c], 1);
+  if (keep) {
+    S.klist[atomicAdd(&S.nkept, 1)] = (short)slot;
+    if (count) atomicAdd(&S.nk[c], 1);
+  }
 }
 
 // Draw and decide the candidates of the cells of group g.
@@ -264,23 +297,33 @@ __device__ void ins_draw(const DevChain &C, InsSmem<Q> &S, const long long *otau
     const int c = threadIdx.x;
     if (c >= c0 && c < c1)
       for (int u = S.upre[c], e = S.upre[c + 1]; u < e; ++u) S.ucell[u - ub] = (uint8_t)c;
+    if (threadIdx.x == 0) S.nkept = 0;
   }
   __syncthreads();
   const uint32_t k0 = (uint32_t)C.seed, k1 = (uint32_t)(C.seed >> 32);
-  for (int u = threadIdx.x; u < nu; u += TILE) {
+  for (int u0 = 0; u0 < nu; u0 += TILE) {  // whole warps, reconverged per step
+    const int u = u0 + threadIdx.x;
+    if (u >= nu) {
+      __syncwarp();
+      continue;
+    }
     const int c = S.ucell[u];
     const int m = u + ub - S.upre[c];
-    const int b = S.b[c], j = S.j[c], K = S.K[c], ks = S.kpre[c] - kb;
-    const uint64_t t0b = C.win[3 * j], teb = C.win[3 * j + 1], db = C.win[3 * j + 2];
-    const U4 o = philox((TAG_INSERT << 24) | (uint32_t)m, (uint32_t)b, (uint32_t)j, C.sweep, k0, k1);
-    const uint64_t lo = ((uint64_t)o.x | ((uint64_t)o.y << 32)) >> 11;
-    const uint64_t hi = ((uint64_t)o.z | ((uint64_t)o.w << 32)) >> 11;
-    if (m == 0) {
-      ins_decide<Q>(C, S, otau, c, ks, hi, t0b, teb, db, count);
-    } else {
-      ins_decide<Q>(C, S, otau, c, ks + 2 * m - 1, lo, t0b, teb, db, count);
-      if (2 * m < K) ins_decide<Q>(C, S, otau, c, ks + 2 * m, hi, t0b, teb, db, count);
+    const int j = S.j[c], K = S.K[c], ks = S.kpre[c] - kb;
+    const double t0 = __longlong_as_double((long long)C.win[3 * j]);
+    const long long teb = (long long)C.win[3 * j + 1];
+    const double d = __longlong_as_double((long long)C.win[3 * j + 2]);
+    const U4 o = philox((TAG_INSERT << 24) | (uint32_t)m, (uint32_t)S.b[c], (uint32_t)j, C.sweep, k0, k1);
+    // words (x, y): candidate 2m-1 (for m = 0 the count); words (z, w): candidate 2m
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = 2 * m - 1 + h;
+      if (k < 0 || k >= K) continue;
+      const uint64_t u53 = (h ? ((uint64_t)o.z | ((uint64_t)o.w << 32))
+                              : ((uint64_t)o.x | ((uint64_t)o.y << 32))) >> 11;
+      ins_decide<Q>(S, otau, c, ks + k, u53, t0, d, teb, count);
     }
+    __syncwarp();
   }
   __syncthreads();
 }
@@ -291,52 +334,75 @@ template <int Q>
 __device__ void ins_write(const DevChain &C, InsSmem<Q> &S, const long long *otau, int g,
                           int64_t base, const Scratch &s) {
   const int c0 = S.gfirst[g], c1 = S.gfirst[g + 1];
-  const int kb = S.kpre[c0], ns = S.kpre[c1] - kb;
+  const int kb = S.kpre[c0];
   const int64_t vb = C.vtx_base;
   long long *vt = (long long *)s.vtau + vb;
   uint8_t *vf = s.vflag + vb, *vc = s.vcell + vb;
-  for (int i = threadIdx.x; i < ns; i += TILE) {
-    const long long tau = S.tau[i];
-    if (tau < 0) continue;
-    const int c = S.scell[i];
-    const int ks = S.kpre[c] - kb, K = S.K[c], k = i - ks;
-    const unsigned long long u = S.u53[i];
+  const int nkept = S.nkept;
+  for (int i0 = 0; i0 < nkept; i0 += TILE) {
+    const int i = i0 + threadIdx.x;
+    if (i >= nkept) {
+      __syncwarp();
+      continue;
+    }
+    const int slot = S.klist[i];
+    const long long tau = S.tau[slot];
+    const int c = S.scell[slot];
+    const int ks = S.kpre[c] - kb, K = S.K[c], k = slot - ks;
+    const unsigned long long key = S.key[slot];
     int r = 0;
     for (int x = 0; x < K; ++x) {
-      const unsigned long long u2 = S.u53[ks + x];
-      r += (S.tau[ks + x] >= 0) & ((u2 < u) | ((u2 == u) & (x < k)));
+      const unsigned long long k2 = S.key[ks + x];
+      r += (k2 < key) | ((k2 == key) & (x < k));
     }
-    for (int q = S.q[c], e = S.q[c + 1]; q < e; ++q) {
-      if (otau[q] > tau) break;
-      ++r;
+    // old operators at or before tau (ascending times)
+    int lo = S.q[c], hi = S.q[c + 1];
+    const int q0 = lo;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (otau[mid] <= tau)
+        lo = mid + 1;
+      else
+        hi = mid;
     }
+    r += lo - q0;
     const int64_t pos = base + S.cex[c] + r;
     vt[pos] = tau;
     vf[pos] = 0;
     vc[pos] = (uint8_t)c;
+    __syncwarp();
   }
-  const int qa = S.q[c0], qb = S.q[c1];
-  for (int q = qa + threadIdx.x; q < qb; q += TILE) {
-    int lo = c0, hi = c1 - 1;  // largest c in [c0, c1) with S.q[c] <= q
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (S.q[mid] <= q)
-        lo = mid;
-      else
-        hi = mid - 1;
+  const int qa = S.q[c0], qb = S.q[c1], qt = S.q[0];
+  const bool mapped = qb - qt <= INS_OPCAP;
+  for (int q0 = qa; q0 < qb; q0 += TILE) {
+    const int q = q0 + threadIdx.x;
+    if (q >= qb) {
+      __syncwarp();
+      continue;
     }
-    const int c = lo;
+    int c;
+    if (mapped) {
+      c = S.qcell[q - qt];
+    } else {
+      int lo = c0, hi = c1 - 1;  // largest c in [c0, c1) with S.q[c] <= q
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (S.q[mid] <= q)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      c = lo;
+    }
     const long long ot = otau[q];
     const int ks = S.kpre[c] - kb, K = S.K[c];
     int r = q - S.q[c];
-    for (int x = 0; x < K; ++x) {
-      const long long t2 = S.tau[ks + x];
-      r += (t2 >= 0) & (t2 < ot);
-    }
+    for (int x = 0; x < K; ++x) r += S.tau[ks + x] < ot;
     const int64_t pos = base + S.cex[c] + r;
     vt[pos] = ot;
     vf[pos] = VF_OLD;
     vc[pos] = (uint8_t)c;
+    __syncwarp();
   }
 }
 
@@ -359,6 +425,11 @@ __global__ void __launch_bounds__(TILE) k_insert(DevChain *__restrict__ ch,
   const long long *otau = (const long long *)C.op_tau[cur];
   const uint8_t *s0 = C.s0[cur];
   int32_t *vp = s.vptr + C.cell_off;
+  if (threadIdx.x < KMAX) {
+    S.T[0][threadIdx.x] = c_T_full[threadIdx.x];
+    S.T[1][threadIdx.x] = C.T_last[threadIdx.x];
+  }
+  __syncthreads();
 
   // -- per-cell setup --------------------------------------------------------
   int K = 0, P = 0, q0 = 0, q1 = 0;
@@ -396,8 +467,11 @@ __global__ void __launch_bounds__(TILE) k_insert(DevChain *__restrict__ ch,
     const U4 o0 = philox(TAG_INSERT << 24, (uint32_t)b, (uint32_t)j, C.sweep, (uint32_t)C.seed,
                          (uint32_t)(C.seed >> 32));
     const uint64_t U = (uint64_t)o0.x | ((uint64_t)o0.y << 32);
-    const uint64_t *T = (j == C.nwin - 1) ? C.T_last : c_T_full;
-    while (K < KMAX - 1 && U >= T[K]) ++K;
+    const unsigned long long *T = S.T[j == C.nwin - 1 ? 1 : 0];
+    // K = number of thresholds T[0..KMAX-2] at or below U (they ascend)
+#pragma unroll
+    for (int step = 32; step > 0; step >>= 1)
+      if (K + step <= KMAX - 1 && T[K + step - 1] <= U) K += step;
     if ((long long)db <= 0) K = 0;  // empty last window
     P = K ? K / 2 + 1 : 0;
   }
@@ -408,6 +482,11 @@ __global__ void __launch_bounds__(TILE) k_insert(DevChain *__restrict__ ch,
   if (c == TILE - 1) S.q[TILE] = q1;
   int tot;
   const int ex = block_excl_scan<int>(K | (P << 16), S.sm, tot);
+  {
+    // old operator -> cell map (all of the tile's operators, if they fit)
+    const int qa = S.q[0];
+    for (int q = q0; q < q1 && q - qa < INS_OPCAP; ++q) S.qcell[q - qa] = (uint8_t)c;
+  }
   S.kpre[c] = ex & 0xffff;
   S.upre[c] = ex >> 16;
   if (c == TILE - 1) {
@@ -662,10 +741,11 @@ __device__ __forceinline__ int key_lower_bound(const long long *vt, int lo, int 
 
 // Linking, then the union of the two fragments below every vertex.  Edges
 // with both nodes in the tile are united in shared memory, and the tile's
-// forest is then stored as each node's local root; edges that leave the tile
-// are marked and united in the global forest by k_link_x, after every tile has
-// stored its forest (a tile too large for shared memory leaves all of its
-// edges to k_link_x, with every node its own root).
+// forest is then stored flat: every node points at its tile component's
+// root, its smallest node.  Edges
+// that leave the tile are marked and united in the global forest by k_link_x,
+// after every tile has stored its forest (a tile too large for shared memory
+// leaves all of its edges to k_link_x, with every node its own root).
 template <int Q>
 __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
                                               const int2 *__restrict__ tab, int64_t blk0,
@@ -710,7 +790,15 @@ __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
   const int64_t vb = C.vtx_base, wb = vb >> 5;
   const long long *__restrict__ vt = (const long long *)s.vtau + vb;
   int32_t *par = s.parent + vb;
-  for (int w = a + threadIdx.x; w < e; w += blockDim.x) {
+  // Whole warps walk the tile (trip count rounded up) and reconverge after
+  // every vertex, so that the divergent union of one iteration does not split
+  // the next one's predecessor search.
+  for (int w0 = a; w0 < e; w0 += blockDim.x) {
+    const int w = w0 + threadIdx.x;
+    if (w >= e) {
+      __syncwarp();
+      continue;
+    }
     const int ci = s.vcell[vb + w];
     const LinkCell<Q> &L = lc[ci];
     const int v0 = cvp[ci];
@@ -756,22 +844,41 @@ __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
     const bool inside = P[0] >= a && P[0] < e && P[1] >= a && P[1] < e;
     if (!inside) {
       set_bit(s.openmark, wb, P[0]);
-      if (local) set_bit(s.xmark, wb, w);
-    } else if (local) {
+      if (local && P[0] != P[1]) set_bit(s.xmark, wb, w);
+    } else if (local && P[0] != P[1]) {
       suf_union(lp, P[0] - a, P[1] - a, nv, s.status);
     }
+    __syncwarp();
   }
   __syncthreads();
   if (local) {
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) par[a + i] = a + suf_find(lp, i, nv, s.status);
+    // Pointer jumping until every node points at its root (the depth halves
+    // each round; 2^12 > SMEM_CAP bounds the rounds).
+    volatile int *vlp = lp;
+    for (int round = 0; round < 12; ++round) {
+      int changed = 0;
+      for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+        const int p = vlp[i], g = vlp[p];
+        if (g != p) {
+          vlp[i] = g;
+          changed = 1;
+        }
+      }
+      if (!__syncthreads_or(changed)) break;
+    }
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) par[a + i] = a + lp[i];
   } else {
     for (int v = a + threadIdx.x; v < e; v += blockDim.x) par[v] = v;
   }
 }
 
 // Global unions of the edges that leave their tile (all edges of a tile too
-// large for shared memory), on the forests the tiles stored.
-__global__ void __launch_bounds__(TPB) k_link_x(const DevChain *__restrict__ ch,
+// large for shared memory), on the forests the tiles stored.  A tile has about
+// 45 words of marks, so small blocks (one thread per word) keep many tiles in
+// flight: the unions are chains of dependent global loads.
+constexpr int TPB_X = 64;
+
+__global__ void __launch_bounds__(TPB_X) k_link_x(const DevChain *__restrict__ ch,
                                                 const int2 *__restrict__ tab, int64_t blk0,
                                                 Scratch s) {
   if (halted(s)) return;
@@ -781,10 +888,26 @@ __global__ void __launch_bounds__(TPB) k_link_x(const DevChain *__restrict__ ch,
   const int32_t *vp = s.vptr + C.cell_off;
   const int a = vp[c0], e = vp[c1];
   const bool local = e - a <= SMEM_CAP;
-  const int64_t vb = C.vtx_base, wb = vb >> 5;
+  const int64_t vb = C.vtx_base;
   int32_t *par = s.parent + vb;
-  for (int w = a + threadIdx.x; w < e; w += blockDim.x)
-    if (!local || get_bit(s.xmark, wb, w)) uf_union(par, s.pl[vb + w], s.pr[vb + w], s.status);
+  if (!local) {
+    for (int w = a + threadIdx.x; w < e; w += blockDim.x)
+      uf_union(par, s.pl[vb + w], s.pr[vb + w], s.status);
+    return;
+  }
+  // one 32-vertex word of the mark bitmap per thread
+  const int64_t wfirst = (vb + a) >> 5, wlast = (vb + e - 1) >> 5;
+  for (int64_t wd = wfirst + threadIdx.x; e > a && wd <= wlast; wd += blockDim.x) {
+    uint32_t bits = __ldcg(s.xmark + wd);
+    const int64_t v0 = (wd << 5) - vb;
+    if (v0 < a) bits &= ~0u << (a - v0);
+    if (v0 + 32 > e) bits &= (e - v0 >= 32) ? ~0u : ((1u << (e - v0)) - 1u);
+    while (bits) {
+      const int w = (int)v0 + __ffs(bits) - 1;
+      bits &= bits - 1;
+      uf_union(par, s.pl[vb + w], s.pr[vb + w], s.status);
+    }
+  }
 }
 
 // ---- compression + coins --------------------------------------------------------
@@ -810,7 +933,12 @@ __global__ void __launch_bounds__(TILE) k_compress(const DevChain *__restrict__ 
     coins[g] = philox(TAG_FLIP << 24, (uint32_t)(g0 + g), 0u, C.sweep, k0, k1);
   __syncthreads();
   int64_t roots = 0;
-  for (int v = a + threadIdx.x; v < e; v += blockDim.x) {
+  for (int v0 = a; v0 < e; v0 += blockDim.x) {  // whole warps, reconverged per step
+    const int v = v0 + threadIdx.x;
+    if (v >= e) {
+      __syncwarp();
+      continue;
+    }
     const int r = uf_root(par, v, s.status);
     if (r != v) par[v] = r;
     if (r == v) {
@@ -821,14 +949,32 @@ __global__ void __launch_bounds__(TILE) k_compress(const DevChain *__restrict__ 
       if (oversized) set_bit(s.openroot, wb, v);
     }
     if (get_bit(s.openmark, wb, v)) set_bit(s.openroot, wb, r);
+    __syncwarp();
   }
   const int64_t tot = block_sum<int64_t>(roots, sm);
   if (threadIdx.x == 0) s.tile_roots[gt] = tot;
 }
 
 // ---- loop properties, new flags ---------------------------------------------------
-__device__ __forceinline__ void open_add(int *keys, unsigned long long *vals, int key,
-                                         long long W, long long Cc, long long Ss, const Scratch &s,
+// Exact 64-bit two's-complement sums kept in shared memory as two 32-bit words
+// and added with native 32-bit atomics (a 64-bit shared-memory add would be a
+// compare-and-swap loop): the low word first, then the high word plus the
+// carry out of the low word.
+__device__ __forceinline__ void sadd64(unsigned *w, long long x) {
+  const unsigned lo = (unsigned)x, hi = (unsigned)((unsigned long long)x >> 32);
+  const unsigned old = atomicAdd(w, lo);
+  const unsigned h = hi + ((old + lo < old) ? 1u : 0u);
+  if (h) atomicAdd(w + 1, h);
+}
+
+__device__ __forceinline__ unsigned long long sget64(const unsigned *w) {
+  return ((unsigned long long)w[1] << 32) | w[0];
+}
+
+// Sums of a loop that leaves the tile: a shared hash of the tile's open roots
+// (3 split sums per slot), spilling to the root's global record when full.
+__device__ __forceinline__ void open_add(int *keys, unsigned *vals, int key, long long W,
+                                         long long Cc, long long Ss, const Scratch &s,
                                          int64_t vb) {
   unsigned h = ((unsigned)key * 2654435761u) & (OPEN_SLOTS - 1);
   for (int probe = 0; probe < OPEN_SLOTS; ++probe) {
@@ -838,9 +984,9 @@ __device__ __forceinline__ void open_add(int *keys, unsigned long long *vals, in
       if (k == -1) k = key;
     }
     if (k == key) {
-      atomicAdd(vals + 3 * h + 0, (unsigned long long)W);
-      atomicAdd(vals + 3 * h + 1, (unsigned long long)Cc);
-      atomicAdd(vals + 3 * h + 2, (unsigned long long)Ss);
+      sadd64(vals + 6 * h + 0, W);
+      sadd64(vals + 6 * h + 2, Cc);
+      sadd64(vals + 6 * h + 4, Ss);
       return;
     }
     h = (h + 1) & (OPEN_SLOTS - 1);
@@ -854,17 +1000,16 @@ __device__ __forceinline__ void open_add(int *keys, unsigned long long *vals, in
 constexpr int TPB_EST = 512;
 
 template <int Q>
-__global__ void __launch_bounds__(TPB_EST) k_est(const DevChain *__restrict__ ch,
+__global__ void __launch_bounds__(TPB_EST, 3) k_est(const DevChain *__restrict__ ch,
                                              const int2 *__restrict__ tab, int64_t blk0,
                                              Scratch s) {
-  extern __shared__ unsigned long long est_dyn[];
-  unsigned long long *cW = est_dyn, *cC = est_dyn + SMEM_CAP, *cS = est_dyn + 2 * SMEM_CAP;
+  extern __shared__ unsigned est_dyn[];  // closed loops' split sums, by root slot
+  unsigned *cW = est_dyn, *cC = est_dyn + 2 * SMEM_CAP, *cS = est_dyn + 4 * SMEM_CAP;
   __shared__ int okeys[OPEN_SLOTS];
-  __shared__ unsigned long long ovals[3 * OPEN_SLOTS];
+  __shared__ unsigned ovals[6 * OPEN_SLOTS];
   __shared__ int cvp[TILE + 1];
   __shared__ int cnew[TILE];
   __shared__ long long ccl[TILE], csl[TILE], ccr[TILE], csr[TILE], cxl[TILE], cxr[TILE];
-  __shared__ long long wbuf[TPB_EST / 32][32][3];
   __shared__ int64_t sm[33];
   if (halted(s)) return;
   const int64_t gt = blk0 + blockIdx.x;
@@ -890,19 +1035,20 @@ __global__ void __launch_bounds__(TPB_EST) k_est(const DevChain *__restrict__ ch
   __syncthreads();
   const int a = cvp[0], e = cvp[ncl];
   const int nv = min(e - a, SMEM_CAP);
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) cW[i] = cC[i] = cS[i] = 0ull;
+  for (int i = threadIdx.x; i < 2 * nv; i += blockDim.x) cW[i] = cC[i] = cS[i] = 0u;
   for (int i = threadIdx.x; i < OPEN_SLOTS; i += blockDim.x) {
     okeys[i] = -1;
-    ovals[3 * i] = ovals[3 * i + 1] = ovals[3 * i + 2] = 0ull;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) ovals[6 * i + k] = 0u;
   }
   __syncthreads();
   const int64_t vb = C.vtx_base, wb = vb >> 5;
   const int32_t *par = s.parent + vb;
   const uint64_t *vt = (const uint64_t *)s.vtau + vb;
   const int F = C.F;
-  // Whole warps walk the tile (trip count rounded up) so that the warp-wide
-  // key reduction below has every lane present.
-  const int lane = threadIdx.x & 31;
+  // Whole warps walk the tile (trip count rounded up), reconverging after
+  // every vertex.
+  u128 w2 = 0, f2 = 0;  // this thread's share of sum W^2 and sum (C^2 + S^2)
   for (int w0 = a; w0 < e; w0 += blockDim.x) {
     const int w = w0 + threadIdx.x;
     int key = -1;  // root of the loop the two fragments below w belong to
@@ -911,37 +1057,35 @@ __global__ void __launch_bounds__(TPB_EST) k_est(const DevChain *__restrict__ ch
       const int ci = s.vcell[vb + w];
       const int P = s.pl[vb + w], R = s.pr[vb + w];
       const uint8_t f = s.vflag[vb + w];
-      const int rb = __ldcg(par + P), ra = __ldcg(par + w);
+      // a node whose two upper legs both end at w is a loop by itself: its
+      // own root
+      const int rb = (P == R) ? P : __ldcg(par + P), ra = __ldcg(par + w);
       const int nf = (f & VF_OLD) ^ get_bit(s.flipbits, wb, rb) ^ get_bit(s.flipbits, wb, ra);
       s.vflag[vb + w] = (uint8_t)(f | (nf ? VF_NEW : 0));
       if (nf) atomicAdd(cnew + ci, 1);
       // fragment lengths in ticks of 2^-F: q(tau_top) - q(tau_bottom) (+ crossings)
       const long long qw = q_time(vt[w], F);
-      long long dl = qw - q_time(vt[P], F);
+      const long long qP = q_time(vt[P], F);
+      long long dl = qw - qP;
       if (f & VF_WRAP_L) dl += cxl[ci];
-      long long dr = qw - q_time(vt[R], F);
+      long long dr = qw - (R == P ? qP : q_time(vt[R], F));
       if (f & VF_WRAP_R) dr += cxr[ci];
       W = dl + dr;
       Cc = mul_q32(dl, ccl[ci]) + mul_q32(dr, ccr[ci]);
       Ss = mul_q32(dl, csl[ci]) + mul_q32(dr, csr[ci]);
-      key = rb;
-    }
-    // Lanes holding the same loop root (mostly the giant loop) are summed by
-    // the group's lowest lane from a per-warp buffer; one set of atomics per
-    // distinct root and warp.
-    const unsigned grp = __match_any_sync(0xffffffffu, key);
-    const int wid = threadIdx.x >> 5;
-    wbuf[wid][lane][0] = W;
-    wbuf[wid][lane][1] = Cc;
-    wbuf[wid][lane][2] = Ss;
-    __syncwarp();
-    if (key >= 0 && lane == __ffs(grp) - 1) {
-      for (unsigned mm = grp & (grp - 1); mm; mm &= mm - 1) {
-        const int j = __ffs(mm) - 1;
-        W += wbuf[wid][j][0];
-        Cc += wbuf[wid][j][1];
-        Ss += wbuf[wid][j][2];
+      if (P == R) {
+        // Both upper legs of node P end at w, so P is a loop by itself and its
+        // two fragments are the two below w: the loop's sums are complete here.
+        w2 += sq_abs(W);
+        f2 += sq_abs(Cc) + sq_abs(Ss);
+      } else {
+        key = rb;
       }
+    }
+    // Each lane adds its vertex's sums to its loop: loops are small (a warp
+    // sees about 26 different roots in 32 vertices), so lanes add directly and
+    // the rare collisions serialize in the atomic unit.
+    if (key >= 0) {
       if (get_bit(s.openroot, wb, key)) {
         open_add(okeys, ovals, key, W, Cc, Ss, s, vb);
       } else {
@@ -949,9 +1093,9 @@ __global__ void __launch_bounds__(TPB_EST) k_est(const DevChain *__restrict__ ch
         if (li < 0 || li >= nv) {
           fail_check(s, 3, c0, w, key, a, nv);
         } else {
-          atomicAdd(cW + li, (unsigned long long)W);
-          atomicAdd(cC + li, (unsigned long long)Cc);
-          atomicAdd(cS + li, (unsigned long long)Ss);
+          sadd64(cW + 2 * li, W);
+          sadd64(cC + 2 * li, Cc);
+          sadd64(cS + 2 * li, Ss);
         }
       }
     }
@@ -965,21 +1109,22 @@ __global__ void __launch_bounds__(TPB_EST) k_est(const DevChain *__restrict__ ch
   }
   const int64_t tot = block_sum<int64_t>((int64_t)newcnt, sm);
   if (threadIdx.x == 0) s.tile_sum2[gt] = tot;
-  u128 w2 = 0, f2 = 0;
+  // Only loops closed in the tile (of more than one node) add to the shared
+  // accumulators, at their root's slot; every other slot stays zero.
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-    const int v = a + i;
-    if (__ldcg(par + v) == v && !get_bit(s.openroot, wb, v)) {
-      w2 += sq_abs((long long)cW[i]);
-      f2 += sq_abs((long long)cC[i]) + sq_abs((long long)cS[i]);
+    const unsigned long long x = sget64(cW + 2 * i), y = sget64(cC + 2 * i), z = sget64(cS + 2 * i);
+    if (x | y | z) {
+      w2 += sq_abs((long long)x);
+      f2 += sq_abs((long long)y) + sq_abs((long long)z);
     }
   }
   for (int h = threadIdx.x; h < OPEN_SLOTS; h += blockDim.x) {
     const int kk = okeys[h];
     if (kk >= 0) {
       unsigned long long *r = s.acc + 4 * (vb + kk);
-      atomicAdd(r, ovals[3 * h]);
-      atomicAdd(r + 1, ovals[3 * h + 1]);
-      atomicAdd(r + 2, ovals[3 * h + 2]);
+      atomicAdd(r, sget64(ovals + 6 * h));
+      atomicAdd(r + 1, sget64(ovals + 6 * h + 2));
+      atomicAdd(r + 2, sget64(ovals + 6 * h + 4));
     }
   }
   w2 = block_sum_u128(w2);
@@ -1007,7 +1152,7 @@ __global__ void __launch_bounds__(TPB) k_compact(const DevChain *__restrict__ ch
   int32_t *nptr = C.op_ptr[C.cur ^ 1];
   double *ntau = C.op_tau[C.cur ^ 1];
   const int32_t *vp = s.vptr + C.cell_off;
-  const int64_t vb = C.vtx_base, wb = vb >> 5;
+  const int64_t vb = C.vtx_base;
   const int64_t base = s.tile_pref2[gt];
   {
     const int cnt = (threadIdx.x < ncl) ? nptr[c0 + threadIdx.x] : 0;
@@ -1053,11 +1198,12 @@ __global__ void __launch_bounds__(TPB) k_compact(const DevChain *__restrict__ ch
     while (bits) {
       const int i = __ffs(bits) - 1;
       bits &= bits - 1;
-      ulonglong4 *r = (ulonglong4 *)(s.acc + 4 * (vb + v0 + i));
-      const ulonglong4 x = *r;
-      *r = make_ulonglong4(0ull, 0ull, 0ull, 0ull);
+      ulonglong2 *r = (ulonglong2 *)(s.acc + 4 * (vb + v0 + i));
+      const ulonglong2 x = r[0], y = r[1];
+      r[0] = make_ulonglong2(0ull, 0ull);
+      r[1] = make_ulonglong2(0ull, 0ull);
       w2 += sq_abs((long long)x.x);
-      f2 += sq_abs((long long)x.y) + sq_abs((long long)x.z);
+      f2 += sq_abs((long long)x.y) + sq_abs((long long)y.x);
     }
   }
   w2 = block_sum_u128(w2);
@@ -1219,7 +1365,7 @@ void launch_link(const Launch &L, cudaStream_t st) {
   if (L.ntile[0]) k_link<1><<<g1(L.ntile[0]), TPB, 0, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
   if (L.ntile[1]) k_link<2><<<g1(L.ntile[1]), TPB, 0, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
   const int64_t n = L.ntile[0] + L.ntile[1];
-  if (n) k_link_x<<<g1(n), TPB, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
+  if (n) k_link_x<<<g1(n), TPB_X, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
 }
 
 void launch_compress(const Launch &L, cudaStream_t st) {
@@ -1227,7 +1373,7 @@ void launch_compress(const Launch &L, cudaStream_t st) {
   if (n) k_compress<<<g1(n), TILE, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
 }
 
-constexpr size_t EST_DYN_SMEM = 3 * SMEM_CAP * sizeof(unsigned long long);
+constexpr size_t EST_DYN_SMEM = 6 * SMEM_CAP * sizeof(unsigned);
 
 int init_kernel_attributes() {
   if (cudaFuncSetAttribute(k_est<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EST_DYN_SMEM) !=
