@@ -39,6 +39,19 @@ DEFAULT_WORKLOAD = "L65536_beta4096"
 ORACLE_SAMPLE_L = 1024
 KERNELS_PER_UPDATE = 11
 RECORD_BYTES = 104
+# DRAM bytes per vertex of each phase's kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture at L=16384, beta=4096, divided by
+# that update's vertex count; profiles/topkernels_L16384_beta4096.md), valid
+# for the kernel source with this sha1 only.
+TRAFFIC_PER_VERTEX = {"insert": 13.1, "link_union": 26.8, "loop_ids": 7.5, "loop_props": 24.9,
+                      "op_rewrite": 14.8}
+TRAFFIC_KERNELS_SHA1 = "d8bf4742c379e5b33c6c4798fbb7847926405f3b"
+
+
+def kernels_sha1():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1810_07485_gb300", "csrc", "kernels.cu"), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
 
 
 def load_peaks():
@@ -246,8 +259,12 @@ def run_ours(args, world, rank, local):
     dom = max(ph, key=lambda k: ph[k])
     peak, peak_kind = load_peaks()
     achieved = nb[dom] / (ph[dom] * 1e-3) / 1e9 if ph[dom] > 0 else 0.0
+    traffic = None  # bytes per launch, only while the kernels are the profiled ones
+    if kernels_sha1() == TRAFFIC_KERNELS_SHA1 and dom in TRAFFIC_PER_VERTEX:
+        traffic = TRAFFIC_PER_VERTEX[dom] * float(pr["n"].mean())
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": dom, "peak_kind": peak_kind,
+                "frac": achieved / peak, "traffic": traffic,
+                "algorithmic_bytes": nb[dom] / nph, "kernel": dom, "peak_kind": peak_kind,
                 "phase_ms_per_update": {k: ph[k] / nph for k in ph},
                 "phase_frac_of_hbm": {k: (nb[k] / (ph[k] * 1e-3) / 1e9) / peak if ph[k] > 0 else None for k in ph}}
 
