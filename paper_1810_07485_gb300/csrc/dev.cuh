@@ -13,7 +13,6 @@ constexpr int KMAX = 48;          // Poisson count table length (K <= KMAX-1)
 constexpr int TW = LCQMC_TW;      // windows per time block of the cell order
 constexpr int TILE = 128;         // cells per tile (one thread block)
 constexpr int SMEM_CAP = 2048;    // vertices a tile can accumulate in shared memory
-constexpr int OPEN_SLOTS = 128;   // shared hash slots for loops that leave a tile
 constexpr int MAX_COIN_GROUPS = 64;
 constexpr int SITE_BLOCK = 128;   // original sites per block
 constexpr int BOND_BLOCK = 128;   // bonds per block

@@ -971,13 +971,17 @@ __device__ __forceinline__ unsigned long long sget64(const unsigned *w) {
   return ((unsigned long long)w[1] << 32) | w[0];
 }
 
-// Sums of a loop that leaves the tile: a shared hash of the tile's open roots
-// (3 split sums per slot), spilling to the root's global record when full.
-__device__ __forceinline__ void open_add(int *keys, unsigned *vals, int key, long long W,
+// Per-tile table of loop sums keyed by root: a vertex of a loop of more than
+// one node adds its (W, C, S) to its root's slot (linear probing, split
+// sums).  If the table is full the sums go to the root's global record and
+// the root is marked open, so that they are squared with the open loops.
+constexpr int LOOP_SLOTS = 256;
+
+__device__ __forceinline__ void loop_add(int *keys, unsigned *vals, int key, long long W,
                                          long long Cc, long long Ss, const Scratch &s,
                                          int64_t vb) {
-  unsigned h = ((unsigned)key * 2654435761u) & (OPEN_SLOTS - 1);
-  for (int probe = 0; probe < OPEN_SLOTS; ++probe) {
+  unsigned h = ((unsigned)key * 2654435761u) >> 24;  // top 8 bits: LOOP_SLOTS = 256
+  for (int probe = 0; probe < LOOP_SLOTS; ++probe) {
     int k = keys[h];
     if (k == -1) {
       k = atomicCAS(keys + h, -1, key);
@@ -989,24 +993,23 @@ __device__ __forceinline__ void open_add(int *keys, unsigned *vals, int key, lon
       sadd64(vals + 6 * h + 4, Ss);
       return;
     }
-    h = (h + 1) & (OPEN_SLOTS - 1);
+    h = (h + 1) & (LOOP_SLOTS - 1);
   }
   unsigned long long *r = s.acc + 4 * (vb + key);
   atomicAdd(r, (unsigned long long)W);
   atomicAdd(r + 1, (unsigned long long)Cc);
   atomicAdd(r + 2, (unsigned long long)Ss);
+  set_bit(s.openroot, vb >> 5, key);
 }
 
 constexpr int TPB_EST = 512;
 
 template <int Q>
-__global__ void __launch_bounds__(TPB_EST, 3) k_est(const DevChain *__restrict__ ch,
+__global__ void __launch_bounds__(TPB_EST, 4) k_est(const DevChain *__restrict__ ch,
                                              const int2 *__restrict__ tab, int64_t blk0,
                                              Scratch s) {
-  extern __shared__ unsigned est_dyn[];  // closed loops' split sums, by root slot
-  unsigned *cW = est_dyn, *cC = est_dyn + 2 * SMEM_CAP, *cS = est_dyn + 4 * SMEM_CAP;
-  __shared__ int okeys[OPEN_SLOTS];
-  __shared__ unsigned ovals[6 * OPEN_SLOTS];
+  __shared__ int lkeys[LOOP_SLOTS];
+  __shared__ unsigned lvals[6 * LOOP_SLOTS];
   __shared__ int cvp[TILE + 1];
   __shared__ int cnew[TILE];
   __shared__ long long ccl[TILE], csl[TILE], ccr[TILE], csr[TILE], cxl[TILE], cxr[TILE];
@@ -1032,16 +1035,13 @@ __global__ void __launch_bounds__(TPB_EST, 3) k_est(const DevChain *__restrict__
     cxr[threadIdx.x] = (long long)s.cut_cross[C.sub_off + ur] * C.qbeta;
     cnew[threadIdx.x] = 0;
   }
-  __syncthreads();
-  const int a = cvp[0], e = cvp[ncl];
-  const int nv = min(e - a, SMEM_CAP);
-  for (int i = threadIdx.x; i < 2 * nv; i += blockDim.x) cW[i] = cC[i] = cS[i] = 0u;
-  for (int i = threadIdx.x; i < OPEN_SLOTS; i += blockDim.x) {
-    okeys[i] = -1;
+  for (int i = threadIdx.x; i < LOOP_SLOTS; i += blockDim.x) {
+    lkeys[i] = -1;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) ovals[6 * i + k] = 0u;
+    for (int k = 0; k < 6; ++k) lvals[6 * i + k] = 0u;
   }
   __syncthreads();
+  const int a = cvp[0], e = cvp[ncl];
   const int64_t vb = C.vtx_base, wb = vb >> 5;
   const int32_t *par = s.parent + vb;
   const uint64_t *vt = (const uint64_t *)s.vtau + vb;
@@ -1051,8 +1051,6 @@ __global__ void __launch_bounds__(TPB_EST, 3) k_est(const DevChain *__restrict__
   u128 w2 = 0, f2 = 0;  // this thread's share of sum W^2 and sum (C^2 + S^2)
   for (int w0 = a; w0 < e; w0 += blockDim.x) {
     const int w = w0 + threadIdx.x;
-    int key = -1;  // root of the loop the two fragments below w belong to
-    long long W = 0, Cc = 0, Ss = 0;
     if (w < e) {
       const int ci = s.vcell[vb + w];
       const int P = s.pl[vb + w], R = s.pr[vb + w];
@@ -1070,33 +1068,16 @@ __global__ void __launch_bounds__(TPB_EST, 3) k_est(const DevChain *__restrict__
       if (f & VF_WRAP_L) dl += cxl[ci];
       long long dr = qw - (R == P ? qP : q_time(vt[R], F));
       if (f & VF_WRAP_R) dr += cxr[ci];
-      W = dl + dr;
-      Cc = mul_q32(dl, ccl[ci]) + mul_q32(dr, ccr[ci]);
-      Ss = mul_q32(dl, csl[ci]) + mul_q32(dr, csr[ci]);
+      const long long W = dl + dr;
+      const long long Cc = mul_q32(dl, ccl[ci]) + mul_q32(dr, ccr[ci]);
+      const long long Ss = mul_q32(dl, csl[ci]) + mul_q32(dr, csr[ci]);
       if (P == R) {
         // Both upper legs of node P end at w, so P is a loop by itself and its
         // two fragments are the two below w: the loop's sums are complete here.
         w2 += sq_abs(W);
         f2 += sq_abs(Cc) + sq_abs(Ss);
       } else {
-        key = rb;
-      }
-    }
-    // Each lane adds its vertex's sums to its loop: loops are small (a warp
-    // sees about 26 different roots in 32 vertices), so lanes add directly and
-    // the rare collisions serialize in the atomic unit.
-    if (key >= 0) {
-      if (get_bit(s.openroot, wb, key)) {
-        open_add(okeys, ovals, key, W, Cc, Ss, s, vb);
-      } else {
-        const int li = key - a;
-        if (li < 0 || li >= nv) {
-          fail_check(s, 3, c0, w, key, a, nv);
-        } else {
-          sadd64(cW + 2 * li, W);
-          sadd64(cC + 2 * li, Cc);
-          sadd64(cS + 2 * li, Ss);
-        }
+        loop_add(lkeys, lvals, rb, W, Cc, Ss, s, vb);
       }
     }
     __syncwarp();
@@ -1109,22 +1090,22 @@ __global__ void __launch_bounds__(TPB_EST, 3) k_est(const DevChain *__restrict__
   }
   const int64_t tot = block_sum<int64_t>((int64_t)newcnt, sm);
   if (threadIdx.x == 0) s.tile_sum2[gt] = tot;
-  // Only loops closed in the tile (of more than one node) add to the shared
-  // accumulators, at their root's slot; every other slot stays zero.
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-    const unsigned long long x = sget64(cW + 2 * i), y = sget64(cC + 2 * i), z = sget64(cS + 2 * i);
-    if (x | y | z) {
+  // A loop closed in the tile is complete in its slot: square it here.  A loop
+  // that leaves the tile adds its slot to the root's global record, squared
+  // once every tile has added (next operator list kernel).
+  for (int h = threadIdx.x; h < LOOP_SLOTS; h += blockDim.x) {
+    const int kk = lkeys[h];
+    if (kk < 0) continue;
+    const unsigned long long x = sget64(lvals + 6 * h), y = sget64(lvals + 6 * h + 2),
+                             z = sget64(lvals + 6 * h + 4);
+    if (get_bit(s.openroot, wb, kk)) {
+      unsigned long long *r = s.acc + 4 * (vb + kk);
+      atomicAdd(r, x);
+      atomicAdd(r + 1, y);
+      atomicAdd(r + 2, z);
+    } else {
       w2 += sq_abs((long long)x);
       f2 += sq_abs((long long)y) + sq_abs((long long)z);
-    }
-  }
-  for (int h = threadIdx.x; h < OPEN_SLOTS; h += blockDim.x) {
-    const int kk = okeys[h];
-    if (kk >= 0) {
-      unsigned long long *r = s.acc + 4 * (vb + kk);
-      atomicAdd(r, sget64(ovals + 6 * h));
-      atomicAdd(r + 1, sget64(ovals + 6 * h + 2));
-      atomicAdd(r + 2, sget64(ovals + 6 * h + 4));
     }
   }
   w2 = block_sum_u128(w2);
@@ -1373,21 +1354,12 @@ void launch_compress(const Launch &L, cudaStream_t st) {
   if (n) k_compress<<<g1(n), TILE, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
 }
 
-constexpr size_t EST_DYN_SMEM = 6 * SMEM_CAP * sizeof(unsigned);
-
-int init_kernel_attributes() {
-  if (cudaFuncSetAttribute(k_est<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EST_DYN_SMEM) !=
-      cudaSuccess)
-    return -1;
-  if (cudaFuncSetAttribute(k_est<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EST_DYN_SMEM) !=
-      cudaSuccess)
-    return -1;
-  return 0;
-}
+// Kernel attributes set once per process (none needed at present).
+int init_kernel_attributes() { return 0; }
 
 void launch_est(const Launch &L, cudaStream_t st) {
-  if (L.ntile[0]) k_est<1><<<g1(L.ntile[0]), TPB_EST, EST_DYN_SMEM, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
-  if (L.ntile[1]) k_est<2><<<g1(L.ntile[1]), TPB_EST, EST_DYN_SMEM, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
+  if (L.ntile[0]) k_est<1><<<g1(L.ntile[0]), TPB_EST, 0, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
+  if (L.ntile[1]) k_est<2><<<g1(L.ntile[1]), TPB_EST, 0, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
 }
 
 void launch_compact(const Launch &L, cudaStream_t st) {
