@@ -89,6 +89,43 @@ __device__ u128 block_sum_u128(u128 v) {
   return t;
 }
 
+__device__ __forceinline__ u128 shfl_down_u128(u128 v, int o) {
+  const unsigned long long l = __shfl_down_sync(0xffffffffu, (unsigned long long)v, o);
+  const unsigned long long h = __shfl_down_sync(0xffffffffu, (unsigned long long)(v >> 64), o);
+  return ((u128)h << 64) | (u128)l;
+}
+
+// Exact block-wide sums of one int64 and two 128-bit values with a single
+// barrier; the totals are valid in thread 0.  Once per kernel.
+__device__ void block_sum3(long long &c, u128 &x, u128 &y) {
+  __shared__ long long pc[32];
+  __shared__ u128 px[32], py[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    c += __shfl_down_sync(0xffffffffu, c, o);
+    x += shfl_down_u128(x, o);
+    y += shfl_down_u128(y, o);
+  }
+  if (lane == 0) {
+    pc[wid] = c;
+    px[wid] = x;
+    py[wid] = y;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    c = lane < nw ? pc[lane] : 0;
+    x = lane < nw ? px[lane] : (u128)0;
+    y = lane < nw ? py[lane] : (u128)0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      c += __shfl_down_sync(0xffffffffu, c, o);
+      x += shfl_down_u128(x, o);
+      y += shfl_down_u128(y, o);
+    }
+  }
+}
+
 __device__ __forceinline__ bool halted(const Scratch &s) { return __ldcg(s.status) != 0; }
 
 // Tile blocks of the vertex-parallel kernels: TPB threads walk the tile's
@@ -549,23 +586,47 @@ __global__ void __launch_bounds__(TILE) k_insert(DevChain *__restrict__ ch,
 
 // ---- per-chain scan of the tiles' new-operator counts ------------------------------
 __global__ void __launch_bounds__(1024) k_scan_ops(DevChain *__restrict__ ch, Scratch s) {
+  // Chunks of 4 x 1024 tiles: each thread loads four consecutive counts
+  // (coalesced across the warp), one block scan per chunk; the next chunk's
+  // loads are issued before the current chunk's scan.
   __shared__ int64_t sm[33];
   if (halted(s)) return;
   DevChain &C = ch[blockIdx.x];
   const int nt = C.ntile;
-  const int per = (nt + blockDim.x - 1) / blockDim.x;
-  const int lo = min(nt, (int)threadIdx.x * per), hi = min(nt, lo + per);
-  int64_t sum = 0;
-  for (int i = lo; i < hi; ++i) sum += s.tile_sum2[C.tile0 + i];
-  int64_t total;
-  int64_t run = block_excl_scan<int64_t>(sum, sm, total);
-  for (int i = lo; i < hi; ++i) {
-    s.tile_pref2[C.tile0 + i] = run;
-    run += s.tile_sum2[C.tile0 + i];
+  const int64_t *cnt = s.tile_sum2 + C.tile0;
+  int64_t *pref = s.tile_pref2 + C.tile0;
+  constexpr int V = 4;
+  const int chunk = V * (int)blockDim.x;
+  int64_t v[V], nx[V];
+  auto load = [&](int base, int64_t *x) {
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const int i = base + V * (int)threadIdx.x + k;
+      x[k] = (i < nt) ? cnt[i] : 0;
+    }
+  };
+  load(0, v);
+  int64_t run = 0;
+  for (int base = 0; base < nt; base += chunk) {
+    if (base + chunk < nt) load(base + chunk, nx);
+    int64_t mine = 0;
+#pragma unroll
+    for (int k = 0; k < V; ++k) mine += v[k];
+    int64_t total;
+    int64_t ex = run + block_excl_scan<int64_t>(mine, sm, total);
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const int i = base + V * (int)threadIdx.x + k;
+      if (i < nt) pref[i] = ex;
+      ex += v[k];
+    }
+    run += total;
+#pragma unroll
+    for (int k = 0; k < V; ++k) v[k] = nx[k];
   }
   if (threadIdx.x == 0) {
-    C.n_off_new = total;
-    if (total > C.op_cap) atomicOr(s.status, ST_OP_OVERFLOW);
+    C.n_off_new = run;
+    if (run > C.op_cap) atomicOr(s.status, ST_OP_OVERFLOW);
   }
 }
 
@@ -1013,7 +1074,6 @@ __global__ void __launch_bounds__(TPB_EST, 4) k_est(const DevChain *__restrict__
   __shared__ int cvp[TILE + 1];
   __shared__ int cnew[TILE];
   __shared__ long long ccl[TILE], csl[TILE], ccr[TILE], csr[TILE], cxl[TILE], cxr[TILE];
-  __shared__ int64_t sm[33];
   if (halted(s)) return;
   const int64_t gt = blk0 + blockIdx.x;
   const int2 t = tab[gt];
@@ -1083,13 +1143,11 @@ __global__ void __launch_bounds__(TPB_EST, 4) k_est(const DevChain *__restrict__
     __syncwarp();
   }
   __syncthreads();
-  int newcnt = 0;
+  long long newcnt = 0;
   if (threadIdx.x < ncl) {
     newcnt = cnew[threadIdx.x];
-    C.op_ptr[C.cur ^ 1][c0 + threadIdx.x] = newcnt;
+    C.op_ptr[C.cur ^ 1][c0 + threadIdx.x] = (int32_t)newcnt;
   }
-  const int64_t tot = block_sum<int64_t>((int64_t)newcnt, sm);
-  if (threadIdx.x == 0) s.tile_sum2[gt] = tot;
   // A loop closed in the tile is complete in its slot: square it here.  A loop
   // that leaves the tile adds its slot to the root's global record, squared
   // once every tile has added (next operator list kernel).
@@ -1108,9 +1166,9 @@ __global__ void __launch_bounds__(TPB_EST, 4) k_est(const DevChain *__restrict__
       f2 += sq_abs((long long)y) + sq_abs((long long)z);
     }
   }
-  w2 = block_sum_u128(w2);
-  f2 = block_sum_u128(f2);
+  block_sum3(newcnt, w2, f2);
   if (threadIdx.x == 0) {
+    s.tile_sum2[gt] = newcnt;
     s.tile_sw2[2 * gt] = (unsigned long long)w2;
     s.tile_sw2[2 * gt + 1] = (unsigned long long)(w2 >> 64);
     s.tile_sf2[2 * gt] = (unsigned long long)f2;
@@ -1119,12 +1177,16 @@ __global__ void __launch_bounds__(TPB_EST, 4) k_est(const DevChain *__restrict__
 }
 
 // ---- next operator list + open loops -------------------------------------------------
-// Cell offsets from a block scan of the per-cell counts; vertex positions from
-// a chunked block scan of the new-operator flags in id order (the same order).
+// The tile's flags are read as aligned 32-bit words (four vertices each).
+// Each warp takes a contiguous range of words: a first pass counts its new
+// operators, one barrier exchanges the warp totals, and a second pass places
+// them with warp shuffles (id order = order of the next operator list).  The
+// cell offsets come from a block scan of the per-cell counts.
 __global__ void __launch_bounds__(TPB) k_compact(const DevChain *__restrict__ ch,
                                                  const int2 *__restrict__ tab, int64_t blk0,
                                                  Scratch s) {
   __shared__ int64_t sm[33];
+  __shared__ int wtot[TPB / 32];
   if (halted(s)) return;
   const int64_t gt = blk0 + blockIdx.x;
   const int2 t = tab[gt];
@@ -1135,37 +1197,54 @@ __global__ void __launch_bounds__(TPB) k_compact(const DevChain *__restrict__ ch
   const int32_t *vp = s.vptr + C.cell_off;
   const int64_t vb = C.vtx_base;
   const int64_t base = s.tile_pref2[gt];
+  const int a = vp[c0], e = vp[c1];
+  const uint8_t *vf = s.vflag + vb;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = TPB / 32;
+  // words [wa, we) of four flags; warp wid takes [wa + wid*per, ...)
+  const int wa = a >> 2, we = (e + 3) >> 2;
+  const int per = (we - wa + nw - 1) / nw;
+  const int ww0 = min(we, wa + wid * per), ww1 = min(we, ww0 + per);
+  auto newmask = [&](int wd) {  // bit i: vertex 4*wd + i is a new operator of this tile
+    const uint32_t fl = *(const uint32_t *)(vf + 4 * wd);  // vb and 4*wd are multiples of 4
+    int m = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int w = 4 * wd + i;
+      if (w >= a && w < e && ((fl >> (8 * i)) & VF_NEW)) m |= 1 << i;
+    }
+    return m;
+  };
+  int cnt = 0;
+  for (int wd = ww0 + lane; wd < ww1; wd += 32) cnt += __popc(newmask(wd));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0) wtot[wid] = cnt;
   {
-    const int cnt = (threadIdx.x < ncl) ? nptr[c0 + threadIdx.x] : 0;
+    const int cc = (threadIdx.x < ncl) ? nptr[c0 + threadIdx.x] : 0;
     int64_t tot;
-    const int64_t ex = block_excl_scan<int64_t>((int64_t)cnt, sm, tot);
+    const int64_t ex = block_excl_scan<int64_t>((int64_t)cc, sm, tot);  // also publishes wtot
     if (threadIdx.x < ncl) {
       nptr[c0 + threadIdx.x] = (int32_t)(base + ex);
       if (c0 + (int)threadIdx.x == C.ncell - 1) nptr[C.ncell] = (int32_t)C.n_off_new;
     }
   }
-  const int a = vp[c0], e = vp[c1];
-  // New operators in vertex order: four flags per thread per step (one aligned
-  // 32-bit load), one block scan per 4*TPB vertices.
-  const uint8_t *vf = s.vflag + vb;
-  int64_t run = base;
-  for (int g0 = a & ~3; g0 < e; g0 += 4 * (int)blockDim.x) {
-    const int w0 = g0 + 4 * (int)threadIdx.x;
-    uint32_t fl = 0;
-    if (w0 < e) fl = *(const uint32_t *)(vf + w0);  // vb and w0 are multiples of 4
-    int m = 0;
+  int64_t pos = base;
+  for (int k = 0; k < wid; ++k) pos += wtot[k];
+  for (int s0 = ww0; s0 < ww1; s0 += 32) {
+    const int wd = s0 + lane;
+    const int m = (wd < ww1) ? newmask(wd) : 0;
+    const int c = __popc(m);
+    int inc = c;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int w = w0 + i;
-      if (w >= a && w < e && ((fl >> (8 * i)) & VF_NEW)) m |= 1 << i;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
     }
-    int64_t tot;
-    const int64_t ex = block_excl_scan<int64_t>((int64_t)__popc(m), sm, tot);
-    int64_t pos = run + ex;
+    int64_t p = pos + inc - c;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-      if (m & (1 << i)) ntau[pos++] = s.vtau[vb + w0 + i];
-    run += tot;
+      if (m & (1 << i)) ntau[p++] = s.vtau[vb + 4 * wd + i];
+    pos += __shfl_sync(0xffffffffu, inc, 31);
   }
   // Loops that left their tile: one 32-byte accumulator record per root, read
   // and cleared; a thread takes one 32-vertex word of the open-root bitmap.
@@ -1187,8 +1266,8 @@ __global__ void __launch_bounds__(TPB) k_compact(const DevChain *__restrict__ ch
       f2 += sq_abs((long long)x.y) + sq_abs((long long)y.x);
     }
   }
-  w2 = block_sum_u128(w2);
-  f2 = block_sum_u128(f2);
+  long long none = 0;
+  block_sum3(none, w2, f2);
   if (threadIdx.x == 0) {
     u128 x = ((u128)s.tile_sw2[2 * gt + 1] << 64) | s.tile_sw2[2 * gt];
     u128 y = ((u128)s.tile_sf2[2 * gt + 1] << 64) | s.tile_sf2[2 * gt];
@@ -1252,12 +1331,13 @@ __global__ void __launch_bounds__(SITE_BLOCK) k_sites(const DevChain *__restrict
 }
 
 // ---- per-chain record -----------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_final(DevChain *__restrict__ ch, Scratch s) {
+__global__ void __launch_bounds__(1024) k_final(DevChain *__restrict__ ch, Scratch s) {
   __shared__ int64_t sm[33];
   if (halted(s)) return;
   DevChain &C = ch[blockIdx.x];
   int64_t roots = 0, nfree = 0;
   u128 w2 = 0, f2 = 0;
+#pragma unroll 4
   for (int i = threadIdx.x; i < C.ntile; i += blockDim.x) {
     const int64_t g = C.tile0 + i;
     roots += s.tile_roots[g];
@@ -1373,7 +1453,7 @@ void launch_sites(const Launch &L, cudaStream_t st) {
 }
 
 void launch_final(const Launch &L, cudaStream_t st) {
-  k_final<<<L.nchains, 256, 0, st>>>(L.ch, L.s);
+  k_final<<<L.nchains, 1024, 0, st>>>(L.ch, L.s);
 }
 
 }  // namespace lcq
