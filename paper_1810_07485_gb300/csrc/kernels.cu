@@ -786,13 +786,13 @@ __device__ __forceinline__ void suf_union(int *lp, int a, int b, int bound, int 
   atomicOr(status, ST_TIMEOUT);
 }
 
-// First index q in [lo, hi) whose key (tau, id) is not below (tw, w).
-__device__ __forceinline__ int key_lower_bound(const long long *vt, int lo, int hi, long long tw,
-                                               int w) {
+// First index q in [lo, hi) with vt[q] >= thr.  For a neighbour cell, whose
+// ids are all below w or all above it, "key (tau, id) below (tw, w)" is
+// vt[q] < tw + 1 or vt[q] < tw respectively.
+__device__ __forceinline__ int time_lower_bound(const long long *vt, int lo, int hi, long long thr) {
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    const long long tq = vt[mid];
-    if (tq < tw || (tq == tw && mid < w))
+    if (vt[mid] < thr)
       lo = mid + 1;
     else
       hi = mid;
@@ -879,7 +879,7 @@ __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
       }
 #pragma unroll
       for (int k = 0; k < LinkCell<Q>::NO; ++k) {
-        const int q = key_lower_bound(vt, L.wa[sd][k], L.we[sd][k], tw, w);
+        const int q = time_lower_bound(vt, L.wa[sd][k], L.we[sd][k], tw + (L.wa[sd][k] < w ? 1 : 0));
         const int cand = (q > L.wa[sd][k]) ? q - 1 : L.bj[sd][k];
         if (cand >= 0) {
           const long long tc = vt[cand];
@@ -934,16 +934,20 @@ __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
 }
 
 // Global unions of the edges that leave their tile (all edges of a tile too
-// large for shared memory), on the forests the tiles stored.  A tile has about
-// 45 words of marks, so small blocks (one thread per word) keep many tiles in
-// flight: the unions are chains of dependent global loads.
-constexpr int TPB_X = 64;
+// large for shared memory), on the forests the tiles stored.  One warp per
+// tile, eight tiles per block: a tile has about 45 words of marks, and the
+// unions are chains of dependent global loads, so many tiles are kept in
+// flight.
+constexpr int TPB_X = 256;
 
 __global__ void __launch_bounds__(TPB_X) k_link_x(const DevChain *__restrict__ ch,
-                                                const int2 *__restrict__ tab, int64_t blk0,
+                                                const int2 *__restrict__ tab, int64_t ntiles,
                                                 Scratch s) {
   if (halted(s)) return;
-  const int2 t = tab[blk0 + blockIdx.x];
+  const int lane = threadIdx.x & 31;
+  const int64_t gt = (int64_t)blockIdx.x * (TPB_X / 32) + (threadIdx.x >> 5);
+  if (gt >= ntiles) return;
+  const int2 t = tab[gt];
   const DevChain &C = ch[t.x];
   const int c0 = t.y * TILE, c1 = min(C.ncell, c0 + TILE);
   const int32_t *vp = s.vptr + C.cell_off;
@@ -952,13 +956,11 @@ __global__ void __launch_bounds__(TPB_X) k_link_x(const DevChain *__restrict__ c
   const int64_t vb = C.vtx_base;
   int32_t *par = s.parent + vb;
   if (!local) {
-    for (int w = a + threadIdx.x; w < e; w += blockDim.x)
-      uf_union(par, s.pl[vb + w], s.pr[vb + w], s.status);
+    for (int w = a + lane; w < e; w += 32) uf_union(par, s.pl[vb + w], s.pr[vb + w], s.status);
     return;
   }
-  // one 32-vertex word of the mark bitmap per thread
   const int64_t wfirst = (vb + a) >> 5, wlast = (vb + e - 1) >> 5;
-  for (int64_t wd = wfirst + threadIdx.x; e > a && wd <= wlast; wd += blockDim.x) {
+  for (int64_t wd = wfirst + lane; e > a && wd <= wlast; wd += 32) {
     uint32_t bits = __ldcg(s.xmark + wd);
     const int64_t v0 = (wd << 5) - vb;
     if (v0 < a) bits &= ~0u << (a - v0);
@@ -1426,7 +1428,7 @@ void launch_link(const Launch &L, cudaStream_t st) {
   if (L.ntile[0]) k_link<1><<<g1(L.ntile[0]), TPB, 0, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
   if (L.ntile[1]) k_link<2><<<g1(L.ntile[1]), TPB, 0, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
   const int64_t n = L.ntile[0] + L.ntile[1];
-  if (n) k_link_x<<<g1(n), TPB_X, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
+  if (n) k_link_x<<<g1((n + TPB_X / 32 - 1) / (TPB_X / 32)), TPB_X, 0, st>>>(L.ch, L.tile_tab, n, L.s);
 }
 
 void launch_compress(const Launch &L, cudaStream_t st) {
