@@ -300,29 +300,19 @@ __device__ __forceinline__ int ops_before(const long long *__restrict__ tq, int 
   return lo - base;
 }
 
+// Time of a candidate, tau = fma(d, u53 2^-53, t0) (one IEEE fused
+// multiply-add), and whether it is kept: the bond's spins antiparallel at tau
+// (parity at the window start flipped by the neighbour operators before tau).
 template <int Q>
-__device__ __forceinline__ void ins_decide(InsSmem<Q> &S, const long long *otau, int c, int slot,
+__device__ __forceinline__ bool ins_decide(const long long *otau, const NbOps<Q> &X, int b, int par0,
                                            uint64_t u53, double t0, double d, long long teb,
-                                           bool count) {
-  // tau = fma(d, u53 2^-53, t0), one IEEE fused multiply-add
-  const long long tau =
-      __double_as_longlong(__fma_rn(d, __longlong_as_double((long long)unit_bits(u53)), t0));
-  bool keep = tau < teb;
-  if (keep) {
-    const NbOps<Q> &X = S.X[c];
-    const int b = S.b[c];
-    int p = S.par0[c];
+                                           long long &tau) {
+  tau = __double_as_longlong(__fma_rn(d, __longlong_as_double((long long)unit_bits(u53)), t0));
+  if (!(tau < teb)) return false;
+  int p = par0;
 #pragma unroll
-    for (int k = 0; k < NbOps<Q>::N; ++k) p ^= ops_before(otau, X.o0[k], X.o1[k], tau, X.bond[k], b);
-    keep = p & 1;
-  }
-  S.key[slot] = keep ? u53 : (u53 | KEY_DROP);
-  S.tau[slot] = keep ? tau : LLONG_MAX;
-  S.scell[slot] = (uint8_t)c;
-  if (keep) {
-    S.klist[atomicAdd(&S.nkept, 1)] = (short)slot;
-    if (count) atomicAdd(&S.nk[c], 1);
-  }
+  for (int k = 0; k < NbOps<Q>::N; ++k) p ^= ops_before(otau, X.o0[k], X.o1[k], tau, X.bond[k], b);
+  return p & 1;
 }
 
 // Draw and decide the candidates of the cells of group g.
@@ -338,27 +328,51 @@ __device__ void ins_draw(const DevChain &C, InsSmem<Q> &S, const long long *otau
   }
   __syncthreads();
   const uint32_t k0 = (uint32_t)C.seed, k1 = (uint32_t)(C.seed >> 32);
+  const int lane = threadIdx.x & 31;
   for (int u0 = 0; u0 < nu; u0 += TILE) {  // whole warps, reconverged per step
     const int u = u0 + threadIdx.x;
-    if (u >= nu) {
-      __syncwarp();
-      continue;
+    bool kp[2] = {false, false};
+    int sl[2] = {0, 0}, c = 0;
+    if (u < nu) {
+      c = S.ucell[u];
+      const int m = u + ub - S.upre[c];
+      const int j = S.j[c], K = S.K[c], ks = S.kpre[c] - kb, b = S.b[c], par0 = S.par0[c];
+      const NbOps<Q> X = S.X[c];
+      const double t0 = __longlong_as_double((long long)C.win[3 * j]);
+      const long long teb = (long long)C.win[3 * j + 1];
+      const double d = __longlong_as_double((long long)C.win[3 * j + 2]);
+      const U4 o = philox((TAG_INSERT << 24) | (uint32_t)m, (uint32_t)b, (uint32_t)j, C.sweep, k0, k1);
+      // words (x, y): candidate 2m-1 (for m = 0 the count); words (z, w): candidate 2m
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 2 * m - 1 + h;
+        if (k < 0 || k >= K) continue;
+        const uint64_t u53 = (h ? ((uint64_t)o.z | ((uint64_t)o.w << 32))
+                                : ((uint64_t)o.x | ((uint64_t)o.y << 32))) >> 11;
+        long long tau;
+        const bool keep = ins_decide<Q>(otau, X, b, par0, u53, t0, d, teb, tau);
+        const int slot = ks + k;
+        S.key[slot] = keep ? u53 : (u53 | KEY_DROP);
+        S.tau[slot] = keep ? tau : LLONG_MAX;
+        S.scell[slot] = (uint8_t)c;
+        kp[h] = keep;
+        sl[h] = slot;
+      }
     }
-    const int c = S.ucell[u];
-    const int m = u + ub - S.upre[c];
-    const int j = S.j[c], K = S.K[c], ks = S.kpre[c] - kb;
-    const double t0 = __longlong_as_double((long long)C.win[3 * j]);
-    const long long teb = (long long)C.win[3 * j + 1];
-    const double d = __longlong_as_double((long long)C.win[3 * j + 2]);
-    const U4 o = philox((TAG_INSERT << 24) | (uint32_t)m, (uint32_t)S.b[c], (uint32_t)j, C.sweep, k0, k1);
-    // words (x, y): candidate 2m-1 (for m = 0 the count); words (z, w): candidate 2m
+    // kept list: one shared atomic per warp and half
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int k = 2 * m - 1 + h;
-      if (k < 0 || k >= K) continue;
-      const uint64_t u53 = (h ? ((uint64_t)o.z | ((uint64_t)o.w << 32))
-                              : ((uint64_t)o.x | ((uint64_t)o.y << 32))) >> 11;
-      ins_decide<Q>(S, otau, c, ks + k, u53, t0, d, teb, count);
+      const unsigned km = __ballot_sync(0xffffffffu, kp[h]);
+      if (km) {
+        const int leader = __ffs(km) - 1;
+        int at = 0;
+        if (lane == leader) at = atomicAdd(&S.nkept, __popc(km));
+        at = __shfl_sync(0xffffffffu, at, leader);
+        if (kp[h]) {
+          S.klist[at + __popc(km & ((1u << lane) - 1u))] = (short)sl[h];
+          if (count) atomicAdd(&S.nk[c], 1);
+        }
+      }
     }
     __syncwarp();
   }
