@@ -49,7 +49,7 @@ extern "C" {
 #define LCQMC_E_INVAL (-1)          /* bad argument: L < 2 or odd, beta <= 0, J <= 0, 2S not 1 or 2 */
 #define LCQMC_E_NOMEM (-2)          /* device or host allocation failed */
 #define LCQMC_E_TOO_LARGE (-3)      /* footprint above the budget / the server's HBM budget */
-#define LCQMC_E_ID_OVERFLOW (-4)    /* more than 2^31-1 graph vertices or cells in one chain */
+#define LCQMC_E_ID_OVERFLOW (-4)    /* more than 2^31-4096 graph vertices, or 2^31 cells, in one chain */
 #define LCQMC_E_DEVICE_TIMEOUT (-5) /* a bounded device wait (union-find retry) ran out */
 #define LCQMC_E_CUDA (-6)           /* a CUDA runtime call failed */
 #define LCQMC_E_STATE (-7)          /* imported configuration is not a valid world-line state */

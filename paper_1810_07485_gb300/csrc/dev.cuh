@@ -11,6 +11,7 @@ namespace lcq {
 
 constexpr int KMAX = 48;          // Poisson count table length (K <= KMAX-1)
 constexpr int TW = LCQMC_TW;      // windows per time block of the cell order
+constexpr int64_t VTX_ID_LIMIT = 0x7ffff000;  // largest vertex count of one chain
 constexpr int TILE = 128;         // cells per tile (one thread block)
 constexpr int SMEM_CAP = 2048;    // vertices a tile can accumulate in shared memory
 constexpr int MAX_COIN_GROUPS = 64;
@@ -36,7 +37,8 @@ enum : uint8_t { VF_OLD = 1, VF_WRAP_L = 2, VF_WRAP_R = 4, VF_NEW = 8 };
 
 struct DevChain {
   // geometry
-  int32_t L, Q, nsub, nbond, nwin, nblk, ncell, ntile, nsiteblk, F, ring_cap, pad0;
+  int32_t L, Q, nsub, nbond, nwin, nblk, ncell, ntile, nsiteblk, F, ring_cap;
+  int32_t ins_span;  // candidate slots per insertion group (0: the default)
   double beta, J, w;
   uint64_t seed;
   // tables

@@ -2,6 +2,7 @@
 // per-update launch sequence (captured once as a CUDA graph), capacity growth
 // with replay, and state import / export.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -414,6 +415,10 @@ int Engine::layout() {
       d.sub_off = sub_off;
       if (cs_[c]->vcap <= 0) cs_[c]->vcap = (vertex_estimate(cs_[c]->spec) + 127) / 128 * 128;
       d.vcap = cs_[c]->vcap;
+      // Test hook: a smaller candidate staging group, so that every tile of
+      // insertion takes the multi-group path (count, then draw again to write).
+      d.ins_span = 0;
+      if (const char *e = std::getenv("LCQMC_INSERT_GROUP_SLOTS")) d.ins_span = std::atoi(e);
       cell_off += g.ncell + 1;
       bpar_off += (g.nblk + 1) * g.nbond;
       sub_off += g.nsub;
@@ -668,7 +673,7 @@ int Engine::sync() {
         return LCQMC_E_DEVICE_TIMEOUT;
       }
       if (status & ST_ID_OVERFLOW) {
-        set_error("more than 2^31 graph vertices in one chain");
+        set_error("more than 2^31 - 4096 graph vertices in one chain");
         return LCQMC_E_ID_OVERFLOW;
       }
       if (status & ST_BADSTATE) {

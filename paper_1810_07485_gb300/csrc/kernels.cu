@@ -137,7 +137,7 @@ __device__ __forceinline__ int tile_cell_of(const int *cvp, int ncl, int w) {
   // largest i in [0, ncl) with cvp[i] <= w
   int lo = 0, hi = ncl - 1;
   while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
+    const int mid = lo + ((hi - lo + 1) >> 1);
     if (cvp[mid] <= w)
       lo = mid;
     else
@@ -260,7 +260,8 @@ __device__ int64_t lb_lookback(unsigned long long *st, int64_t g, int64_t first,
 constexpr int INS_CAP = 1280;
 constexpr int INS_SPAN = INS_CAP - KMAX;  // a group's cells start within INS_SPAN slots
 constexpr int INS_UCAP = INS_CAP / 2 + TILE;
-constexpr int INS_MAXG = (TILE * (KMAX - 1)) / INS_SPAN + 2;
+constexpr int INS_MIN_SPAN = 256;  // smallest group span a chain may ask for (tests)
+constexpr int INS_MAXG = (TILE * (KMAX - 1)) / INS_MIN_SPAN + 2;
 constexpr int INS_OPCAP = 2048;  // old operators of a group mapped to their cell
 constexpr unsigned long long KEY_DROP = 1ull << 63;
 
@@ -291,7 +292,7 @@ __device__ __forceinline__ int ops_before(const long long *__restrict__ tq, int 
   const long long thr = tau + (bb < b ? 1 : 0);  // t < thr  <=>  (t, bb) < (tau, b)
   const int base = lo;
   while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
+    const int mid = lo + ((hi - lo) >> 1);  // no overflow near 2^31
     if (tq[mid] < thr)
       lo = mid + 1;
     else
@@ -410,7 +411,7 @@ __device__ void ins_write(const DevChain &C, InsSmem<Q> &S, const long long *ota
     int lo = S.q[c], hi = S.q[c + 1];
     const int q0 = lo;
     while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
+      const int mid = lo + ((hi - lo) >> 1);  // no overflow near 2^31
       if (otau[mid] <= tau)
         lo = mid + 1;
       else
@@ -437,7 +438,7 @@ __device__ void ins_write(const DevChain &C, InsSmem<Q> &S, const long long *ota
     } else {
       int lo = c0, hi = c1 - 1;  // largest c in [c0, c1) with S.q[c] <= q
       while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
+        const int mid = lo + ((hi - lo + 1) >> 1);
         if (S.q[mid] <= q)
           lo = mid;
         else
@@ -546,8 +547,10 @@ __global__ void __launch_bounds__(TILE) k_insert(DevChain *__restrict__ ch,
   }
   __syncthreads();
   {
-    const int gc = S.kpre[c] / INS_SPAN;
-    if (c == 0 || gc != S.kpre[c - 1] / INS_SPAN) S.gfirst[gc] = c;
+    const int span =
+        (C.ins_span >= INS_MIN_SPAN && C.ins_span < INS_SPAN) ? C.ins_span : INS_SPAN;
+    const int gc = S.kpre[c] / span;
+    if (c == 0 || gc != S.kpre[c - 1] / span) S.gfirst[gc] = c;
     if (c == TILE - 1) {
       S.G = gc + 1;
       S.gfirst[gc + 1] = TILE;
@@ -578,7 +581,9 @@ __global__ void __launch_bounds__(TILE) k_insert(DevChain *__restrict__ ch,
       if (t.y == C.ntile - 1) {
         C.n = excl + ctot;
         if (excl + ctot > C.vcap) atomicOr(s.status, ST_VTX_OVERFLOW);
-        if (excl + ctot > (int64_t)0x7fffff00) atomicOr(s.status, ST_ID_OVERFLOW);
+        // vertex ids are int32 and per-tile loops step past the last id by
+        // up to a block: keep every id below 2^31 - 4096
+        if (excl + ctot > (int64_t)VTX_ID_LIMIT) atomicOr(s.status, ST_ID_OVERFLOW);
       }
     }
   }
@@ -805,7 +810,7 @@ __device__ __forceinline__ void suf_union(int *lp, int a, int b, int bound, int 
 // vt[q] < tw + 1 or vt[q] < tw respectively.
 __device__ __forceinline__ int time_lower_bound(const long long *vt, int lo, int hi, long long thr) {
   while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
+    const int mid = lo + ((hi - lo) >> 1);  // no overflow near 2^31
     if (vt[mid] < thr)
       lo = mid + 1;
     else
@@ -1090,6 +1095,7 @@ __global__ void __launch_bounds__(TPB_EST, 4) k_est(const DevChain *__restrict__
   __shared__ int cvp[TILE + 1];
   __shared__ int cnew[TILE];
   __shared__ long long ccl[TILE], csl[TILE], ccr[TILE], csr[TILE], cxl[TILE], cxr[TILE];
+  __shared__ long long qv[SMEM_CAP];  // ticks q(tau) of the tile's vertices
   if (halted(s)) return;
   const int64_t gt = blk0 + blockIdx.x;
   const int2 t = tab[gt];
@@ -1122,6 +1128,12 @@ __global__ void __launch_bounds__(TPB_EST, 4) k_est(const DevChain *__restrict__
   const int32_t *par = s.parent + vb;
   const uint64_t *vt = (const uint64_t *)s.vtau + vb;
   const int F = C.F;
+  // Ticks of every vertex of the tile, once: the fragments below a vertex
+  // mostly start at vertices of the same tile.
+  const int nq = min(e - a, SMEM_CAP);
+  for (int i = threadIdx.x; i < nq; i += blockDim.x) qv[i] = q_time(vt[a + i], F);
+  __syncthreads();
+  auto ticks = [&](int v) { return (v >= a && v < a + nq) ? qv[v - a] : q_time(vt[v], F); };
   // Whole warps walk the tile (trip count rounded up), reconverging after
   // every vertex.
   u128 w2 = 0, f2 = 0;  // this thread's share of sum W^2 and sum (C^2 + S^2)
@@ -1138,11 +1150,11 @@ __global__ void __launch_bounds__(TPB_EST, 4) k_est(const DevChain *__restrict__
       s.vflag[vb + w] = (uint8_t)(f | (nf ? VF_NEW : 0));
       if (nf) atomicAdd(cnew + ci, 1);
       // fragment lengths in ticks of 2^-F: q(tau_top) - q(tau_bottom) (+ crossings)
-      const long long qw = q_time(vt[w], F);
-      const long long qP = q_time(vt[P], F);
+      const long long qw = ticks(w);
+      const long long qP = ticks(P);
       long long dl = qw - qP;
       if (f & VF_WRAP_L) dl += cxl[ci];
-      long long dr = qw - (R == P ? qP : q_time(vt[R], F));
+      long long dr = qw - (R == P ? qP : ticks(R));
       if (f & VF_WRAP_R) dr += cxr[ci];
       const long long W = dl + dr;
       const long long Cc = mul_q32(dl, ccl[ci]) + mul_q32(dr, ccr[ci]);

@@ -96,6 +96,14 @@ def test_update_parity(L, beta, Q, J):
     run_parity(L, beta, Q=Q, J=J, seed=1000 + L, nup=10)
 
 
+@pytest.mark.parametrize("L,beta,Q", [(250, 70.0, 1), (1024, 40.0, 1), (16, 20.0, 2)])
+def test_update_parity_grouped_insertion(monkeypatch, L, beta, Q):
+    # Candidate staging in groups of 256 slots: every tile (about 1024
+    # candidates) counts group by group, then draws each group again to write.
+    monkeypatch.setenv("LCQMC_INSERT_GROUP_SLOTS", "256")
+    run_parity(L, beta, Q=Q, seed=77 + L, nup=6)
+
+
 def test_long_run_parity():
     # 300 chained updates: states stay identical throughout.
     run_parity(32, 24.0, nup=300, graph_every=50, seed=5)
