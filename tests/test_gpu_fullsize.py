@@ -107,3 +107,28 @@ def test_fullsize(L, beta, warm, full):
         s1, ptr1, tau1 = ch.export_config()
         _check_worldlines(L, s1, ptr1, tau1, nwin)
     ch.close()
+
+
+def test_vertex_ids_above_2_30():
+    # L=2^15, beta=2^16: the first update from the Neel state keeps every
+    # candidate, about 2^30 vertices, and the next ones about 1.3e9, so ids
+    # above 2^30 go through every search and union (a 32-bit midpoint
+    # lo + hi overflowed there).  Sampled partition checks on the exported
+    # links and roots.
+    from paper_1810_07485_gb300 import lcqmc
+    L, beta = 1 << 15, float(1 << 16)
+    ch = lcqmc.Chain(L, beta, seed=2)
+    ch.update(2)
+    ch.sync()
+    rec = ch.records()[-1]
+    assert rec["n"] > (1 << 30)
+    assert rec["n_seg"] == 2 * rec["n"] + rec["n_free"]
+    g = ch.export_graph(fields=("pl", "pr", "root"))
+    rng = np.random.default_rng(1)
+    _check_partition_sampled(g, rng)
+    # the top of the id range in particular
+    n = len(g["root"])
+    w = np.arange(n - 1_000_000, n)
+    assert np.all(g["root"][g["pl"][w]] == g["root"][g["pr"][w]])
+    assert np.all(g["root"][w] <= w)
+    ch.close()
