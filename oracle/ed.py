@@ -68,7 +68,14 @@ def spectrum(L, S=0.5, J=1.0):
 
 
 def thermal(L, beta, S=0.5, J=1.0, sectors=None):
-    """E/L, chi(pi), chi(pi + 2 pi / L) at inverse temperature beta."""
+    """E/L, chi(pi), chi(pi + 2 pi / L) and chi(pi, w1), w1 = 2 pi / beta, at
+    inverse temperature beta.
+
+    chi(q, w) = (1/(L Z)) sum_mn |<m|M_q|n>|^2 (e^{-beta E_n} - e^{-beta E_m})
+                (E_m - E_n) / ((E_m - E_n)^2 + w^2)
+    (the Fourier transform over [0, beta) of <M_q(t) M_q(0)> / L at Matsubara
+    frequency w; degenerate pairs contribute beta e^{-beta E_n} at w = 0 and
+    nothing otherwise)."""
     if sectors is None:
         sectors = spectrum(L, S, J)
     Emin = min(E.min() for E, _, _ in sectors)
@@ -76,7 +83,8 @@ def thermal(L, beta, S=0.5, J=1.0, sectors=None):
     Eavg = sum((E * np.exp(-beta * (E - Emin))).sum() for E, _, _ in sectors) / Z
     x = np.arange(L)
     out = {"energy": Eavg / L}
-    for name, q in (("chi_s", np.pi), ("chi_q", np.pi + 2 * np.pi / L)):
+    w1 = 2 * np.pi / beta
+    for name, q, w in (("chi_s", np.pi, 0.0), ("chi_q", np.pi + 2 * np.pi / L, 0.0), ("chi_w", np.pi, w1)):
         phase = np.exp(1j * q * x)
         tot = 0.0
         for E, V, szs in sectors:
@@ -89,8 +97,12 @@ def thermal(L, beta, S=0.5, J=1.0, sectors=None):
             dE = Em - En
             wn = np.exp(-beta * En)
             with np.errstate(over="ignore", invalid="ignore", divide="ignore"):
-                K = np.where(np.abs(dE) > 1e-12, wn * (-np.expm1(-beta * dE)) / np.where(dE == 0, 1, dE),
-                             beta * wn)
+                if w == 0.0:
+                    K = np.where(np.abs(dE) > 1e-12, wn * (-np.expm1(-beta * dE)) / np.where(dE == 0, 1, dE),
+                                 beta * wn)
+                else:
+                    K = np.where(np.abs(dE) > 1e-12, wn * (-np.expm1(-beta * dE)) * dE / (dE * dE + w * w),
+                                 0.0)
             tot += float((A2 * K).sum())
         out[name] = tot / (L * Z)
     return out
@@ -101,7 +113,11 @@ def dimer_closed_form(beta, J=1.0):
     Z = np.exp(1.5 * beta * J) + 3 * np.exp(-0.5 * beta * J)
     E = (-1.5 * J * np.exp(1.5 * beta * J) + 1.5 * J * np.exp(-0.5 * beta * J)) / Z
     chi_s = (np.exp(1.5 * beta * J) - np.exp(-0.5 * beta * J)) / (2 * Z * J)
-    return {"energy": E / 2, "chi_s": chi_s}
+    # M_pi = S1z - S2z joins the singlet and the triplet m=0 (matrix element 1,
+    # gap 2J): chi(pi, w) = (e^{3 beta J/2} - e^{-beta J/2}) 2J / (Z (4J^2 + w^2)).
+    w1 = 2 * np.pi / beta
+    chi_w = (np.exp(1.5 * beta * J) - np.exp(-0.5 * beta * J)) * 2 * J / (Z * (4 * J * J + w1 * w1))
+    return {"energy": E / 2, "chi_s": chi_s, "chi_w": chi_w}
 
 
 def ring4_closed_form(beta, J=1.0):

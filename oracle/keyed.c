@@ -239,6 +239,42 @@ int orc_keyed_cell(const orc_params *p, uint32_t sweep, const uint8_t *s0, const
 typedef unsigned __int128 u128;
 
 /* floor((v c + 2^31) / 2^32): v c / 2^32 rounded to nearest, ties up (exact). */
+/* Phase factors for the temporal moment (Sec. 5: the gap from the
+   imaginary-time moment of the staggered correlation). */
+#define PH_BITS 16
+static int64_t ph_cos[(1 << PH_BITS) + 1], ph_sin[(1 << PH_BITS) + 1];
+static int ph_ready;
+
+static void ph_init(void) {
+  if (ph_ready) return;
+  for (int64_t k = 0; k <= (1 << PH_BITS); ++k) {
+    double ang = (2.0 * M_PI * (double)k) / (double)(1 << PH_BITS);
+    ph_cos[k] = llrint(ldexp(cos(ang), 30));
+    ph_sin[k] = llrint(ldexp(sin(ang), 30));
+  }
+  ph_ready = 1;
+}
+
+static int64_t floor_div_2_32(int64_t x) { /* floor(x / 2^32) */
+  return x >= 0 ? x / 4294967296LL : -((-x + 4294967295LL) / 4294967296LL);
+}
+
+uint64_t orc_phase_recip(int64_t qbeta, int *sh) {
+  int k = 63;
+  while (k > 0 && !(((uint64_t)qbeta >> k) & 1u)) --k;
+  *sh = k; /* 2^k <= qbeta < 2^(k+1) */
+  return (uint64_t)(((((u128)1) << (64 + k)) - 1) / (u128)(uint64_t)qbeta);
+}
+
+void orc_phase(uint64_t q, uint64_t R, int sh, int64_t *c, int64_t *s) {
+  ph_init();
+  uint64_t X = (uint64_t)(((u128)q * R) >> sh); /* fraction of the period, modulo 2^64 */
+  uint64_t k = X >> (64 - PH_BITS);
+  int64_t t = (int64_t)((X >> (32 - PH_BITS)) & 0xffffffffULL);
+  *c = ph_cos[k] + floor_div_2_32((ph_cos[k + 1] - ph_cos[k]) * t);
+  *s = ph_sin[k] + floor_div_2_32((ph_sin[k + 1] - ph_sin[k]) * t);
+}
+
 static int64_t mul_q32(int64_t v, int64_t c) {
   __int128 p = (__int128)v * (__int128)c + ((__int128)1 << 31);
   return (int64_t)(p >> 32);
@@ -499,6 +535,10 @@ int orc_keyed_update(const orc_params *p, uint32_t sweep, const uint8_t *s0,
       int64_t *Wq = (int64_t *)calloc((size_t)nloop + 1, sizeof(int64_t));
       int64_t *Cq = (int64_t *)calloc((size_t)nloop + 1, sizeof(int64_t));
       int64_t *Sq = (int64_t *)calloc((size_t)nloop + 1, sizeof(int64_t));
+      int64_t *Zr = (int64_t *)calloc((size_t)nloop + 1, sizeof(int64_t));
+      int64_t *Zi = (int64_t *)calloc((size_t)nloop + 1, sizeof(int64_t));
+      int rsh;
+      const uint64_t rbeta = orc_phase_recip(qbeta, &rsh);
       int64_t *cx = (int64_t *)malloc(sizeof(int64_t) * (size_t)L);
       int64_t *sx = (int64_t *)malloc(sizeof(int64_t) * (size_t)L);
       for (int64_t x = 0; x < L; ++x) {
@@ -518,13 +558,20 @@ int orc_keyed_update(const orc_params *p, uint32_t sweep, const uint8_t *s0,
             q = partner[2 * q + 1] / 2;
             if (++guard > NS + 2) { rc = -7; break; }
           }
-          int64_t len = llrint(ldexp(vtx[top_v[q]].tau, F)) - llrint(ldexp(vtx[v].tau, F)) +
-                        cross * qbeta;
+          int64_t qt = llrint(ldexp(vtx[top_v[q]].tau, F)), qb = llrint(ldexp(vtx[v].tau, F));
+          int64_t len = qt - qb + cross * qbeta;
           int64_t x = u / Q;
           int64_t l = loop[poff[u] + (side ? pos_r[v] : pos_l[v]) + 1];
           Wq[l] += len;
           Cq[l] += mul_q32(len, cx[x]);
           Sq[l] += mul_q32(len, sx[x]);
+          /* int over the fragment of e^{i w1 t} dt = (e(top) - e(bottom)) / (i w1):
+             the same across the cut, since e(t + beta) = e(t) */
+          int64_t ct, st_, cb, sb;
+          orc_phase((uint64_t)qt, rbeta, rsh, &ct, &st_);
+          orc_phase((uint64_t)qb, rbeta, rsh, &cb, &sb);
+          Zr[l] += ct - cb;
+          Zi[l] += st_ - sb;
         }
       }
       for (int64_t l = 0; l < nloop; ++l) {
@@ -535,13 +582,17 @@ int orc_keyed_update(const orc_params *p, uint32_t sweep, const uint8_t *s0,
         Cq[l] += mul_q32(len, cx[x]);
         Sq[l] += mul_q32(len, sx[x]);
       }
-      u128 sw2 = 0, sf2 = 0;
+      /* (vertex-free loops are whole periods: their temporal sums are 0) */
+      u128 sw2 = 0, sf2 = 0, sz2 = 0;
       for (int64_t l = 0; l < nloop; ++l) {
         uint64_t aw = (uint64_t)(Wq[l] < 0 ? -Wq[l] : Wq[l]);
         uint64_t ac = (uint64_t)(Cq[l] < 0 ? -Cq[l] : Cq[l]);
         uint64_t as = (uint64_t)(Sq[l] < 0 ? -Sq[l] : Sq[l]);
+        uint64_t ar = (uint64_t)(Zr[l] < 0 ? -Zr[l] : Zr[l]);
+        uint64_t ai = (uint64_t)(Zi[l] < 0 ? -Zi[l] : Zi[l]);
         sw2 += (u128)aw * aw;
         sf2 += (u128)ac * ac + (u128)as * as;
+        sz2 += (u128)ar * ar + (u128)ai * ai;
       }
       if (rec) {
         rec->n = n;
@@ -556,11 +607,16 @@ int orc_keyed_update(const orc_params *p, uint32_t sweep, const uint8_t *s0,
         rec->sw2_hi = (uint64_t)(sw2 >> 64);
         rec->sf2_lo = (uint64_t)sf2;
         rec->sf2_hi = (uint64_t)(sf2 >> 64);
+        rec->sz2_lo = (uint64_t)sz2;
+        rec->sz2_hi = (uint64_t)(sz2 >> 64);
         double dsw = (double)rec->sw2_hi * 18446744073709551616.0 + (double)rec->sw2_lo;
         double dsf = (double)rec->sf2_hi * 18446744073709551616.0 + (double)rec->sf2_lo;
+        double dsz = (double)rec->sz2_hi * 18446744073709551616.0 + (double)rec->sz2_lo;
         rec->energy = (double)(Q * Q) * p->J * 0.25 - (double)n / (beta * (double)L);
         rec->chi_s = ldexp(dsw, -2 * F) / (4.0 * beta * (double)L);
         rec->chi_q = ldexp(dsf, -2 * F) / (4.0 * beta * (double)L);
+        /* |int e^{i w1 t} dt|^2 = |Z|^2 2^-60 / w1^2, w1 = 2 pi / beta */
+        rec->chi_w = ldexp(dsz, -60) * beta / (16.0 * M_PI * M_PI * (double)L);
       }
       /* Debug graph export. */
       if (cap_vtx >= n) {
@@ -590,6 +646,8 @@ int orc_keyed_update(const orc_params *p, uint32_t sweep, const uint8_t *s0,
       free(Wq);
       free(Cq);
       free(Sq);
+      free(Zr);
+      free(Zi);
       free(cx);
       free(sx);
       free(newflag);

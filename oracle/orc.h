@@ -68,10 +68,24 @@ typedef struct {
      x q(beta), q(x) = rint(x 2^F)); Fourier terms with cos, sin in 2^-32 units. */
   uint64_t sw2_lo, sw2_hi;  /* sum over loops of Wq^2 (128-bit) */
   uint64_t sf2_lo, sf2_hi;  /* sum over loops of Cq^2 + Sq^2 (128-bit) */
+  /* Temporal moment: per fragment Z = e(top) - e(bottom), e(t) = exp(i w1 t) in
+     2^-30 units (w1 = 2 pi / beta, evaluated as in orc_phase); per loop the sum
+     of Z; here the sum over loops of |sum Z|^2 (128-bit). */
+  uint64_t sz2_lo, sz2_hi;
   double energy;        /* E/L = (Q^2 J/4) - n/(beta L) */
   double chi_s;         /* sum_c W_c^2 / (4 beta L) */
   double chi_q;         /* sum_c |sum e^{ikx} len|^2 / (4 beta L), k = 2 pi/L */
+  double chi_w;         /* sum_c |sum over fragments of int e^{i w1 t} dt|^2 / (4 beta L) */
 } orc_record;
+
+/* exp(i 2 pi q / qbeta) in units of 2^-30 for a tick count q of a time in
+   [0, beta]: the fraction q / qbeta in 64-bit fixed point, X = (q R) >> sh
+   modulo 2^64 with sh = floor(log2 qbeta) and R = floor((2^(64+sh) - 1) / qbeta)
+   (error below 3 units of 2^-64); cos and sin at 2^16 points of the period
+   (rounded to 30 fractional bits); linear interpolation in integers (floor of
+   the 2^-32-scaled correction).  Error below 2e-9 of the unit. */
+void orc_phase(uint64_t q, uint64_t R, int sh, int64_t *c, int64_t *s);
+uint64_t orc_phase_recip(int64_t qbeta, int *sh);
 
 /* Derived chain geometry (both forms use it). */
 int64_t orc_nsub(const orc_params *p);

@@ -30,8 +30,9 @@ class Record(ctypes.Structure):
                 ("F", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("sw2_lo", ctypes.c_uint64), ("sw2_hi", ctypes.c_uint64),
                 ("sf2_lo", ctypes.c_uint64), ("sf2_hi", ctypes.c_uint64),
+                ("sz2_lo", ctypes.c_uint64), ("sz2_hi", ctypes.c_uint64),
                 ("energy", ctypes.c_double), ("chi_s", ctypes.c_double),
-                ("chi_q", ctypes.c_double)]
+                ("chi_q", ctypes.c_double), ("chi_w", ctypes.c_double)]
 
 
 RECORD_DTYPE = np.dtype([(name, np.int64 if t in (ctypes.c_int64,) else
@@ -68,6 +69,10 @@ def lib():
         L.orc_serial_run.argtypes = [P(Params), ctypes.c_uint32, ctypes.c_int64, vp, vp, vp,
                                      vp, ctypes.c_int64, vp]
         L.orc_serial_run.restype = ctypes.c_int
+        L.orc_phase.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, P(ctypes.c_int64),
+                                P(ctypes.c_int64)]
+        L.orc_phase_recip.argtypes = [ctypes.c_int64, P(ctypes.c_int)]
+        L.orc_phase_recip.restype = ctypes.c_uint64
         _lib = L
     return _lib
 
@@ -226,3 +231,11 @@ def keyed_cell(p, sweep, st, b, j):
     if rc != 0:
         raise RuntimeError("orc_keyed_cell failed")
     return tau[: n.value].copy(), flag[: n.value].copy()
+
+
+def phase(q, qbeta):
+    """exp(i 2 pi q / qbeta) in units of 2^-30 as the oracle evaluates it."""
+    c, sn, sh = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+    rb = lib().orc_phase_recip(int(qbeta), ctypes.byref(sh))
+    lib().orc_phase(int(q) & (2**64 - 1), rb, sh.value, ctypes.byref(c), ctypes.byref(sn))
+    return c.value, sn.value

@@ -257,6 +257,9 @@ int orc_serial_update(const orc_params *p, uint32_t sweep, uint8_t *s0, int64_t 
     double *W = (double *)calloc((size_t)ns, sizeof(double));
     double *C = (double *)calloc((size_t)ns, sizeof(double));
     double *S = (double *)calloc((size_t)ns, sizeof(double));
+    double *ZR = (double *)calloc((size_t)ns, sizeof(double));
+    double *ZI = (double *)calloc((size_t)ns, sizeof(double));
+    const double w1 = 2.0 * M_PI / beta; /* first Matsubara frequency */
     for (int64_t x = 0; x < ns; ++x) {
       int64_t rt = uf_find(&uf, x);
       double len = seg[x].t1 - seg[x].t0;
@@ -264,12 +267,16 @@ int orc_serial_update(const orc_params *p, uint32_t sweep, uint8_t *s0, int64_t 
       W[rt] += len;
       C[rt] += len * cos(ang);
       S[rt] += len * sin(ang);
+      /* int_{t0}^{t1} e^{i w1 t} dt = (e^{i w1 t1} - e^{i w1 t0}) / (i w1) */
+      ZR[rt] += cos(w1 * seg[x].t1) - cos(w1 * seg[x].t0);
+      ZI[rt] += sin(w1 * seg[x].t1) - sin(w1 * seg[x].t0);
     }
-    double sw2 = 0.0, sf2 = 0.0;
+    double sw2 = 0.0, sf2 = 0.0, sz2 = 0.0;
     for (int64_t x = 0; x < ns; ++x) {
       if (uf_find(&uf, x) != x) continue;
       sw2 += W[x] * W[x];
       sf2 += C[x] * C[x] + S[x] * S[x];
+      sz2 += ZR[x] * ZR[x] + ZI[x] * ZI[x];
     }
     if (rec) {
       memset(rec, 0, sizeof(*rec));
@@ -282,7 +289,10 @@ int orc_serial_update(const orc_params *p, uint32_t sweep, uint8_t *s0, int64_t 
       rec->energy = (double)(Q * Q) * p->J * 0.25 - (double)nv / (beta * (double)L);
       rec->chi_s = sw2 / (4.0 * beta * (double)L);
       rec->chi_q = sf2 / (4.0 * beta * (double)L);
+      rec->chi_w = sz2 / (w1 * w1 * 4.0 * beta * (double)L);
     }
+    free(ZR);
+    free(ZI);
     free(W);
     free(C);
     free(S);

@@ -11,6 +11,15 @@ def test_dimer(beta):
     c = ed.dimer_closed_form(beta)
     assert t["energy"] == pytest.approx(c["energy"], rel=1e-12, abs=1e-14)
     assert t["chi_s"] == pytest.approx(c["chi_s"], rel=1e-12)
+    assert t["chi_w"] == pytest.approx(c["chi_w"], rel=1e-12)
+
+
+@pytest.mark.parametrize("L,beta", [(6, 2.0), (8, 8.0)])
+def test_chi_w_bounds(L, beta):
+    # spectral weights are positive: 0 < chi(pi, w1) < chi(pi, 0); at low T
+    # the ratio approaches the single-gap Lorentzian.
+    t = ed.thermal(L, beta)
+    assert 0 < t["chi_w"] < t["chi_s"]
 
 
 @pytest.mark.parametrize("beta", [0.5, 2.0, 8.0])

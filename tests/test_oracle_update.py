@@ -170,6 +170,18 @@ def test_keyed_estimator_sums_exact(orc):
         sw2 = sum(v * v for v in W.values())
         sw2 += int((~touched).sum()) * int(np.rint(np.ldexp(beta, F))) ** 2
         assert sw2 == orc.u128(rec["sw2_lo"], rec["sw2_hi"])
+        # temporal sums: per fragment e(top) - e(bottom), per loop summed
+        qb = int(np.rint(np.ldexp(beta, F)))
+        Z = {}
+        for w in range(n):
+            cw = orc.phase(int(np.rint(np.ldexp(gr["tau"][w], F))), qb)
+            for P in (int(gr["pl"][w]), int(gr["pr"][w])):
+                cp = orc.phase(int(np.rint(np.ldexp(gr["tau"][P], F))), qb)
+                r = int(gr["root"][P])
+                zr, zi = Z.get(r, (0, 0))
+                Z[r] = (zr + cw[0] - cp[0], zi + cw[1] - cp[1])
+        sz2 = sum(a * a + b * b for a, b in Z.values())
+        assert sz2 == orc.u128(rec["sz2_lo"], rec["sz2_hi"])
         assert int(rec["n_free"]) == int((~touched).sum())
         st = new
 
@@ -216,7 +228,7 @@ def test_vs_ed(orc, form, L, beta, Q, seed):
         r, _, _ = orc.serial_run(p, 0, n + 500)
         r = r[500:]
     ex = ed.thermal(L, beta, S=Q / 2)
-    for name in ("energy", "chi_s", "chi_q"):
+    for name in ("energy", "chi_s", "chi_q", "chi_w"):
         m, e = stats.mean_err(r[name], 100)
         assert stats.within_sigma(m, e, ex[name], 3.0), (name, m, e, ex[name])
 
@@ -271,3 +283,16 @@ def test_paper_table4_s1(orc):
     assert stats.within_sigma(m, e, g["chi_s"], 3.0, g["chi_s_err"])
     xi, xe = stats.jackknife(stats.xi_second_moment(L), r["chi_s"], r["chi_q"], nbins=40)
     assert stats.within_sigma(xi, xe, g["xi"], 3.0, g["xi_err"])
+
+
+def test_phase_factor(orc):
+    """The integer phase factor against numpy's exp(i 2 pi q / qbeta), within
+    the table-and-interpolation bound (2 pi / 2^16)^2 / 8 of the 2^30 unit plus
+    the roundings, over tick counts of several magnitudes."""
+    rng = np.random.default_rng(5)
+    for qbeta in (1000003, 1 << 30, 3 * (1 << 44) + 12345, (1 << 59) + 7):
+        qs = list(rng.integers(0, qbeta, 400, dtype=np.int64)) + [0, qbeta - 1, qbeta // 4, qbeta // 2]
+        for q in qs:
+            c, s = orc.phase(int(q), qbeta)
+            ang = 2 * np.pi * (int(q) / qbeta)
+            assert abs(c - np.cos(ang) * 2**30) < 4.0 and abs(s - np.sin(ang) * 2**30) < 4.0, (qbeta, q)
