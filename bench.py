@@ -38,7 +38,6 @@ DEFAULT_WORKLOAD = "L65536_beta4096"
 # Oracle sample of the same workload: same beta, fewer sites.
 ORACLE_SAMPLE_L = 1024
 KERNELS_PER_UPDATE = 11
-RECORD_BYTES = 104
 # DRAM bytes per vertex of each phase's kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture at L=16384, beta=4096, divided by
 # that update's vertex count; profiles/topkernels_L16384_beta4096.md), valid
@@ -204,6 +203,8 @@ def run_ours(args, world, rank, local):
     L, beta, therm = WORKLOADS[args.workload]
     stream = torch.cuda.Stream()
     ch = lcqmc.Chain(L, beta, seed=chain_seed(rank), stream=stream.cuda_stream)
+    if args.temporal:
+        ch.set_temporal(True)
     geo = ch.geometry()
     # thermalization from the Neel state, then W warm-up updates (untimed)
     ch.update(therm + args.warmup)
@@ -282,11 +283,12 @@ def run_ours(args, world, rank, local):
         "config": {"workload": f"S=1/2 AFM Heisenberg chain, J=1, L={L}, beta={beta:g}, one chain per GPU "
                                f"(seed 1+rank), Neel start, {therm}+{args.warmup} untimed updates",
                    "L": L, "beta": beta, "vertices_per_update": mean_n,
+                   "temporal_moment": bool(args.temporal),
                    "l2": "inputs larger than L2 (state and per-update graph are several GB)"},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "V+E/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": RECORD_BYTES},
+                "d2h_bytes_per_step": lcqmc.RECORD_DTYPE.itemsize},
         "gpu_launches": KERNELS_PER_UPDATE * args.steps,
         "clocks": clocks,
     }
@@ -447,6 +449,8 @@ def main():
     ap.add_argument("--req-updates", type=int, default=50)
     ap.add_argument("--slots", type=int, default=512)
     ap.add_argument("--time-limit", type=float, default=60.0)
+    ap.add_argument("--temporal", action="store_true",
+                    help="also measure the temporal moment chi(pi, 2 pi/beta) (single mode)")
     args = ap.parse_args()
     world, rank, local = dist_setup(args.gpus)
     if args.mode == "batched":

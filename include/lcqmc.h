@@ -66,24 +66,32 @@ typedef struct lcqmc_server *lcqmc_server_t;
 /* Running averages since create / the last reset (caller-owned). Index k of
  * sum/sumsq: 0 E/L, 1 chi_s, 2 chi(pi+2pi/L), 3 n (graph vertices),
  * 4 n_off (off-diagonal operators after the update), 5 world-line fragments,
- * 6 loops, 7 vertices+edges of the cluster graph (fragments + 2n). */
+ * 6 loops, 7 vertices+edges of the cluster graph (fragments + 2n),
+ * 8 chi(pi, w1) at the first Matsubara frequency w1 = 2pi/beta. */
 typedef struct {
   int64_t n_updates;
-  double sum[8];
-  double sumsq[8];
-  double xi; /* (L/2pi) sqrt(<chi_s>/<chi(pi+2pi/L)> - 1), ratio of means */
+  double sum[9];
+  double sumsq[9];
+  double xi;     /* (L/2pi) sqrt(<chi_s>/<chi(pi+2pi/L)> - 1), ratio of means */
+  double xi_tau; /* (beta/2pi) sqrt(<chi_s>/<chi(pi,w1)> - 1): imaginary-time length */
+  double gap;    /* 1/xi_tau (Sec. 5: gap from the second moment in time) */
 } lcqmc_obs;
 
 /* One update's measurements.  The sums of squared loop lengths are exact
  * 128-bit integers in units of 2^-2F (F = 60 - ceil(log2(Q L beta))): every
  * fragment length is rounded once to a multiple of 2^-F, then summed per loop
  * exactly.  energy = Q^2 J/4 - n/(beta L); chi_s = sw2 2^-2F/(4 beta L);
- * chi_q = sf2 2^-2F/(4 beta L) with q = pi + 2 pi / L. */
+ * chi_q = sf2 2^-2F/(4 beta L) with q = pi + 2 pi / L.  Temporal moment: per
+ * fragment Z = e(top) - e(bottom) with e(t) = exp(i w1 t) in units of 2^-30
+ * (w1 = 2 pi / beta; the period fraction of the time's tick count in 64-bit
+ * fixed point, cos/sin at 2^16 points rounded to 30 bits, integer linear
+ * interpolation), summed per loop; sz2 = sum over loops of |sum Z|^2 (exact);
+ * chi_w = sz2 2^-60 beta / (16 pi^2 L) = sum_c |int e^{i w1 t} dt|^2 / (4 beta L). */
 typedef struct {
   int64_t n, n_off_old, n_off_new, n_free, n_clusters, n_seg;
   int32_t F, pad;
-  uint64_t sw2_lo, sw2_hi, sf2_lo, sf2_hi;
-  double energy, chi_s, chi_q;
+  uint64_t sw2_lo, sw2_hi, sf2_lo, sf2_hi, sz2_lo, sz2_hi;
+  double energy, chi_s, chi_q, chi_w;
 } lcqmc_record;
 
 typedef struct {
@@ -177,6 +185,13 @@ int lcqmc_restore(lcqmc_handle h, const void *buf, size_t len);
  * 5 operator offsets, 6 operator rewrite, 7 spin rewrite and record. */
 #define LCQMC_NPHASE 8
 int lcqmc_set_phase_timing(lcqmc_handle h, int enable);
+
+/* Turns the temporal moment on or off (off after create): chi(pi, w1) at the
+ * first Matsubara frequency w1 = 2 pi / beta, the record's sz2 and chi_w and
+ * the obs' sum[8], xi_tau and gap (Sec. 5: the gap from the second moment in
+ * imaginary time).  Off, those are 0 and every other result is unchanged.
+ * Waits for enqueued updates; applies to the following ones. */
+int lcqmc_set_temporal(lcqmc_handle h, int enable);
 int lcqmc_get_phase_times(lcqmc_handle h, double *ms, int nphase);
 
 /* Raw CUDA stream of the handle (cudaStream_t as void*). */
@@ -199,6 +214,7 @@ int lcqmc_batch_create(int64_t nchains, const lcqmc_chain_spec *specs, void *cud
                        lcqmc_batch_t *out);
 int lcqmc_batch_update(lcqmc_batch_t b, int64_t n);
 int lcqmc_batch_sync(lcqmc_batch_t b);
+int lcqmc_batch_set_temporal(lcqmc_batch_t b, int enable); /* as lcqmc_set_temporal, all chains */
 int lcqmc_batch_measure(lcqmc_batch_t b, int64_t chain, lcqmc_obs *out);
 int lcqmc_batch_get_records(lcqmc_batch_t b, int64_t chain, lcqmc_record *out, int64_t max,
                             int64_t *count);

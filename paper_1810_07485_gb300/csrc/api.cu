@@ -252,6 +252,10 @@ int lcqmc_set_phase_timing(lcqmc_handle h, int enable) {
   NEED(h);
   return h->eng.set_phase_timing(enable);
 }
+int lcqmc_set_temporal(lcqmc_handle h, int enable) {
+  NEED(h);
+  return h->eng.set_temporal(enable);
+}
 int lcqmc_get_phase_times(lcqmc_handle h, double *ms, int nphase) {
   NEED(h);
   if (!ms) return LCQMC_E_INVAL;
@@ -306,6 +310,10 @@ int lcqmc_batch_get_records(lcqmc_batch_t b, int64_t chain, lcqmc_record *out, i
   NEED(b);
   if (chain < 0 || chain >= b->eng.nchains() || !count) return LCQMC_E_INVAL;
   return b->eng.records(chain, out, max, count);
+}
+int lcqmc_batch_set_temporal(lcqmc_batch_t b, int enable) {
+  if (!b) return LCQMC_E_INVAL;
+  return b->eng.set_temporal(enable);
 }
 int lcqmc_batch_destroy(lcqmc_batch_t b) {
   delete b;

@@ -12,6 +12,9 @@ namespace lcq {
 constexpr int KMAX = 48;          // Poisson count table length (K <= KMAX-1)
 constexpr int TW = LCQMC_TW;      // windows per time block of the cell order
 constexpr int64_t VTX_ID_LIMIT = 0x7ffff000;  // largest vertex count of one chain
+constexpr int NOBS = 9;         // running averages per chain (lcqmc_obs.sum)
+constexpr int ACC_WORDS = 4;    // 64-bit words of an open loop's record (32 bytes)
+constexpr int PHASE_BITS = 16;  // phase factor table: 2^16 points of the period
 constexpr int TILE = 128;         // cells per tile (one thread block)
 constexpr int SMEM_CAP = 2048;    // vertices a tile can accumulate in shared memory
 constexpr int MAX_COIN_GROUPS = 64;
@@ -46,6 +49,8 @@ struct DevChain {
   const uint64_t *win;         // per window: bits of t0, t_end, t_end - t0
   const long long *cosq, *sinq;  // rint(2^32 cos(2 pi x / L)), rint(2^32 sin(...))
   long long qbeta;             // rint(beta 2^F)
+  uint64_t phR;                // floor((2^(64+phS) - 1) / qbeta): period fraction of a tick count
+  int32_t phS, pad1;           // floor(log2 qbeta)
   // persistent state, double-buffered (index cur is current)
   uint8_t *s0[2];
   int32_t *op_ptr[2];
@@ -68,13 +73,13 @@ struct DevChain {
   lcqmc_record *ring;
   int64_t n_rec;
   int64_t n_updates;
-  double sum[8], sumsq[8];
+  double sum[NOBS], sumsq[NOBS];
 };
 
 struct Scratch {
   int32_t *vptr;
   int64_t *tile_sum, *tile_pref, *tile_sum2, *tile_pref2, *tile_roots;
-  unsigned long long *tile_sw2, *tile_sf2;   // 2 words (lo, hi) per tile
+  unsigned long long *tile_sw2, *tile_sf2, *tile_sz2;  // 2 words (lo, hi) per tile
   int64_t *site_free;
   unsigned long long *site_sw2, *site_sf2;   // 2 words per site block
   uint8_t *bpar;
@@ -84,7 +89,11 @@ struct Scratch {
   uint8_t *vflag;
   uint8_t *vcell;  // per vertex: its cell's index inside the tile (0..127)
   int32_t *pl, *pr, *parent;
-  unsigned long long *acc;  // per vertex: W, C, S, pad (32-byte record), open loops only
+  union {
+    unsigned long long *acc;  // per vertex: W, C, S, Zr (32-byte record), open loops only
+    ulonglong2 *acc2;         // the same records as two 16-byte halves
+  };
+  unsigned long long *accz;  // per vertex: Zi, open loops only, temporal moment on
   uint32_t *openmark, *openroot, *flipbits, *xmark;
   int64_t vcap;
   unsigned long long *tile_state;  // per tile: insertion look-back word (flag << 62 | count)
@@ -229,6 +238,20 @@ __host__ __device__ __forceinline__ long long q_time(uint64_t x_bits, int F) {
   const uint64_t rem = m & ((1ull << r) - 1), half = 1ull << (r - 1);
   if (rem > half || (rem == half && (q & 1))) ++q;
   return (long long)q;
+}
+
+// exp(i 2 pi q / qbeta) in units of 2^-30 (.x cos, .y sin) for a tick count
+// q: the period fraction X = (q R) >> sh modulo 2^64 (R, sh per chain), the
+// table at 2^16 points (tab[k] for angle 2 pi k / 2^16, one extra entry at the
+// end) and linear interpolation with the 2^-32-scaled correction floored.
+__device__ __forceinline__ int2 phase_of(uint64_t q, uint64_t R, int sh, const int2 *tab) {
+  const uint64_t lo = q * R, hi = __umul64hi(q, R);
+  const uint64_t X = (sh == 0) ? lo : ((lo >> sh) | (hi << (64 - sh)));
+  const int k = (int)(X >> (64 - PHASE_BITS));
+  const long long t = (long long)((X >> (32 - PHASE_BITS)) & 0xffffffffull);
+  const int2 a = tab[k], b = tab[k + 1];
+  const long long dc = (long long)(b.x - a.x) * t, ds = (long long)(b.y - a.y) * t;
+  return make_int2(a.x + (int)(dc >> 32), a.y + (int)(ds >> 32));  // arithmetic shift: floor
 }
 
 // round(v * c / 2^32) with ties upward: floor((v c + 2^31) / 2^32), 128-bit exact.

@@ -113,7 +113,7 @@ size_t Engine::estimate_footprint(const std::vector<ChainSpec> &specs, int ring_
              14 * g.nsub + sizeof(DevChain) + 8 * (g.ntile + g.nsiteblk + g.nbondblk);
     vc += (vertex_estimate(c) + 127) / 128 * 128;
   }
-  bytes += (size_t)vc * (8 + 2 + 12 + 32) + 4 * (size_t)(vc / 32 + 1) * 4;
+  bytes += (size_t)vc * (8 + 2 + 12 + 8 * ACC_WORDS + 8) + 4 * (size_t)(vc / 32 + 1) * 4;
   return bytes;
 }
 
@@ -155,6 +155,7 @@ void Engine::free_vertex() {
   dfree(s_.pr);
   dfree(s_.parent);
   dfree(s_.acc);
+  dfree(s_.accz);
   dfree(s_.openmark);
   dfree(s_.openroot);
   dfree(s_.flipbits);
@@ -164,6 +165,7 @@ void Engine::free_vertex() {
   s_.vcell = nullptr;
   s_.pl = s_.pr = s_.parent = nullptr;
   s_.acc = nullptr;
+  s_.accz = nullptr;
   s_.openmark = s_.openroot = s_.flipbits = s_.xmark = nullptr;
   vertex_bytes_ = 0;
 }
@@ -177,16 +179,18 @@ int Engine::alloc_vertex(int64_t vcap) {
   DALLOC(s_.pl, int32_t, vcap);
   DALLOC(s_.pr, int32_t, vcap);
   DALLOC(s_.parent, int32_t, vcap);
-  DALLOC(s_.acc, unsigned long long, 4 * vcap);
+  DALLOC(s_.acc, unsigned long long, ACC_WORDS * vcap);
+  DALLOC(s_.accz, unsigned long long, vcap);
   const int64_t nw = vcap / 32 + 1;
   DALLOC(s_.openmark, uint32_t, nw);
   DALLOC(s_.openroot, uint32_t, nw);
   DALLOC(s_.flipbits, uint32_t, nw);
   DALLOC(s_.xmark, uint32_t, nw);
-  CK(cudaMemsetAsync(s_.acc, 0, 4 * sizeof(unsigned long long) * vcap, st_));
+  CK(cudaMemsetAsync(s_.acc, 0, ACC_WORDS * sizeof(unsigned long long) * vcap, st_));
+  CK(cudaMemsetAsync(s_.accz, 0, sizeof(unsigned long long) * vcap, st_));
   s_.vcap = vcap;
   vcap_ = vcap;
-  vertex_bytes_ = (size_t)vcap * (8 + 2 + 12 + 32) + 4 * (size_t)nw * 4;
+  vertex_bytes_ = (size_t)vcap * (8 + 2 + 12 + 8 * ACC_WORDS + 8) + 4 * (size_t)nw * 4;
   L_.s = s_;
   if (gexec_) {
     cudaGraphExecDestroy(gexec_);
@@ -229,6 +233,7 @@ Engine::~Engine() {
   dfree(s_.tile_roots);
   dfree(s_.tile_sw2);
   dfree(s_.tile_sf2);
+  dfree(s_.tile_sz2);
   dfree(s_.site_free);
   dfree(s_.site_sw2);
   dfree(s_.site_sf2);
@@ -249,7 +254,7 @@ Engine::~Engine() {
 int Engine::open(void *stream, const lcqmc_allocator *alloc, int ring_cap) {
   CK(cudaGetDevice(&device_));
   if (init_kernel_attributes() != 0) {
-    set_error("cudaFuncSetAttribute failed");
+    set_error("device table initialization failed");
     return LCQMC_E_CUDA;
   }
   if (alloc && alloc->alloc && alloc->free) {
@@ -348,6 +353,13 @@ int Engine::create_state(const ChainSpec &spec, ChainState *out) {
   d.win = b.win;
   d.ring = b.ring;
   d.qbeta = std::llrint(std::ldexp(d.beta, d.F));
+  {
+    // period fraction of a tick count: X = (q phR) >> phS, phS = floor(log2 qbeta)
+    int k = 63;
+    while (k > 0 && !(((uint64_t)d.qbeta >> k) & 1u)) --k;
+    d.phS = k;
+    d.phR = (uint64_t)((((unsigned __int128)1 << (64 + k)) - 1) / (unsigned __int128)(uint64_t)d.qbeta);
+  }
   CK(cudaStreamSynchronize(st_));  // host staging vectors go out of scope
   return LCQMC_OK;
 }
@@ -446,7 +458,7 @@ int Engine::layout() {
   GROW(bond_tab_, cap_bt_, nb, int2);
   GROW(s_.vptr, cap_cells_, std::max<int64_t>(1, cell_off), int32_t);
   int64_t c1 = cap_tiles_, c2 = cap_tiles_, c3 = cap_tiles_, c4 = cap_tiles_, c5 = cap_tiles_,
-          c6 = cap_tiles_, c7 = cap_tiles_;
+          c6 = cap_tiles_, c7 = cap_tiles_, c9 = cap_tiles_;
   if (nt > cap_tiles_) {
     GROW(s_.tile_sum, c1, nt, int64_t);
     GROW(s_.tile_pref, c2, nt, int64_t);
@@ -455,6 +467,7 @@ int Engine::layout() {
     GROW(s_.tile_roots, c5, nt, int64_t);
     GROW(s_.tile_sw2, c6, 2 * nt, unsigned long long);
     GROW(s_.tile_sf2, c7, 2 * nt, unsigned long long);
+    GROW(s_.tile_sz2, c9, 2 * nt, unsigned long long);
     int64_t c8 = cap_tiles_;
     GROW(s_.tile_state, c8, nt, unsigned long long);
     cap_tiles_ = nt;
@@ -484,7 +497,7 @@ int Engine::layout() {
     CK(cudaMemcpyAsync(site_tab_, stab.data(), sizeof(int2) * stab.size(), cudaMemcpyHostToDevice, st_));
     CK(cudaMemcpyAsync(bond_tab_, btab.data(), sizeof(int2) * btab.size(), cudaMemcpyHostToDevice, st_));
   }
-  fixed_bytes_ = 4 * (size_t)cap_cells_ + 96 * (size_t)cap_tiles_ + 48 * (size_t)cap_sites_ +
+  fixed_bytes_ = 4 * (size_t)cap_cells_ + 112 * (size_t)cap_tiles_ + 48 * (size_t)cap_sites_ +
                  (size_t)cap_bpar_ + 14 * (size_t)cap_subs_ + sizeof(DevChain) * (size_t)cap_chains_;
   L_.ch = dch_;
   L_.nchains = nc;
@@ -727,13 +740,20 @@ int Engine::measure(int64_t c, lcqmc_obs *out) {
   const DevChain &d = hch[c];
   std::memset(out, 0, sizeof(*out));
   out->n_updates = d.n_updates;
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < NOBS; ++k) {
     out->sum[k] = d.sum[k];
     out->sumsq[k] = d.sumsq[k];
   }
   if (d.n_updates > 0 && d.sum[2] > 0) {
     const double r = d.sum[1] / d.sum[2] - 1.0;
     out->xi = r > 0 ? (double)d.L / (2.0 * M_PI) * std::sqrt(r) : 0.0;
+  }
+  // second moment in imaginary time: xi_tau = (beta/2pi) sqrt(chi(pi,0)/chi(pi,w1) - 1),
+  // gap = 1/xi_tau (Sec. 5)
+  if (d.n_updates > 0 && d.sum[8] > 0) {
+    const double r = d.sum[1] / d.sum[8] - 1.0;
+    out->xi_tau = r > 0 ? d.beta / (2.0 * M_PI) * std::sqrt(r) : 0.0;
+    out->gap = out->xi_tau > 0 ? 1.0 / out->xi_tau : 0.0;
   }
   return LCQMC_OK;
 }
@@ -743,7 +763,7 @@ int Engine::reset_obs(int64_t c) {
   if (rc) return rc;
   DevChain &d = hch[c];
   d.n_updates = 0;
-  for (int k = 0; k < 8; ++k) d.sum[k] = d.sumsq[k] = 0.0;
+  for (int k = 0; k < NOBS; ++k) d.sum[k] = d.sumsq[k] = 0.0;
   return push_chains();
 }
 
@@ -928,6 +948,19 @@ int Engine::set_phase_timing(int enable) {
   if (rc) return rc;
   timing_ = enable != 0;
   for (double &x : phase_ms_) x = 0.0;
+  return LCQMC_OK;
+}
+
+int Engine::set_temporal(int enable) {
+  int rc = sync();
+  if (rc) return rc;
+  if ((L_.temporal != 0) != (enable != 0)) {
+    L_.temporal = enable != 0;
+    if (gexec_) {  // the captured launches carry the choice
+      cudaGraphExecDestroy(gexec_);
+      gexec_ = nullptr;
+    }
+  }
   return LCQMC_OK;
 }
 

@@ -72,6 +72,7 @@ class Engine {
   int geometry(int64_t chain, lcqmc_geometry *out);
   int export_cells(int64_t chain, int32_t *vptr, int64_t cap);
   int set_phase_timing(int enable);
+  int set_temporal(int enable);  // temporal moment chi(pi, 2 pi/beta) for every chain
   int phase_times(double *ms, int nphase);
   size_t footprint() const;  // device bytes held
   static size_t estimate_footprint(const std::vector<ChainSpec> &specs, int ring_cap);

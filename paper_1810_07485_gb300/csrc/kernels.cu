@@ -17,7 +17,9 @@
 //   k_compact        next operator list, squared lengths of open loops  [8]
 //   k_sites          spins at tau = 0, vertex-free loops                [8]
 //   k_final          per-chain record, running sums, buffer swap
+#include <cmath>
 #include <cstdio>
+#include <mutex>
 
 #include "dev.cuh"
 #include "kernels.h"
@@ -26,6 +28,8 @@
 namespace lcq {
 
 __constant__ uint64_t c_T_full[KMAX];
+// exp(i 2 pi k / 2^16) in units of 2^-30, k = 0..2^16 (temporal moment)
+__device__ int2 g_phase_tab[(1 << PHASE_BITS) + 1];
 
 // ---- block-wide helpers (blockDim.x is a multiple of 32, <= 1024) ---------
 template <typename T>
@@ -95,33 +99,38 @@ __device__ __forceinline__ u128 shfl_down_u128(u128 v, int o) {
   return ((u128)h << 64) | (u128)l;
 }
 
-// Exact block-wide sums of one int64 and two 128-bit values with a single
-// barrier; the totals are valid in thread 0.  Once per kernel.
-__device__ void block_sum3(long long &c, u128 &x, u128 &y) {
+// Exact block-wide sums of one int64 and two (Z: three) 128-bit values with a
+// single barrier; the totals are valid in thread 0.  Once per kernel.
+template <bool Z>
+__device__ void block_sums(long long &c, u128 &x, u128 &y, u128 &z) {
   __shared__ long long pc[32];
-  __shared__ u128 px[32], py[32];
+  __shared__ u128 px[32], py[32], pz[Z ? 32 : 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     c += __shfl_down_sync(0xffffffffu, c, o);
     x += shfl_down_u128(x, o);
     y += shfl_down_u128(y, o);
+    if (Z) z += shfl_down_u128(z, o);
   }
   if (lane == 0) {
     pc[wid] = c;
     px[wid] = x;
     py[wid] = y;
+    if (Z) pz[wid] = z;
   }
   __syncthreads();
   if (wid == 0) {
     c = lane < nw ? pc[lane] : 0;
     x = lane < nw ? px[lane] : (u128)0;
     y = lane < nw ? py[lane] : (u128)0;
+    if (Z) z = lane < nw ? pz[lane] : (u128)0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       c += __shfl_down_sync(0xffffffffu, c, o);
       x += shfl_down_u128(x, o);
       y += shfl_down_u128(y, o);
+      if (Z) z += shfl_down_u128(z, o);
     }
   }
 }
@@ -1054,14 +1063,29 @@ __device__ __forceinline__ unsigned long long sget64(const unsigned *w) {
 }
 
 // Per-tile table of loop sums keyed by root: a vertex of a loop of more than
-// one node adds its (W, C, S) to its root's slot (linear probing, split
-// sums).  If the table is full the sums go to the root's global record and
-// the root is marked open, so that they are squared with the open loops.
+// one node adds its (W, C, S, Zr, Zi) to its root's slot (linear probing,
+// split sums).  If the table is full the sums go to the root's global record
+// and the root is marked open, so that they are squared with the open loops.
 constexpr int LOOP_SLOTS = 256;
+constexpr int LOOP_SUMS = 5;  // W, C, S, Zr, Zi
 
-__device__ __forceinline__ void loop_add(int *keys, unsigned *vals, int key, long long W,
-                                         long long Cc, long long Ss, const Scratch &s,
-                                         int64_t vb) {
+struct LoopSums {
+  long long v[LOOP_SUMS];
+};
+
+// Adds a loop's first NS sums to the global record of its root (vertex v):
+// W, C, S, Zr in one 32-byte record, Zi beside it in its own array.
+template <int NS>
+__device__ __forceinline__ void acc_add(const Scratch &s, int64_t v, const long long *x) {
+  unsigned long long *r = s.acc + ACC_WORDS * v;
+#pragma unroll
+  for (int i = 0; i < NS; ++i) atomicAdd(i < ACC_WORDS ? r + i : s.accz + v, (unsigned long long)x[i]);
+}
+
+// NS: how many of the sums are carried (3 without the temporal moment).
+template <int NS>
+__device__ __forceinline__ void loop_add(int *keys, unsigned *vals, int key, const LoopSums &x,
+                                         const Scratch &s, int64_t vb) {
   unsigned h = ((unsigned)key * 2654435761u) >> 24;  // top 8 bits: LOOP_SLOTS = 256
   for (int probe = 0; probe < LOOP_SLOTS; ++probe) {
     int k = keys[h];
@@ -1070,32 +1094,39 @@ __device__ __forceinline__ void loop_add(int *keys, unsigned *vals, int key, lon
       if (k == -1) k = key;
     }
     if (k == key) {
-      sadd64(vals + 6 * h + 0, W);
-      sadd64(vals + 6 * h + 2, Cc);
-      sadd64(vals + 6 * h + 4, Ss);
+#pragma unroll
+      for (int i = 0; i < NS; ++i) sadd64(vals + 2 * (LOOP_SUMS * h + i), x.v[i]);
       return;
     }
     h = (h + 1) & (LOOP_SLOTS - 1);
   }
-  unsigned long long *r = s.acc + 4 * (vb + key);
-  atomicAdd(r, (unsigned long long)W);
-  atomicAdd(r + 1, (unsigned long long)Cc);
-  atomicAdd(r + 2, (unsigned long long)Ss);
+  acc_add<NS>(s, vb + key, x.v);
   set_bit(s.openroot, vb >> 5, key);
+}
+
+// Squares of one loop's sums: W^2 to w2, C^2 + S^2 to f2, (T) Zr^2 + Zi^2 to z2.
+template <bool T>
+__device__ __forceinline__ void loop_squares(const long long *v, u128 &w2, u128 &f2, u128 &z2) {
+  w2 += sq_abs(v[0]);
+  f2 += sq_abs(v[1]) + sq_abs(v[2]);
+  if (T) z2 += sq_abs(v[3]) + sq_abs(v[4]);
 }
 
 constexpr int TPB_EST = 512;
 
-template <int Q>
-__global__ void __launch_bounds__(TPB_EST, 4) k_est(const DevChain *__restrict__ ch,
+// T: also the temporal moment (phase factors, Zr and Zi); off by default.
+template <int Q, bool T>
+__global__ void __launch_bounds__(TPB_EST, T ? 3 : 4) k_est(const DevChain *__restrict__ ch,
                                              const int2 *__restrict__ tab, int64_t blk0,
                                              Scratch s) {
   __shared__ int lkeys[LOOP_SLOTS];
-  __shared__ unsigned lvals[6 * LOOP_SLOTS];
+  __shared__ unsigned lvals[2 * LOOP_SUMS * LOOP_SLOTS];
   __shared__ int cvp[TILE + 1];
   __shared__ int cnew[TILE];
   __shared__ long long ccl[TILE], csl[TILE], ccr[TILE], csr[TILE], cxl[TILE], cxr[TILE];
-  __shared__ long long qv[SMEM_CAP];  // ticks q(tau) of the tile's vertices
+  extern __shared__ long long est_dyn[];
+  long long *qv = est_dyn;                   // ticks q(tau) of the tile's vertices
+  int2 *ev = (int2 *)(est_dyn + SMEM_CAP);   // their phase factors exp(i w1 tau)
   if (halted(s)) return;
   const int64_t gt = blk0 + blockIdx.x;
   const int2 t = tab[gt];
@@ -1120,7 +1151,7 @@ __global__ void __launch_bounds__(TPB_EST, 4) k_est(const DevChain *__restrict__
   for (int i = threadIdx.x; i < LOOP_SLOTS; i += blockDim.x) {
     lkeys[i] = -1;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) lvals[6 * i + k] = 0u;
+    for (int k = 0; k < 2 * LOOP_SUMS; ++k) lvals[2 * LOOP_SUMS * i + k] = 0u;
   }
   __syncthreads();
   const int a = cvp[0], e = cvp[ncl];
@@ -1130,13 +1161,24 @@ __global__ void __launch_bounds__(TPB_EST, 4) k_est(const DevChain *__restrict__
   const int F = C.F;
   // Ticks of every vertex of the tile, once: the fragments below a vertex
   // mostly start at vertices of the same tile.
+  // Their phase factors too (temporal moment, w1 = 2 pi / beta).
+  const uint64_t phR = C.phR;
+  const int phS = C.phS;
   const int nq = min(e - a, SMEM_CAP);
-  for (int i = threadIdx.x; i < nq; i += blockDim.x) qv[i] = q_time(vt[a + i], F);
+  for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+    const long long q = q_time(vt[a + i], F);
+    qv[i] = q;
+    if (T) ev[i] = phase_of((uint64_t)q, phR, phS, g_phase_tab);
+  }
   __syncthreads();
-  auto ticks = [&](int v) { return (v >= a && v < a + nq) ? qv[v - a] : q_time(vt[v], F); };
+  auto inq = [&](int v) { return v >= a && v < a + nq; };
+  auto ticks = [&](int v) { return inq(v) ? qv[v - a] : q_time(vt[v], F); };
+  auto phase = [&](int v) {
+    return inq(v) ? ev[v - a] : phase_of((uint64_t)q_time(vt[v], F), phR, phS, g_phase_tab);
+  };
   // Whole warps walk the tile (trip count rounded up), reconverging after
   // every vertex.
-  u128 w2 = 0, f2 = 0;  // this thread's share of sum W^2 and sum (C^2 + S^2)
+  u128 w2 = 0, f2 = 0, z2 = 0;  // this thread's share of the loops' squared sums
   for (int w0 = a; w0 < e; w0 += blockDim.x) {
     const int w = w0 + threadIdx.x;
     if (w < e) {
@@ -1156,16 +1198,24 @@ __global__ void __launch_bounds__(TPB_EST, 4) k_est(const DevChain *__restrict__
       if (f & VF_WRAP_L) dl += cxl[ci];
       long long dr = qw - (R == P ? qP : ticks(R));
       if (f & VF_WRAP_R) dr += cxr[ci];
-      const long long W = dl + dr;
-      const long long Cc = mul_q32(dl, ccl[ci]) + mul_q32(dr, ccr[ci]);
-      const long long Ss = mul_q32(dl, csl[ci]) + mul_q32(dr, csr[ci]);
+      LoopSums x;
+      x.v[0] = dl + dr;
+      x.v[1] = mul_q32(dl, ccl[ci]) + mul_q32(dr, ccr[ci]);
+      x.v[2] = mul_q32(dl, csl[ci]) + mul_q32(dr, csr[ci]);
+      // int over a fragment of e^{i w1 t} dt = (e(top) - e(bottom)) / (i w1),
+      // across the cut too (e(t + beta) = e(t)): both fragments end at w
+      x.v[3] = x.v[4] = 0;
+      if (T) {
+        const int2 ew = phase(w), eP = phase(P), eR = (R == P) ? eP : phase(R);
+        x.v[3] = 2ll * ew.x - eP.x - eR.x;
+        x.v[4] = 2ll * ew.y - eP.y - eR.y;
+      }
       if (P == R) {
         // Both upper legs of node P end at w, so P is a loop by itself and its
         // two fragments are the two below w: the loop's sums are complete here.
-        w2 += sq_abs(W);
-        f2 += sq_abs(Cc) + sq_abs(Ss);
+        loop_squares<T>(x.v, w2, f2, z2);
       } else {
-        loop_add(lkeys, lvals, rb, W, Cc, Ss, s, vb);
+        loop_add<T ? LOOP_SUMS : 3>(lkeys, lvals, rb, x, s, vb);
       }
     }
     __syncwarp();
@@ -1182,25 +1232,24 @@ __global__ void __launch_bounds__(TPB_EST, 4) k_est(const DevChain *__restrict__
   for (int h = threadIdx.x; h < LOOP_SLOTS; h += blockDim.x) {
     const int kk = lkeys[h];
     if (kk < 0) continue;
-    const unsigned long long x = sget64(lvals + 6 * h), y = sget64(lvals + 6 * h + 2),
-                             z = sget64(lvals + 6 * h + 4);
+    long long v[LOOP_SUMS] = {};
+#pragma unroll
+    for (int i = 0; i < (T ? LOOP_SUMS : 3); ++i) v[i] = (long long)sget64(lvals + 2 * (LOOP_SUMS * h + i));
     if (get_bit(s.openroot, wb, kk)) {
-      unsigned long long *r = s.acc + 4 * (vb + kk);
-      atomicAdd(r, x);
-      atomicAdd(r + 1, y);
-      atomicAdd(r + 2, z);
+      acc_add<T ? LOOP_SUMS : 3>(s, vb + kk, v);
     } else {
-      w2 += sq_abs((long long)x);
-      f2 += sq_abs((long long)y) + sq_abs((long long)z);
+      loop_squares<T>(v, w2, f2, z2);
     }
   }
-  block_sum3(newcnt, w2, f2);
+  block_sums<T>(newcnt, w2, f2, z2);
   if (threadIdx.x == 0) {
     s.tile_sum2[gt] = newcnt;
     s.tile_sw2[2 * gt] = (unsigned long long)w2;
     s.tile_sw2[2 * gt + 1] = (unsigned long long)(w2 >> 64);
     s.tile_sf2[2 * gt] = (unsigned long long)f2;
     s.tile_sf2[2 * gt + 1] = (unsigned long long)(f2 >> 64);
+    s.tile_sz2[2 * gt] = (unsigned long long)z2;
+    s.tile_sz2[2 * gt + 1] = (unsigned long long)(z2 >> 64);
   }
 }
 
@@ -1210,7 +1259,8 @@ __global__ void __launch_bounds__(TPB_EST, 4) k_est(const DevChain *__restrict__
 // operators, one barrier exchanges the warp totals, and a second pass places
 // them with warp shuffles (id order = order of the next operator list).  The
 // cell offsets come from a block scan of the per-cell counts.
-__global__ void __launch_bounds__(TPB) k_compact(const DevChain *__restrict__ ch,
+template <bool T>
+__global__ void __launch_bounds__(TPB, T ? 4 : 8) k_compact(const DevChain *__restrict__ ch,
                                                  const int2 *__restrict__ tab, int64_t blk0,
                                                  Scratch s) {
   __shared__ int64_t sm[33];
@@ -1274,37 +1324,73 @@ __global__ void __launch_bounds__(TPB) k_compact(const DevChain *__restrict__ ch
       if (m & (1 << i)) ntau[p++] = s.vtau[vb + 4 * wd + i];
     pos += __shfl_sync(0xffffffffu, inc, 31);
   }
-  // Loops that left their tile: one 32-byte accumulator record per root, read
-  // and cleared; a thread takes one 32-vertex word of the open-root bitmap.
-  u128 w2 = 0, f2 = 0;
+  // Loops that left their tile: one 32-byte accumulator record per root (and
+  // its Zi word), read and cleared; a thread takes one 32-vertex word of the
+  // open-root bitmap.  With the Zi words, the next root's reads are issued
+  // before the current root is cleared (two roots in flight per thread);
+  // without them, the plain loop needs fewer registers and more resident
+  // warps hide the latency better.
+  u128 w2 = 0, f2 = 0, z2 = 0;
   const int64_t wfirst = (vb + a) >> 5, wlast = (vb + e - 1) >> 5;
   for (int64_t wd = wfirst + threadIdx.x; e > a && wd <= wlast; wd += blockDim.x) {
     uint32_t bits = __ldcg(s.openroot + wd);
     const int64_t v0 = (wd << 5) - vb;
     if (v0 < a) bits &= ~0u << (a - v0);
     if (v0 + 32 > e) bits &= (e - v0 >= 32) ? ~0u : ((1u << (e - v0)) - 1u);
-    while (bits) {
-      const int i = __ffs(bits) - 1;
-      bits &= bits - 1;
-      ulonglong2 *r = (ulonglong2 *)(s.acc + 4 * (vb + v0 + i));
-      const ulonglong2 x = r[0], y = r[1];
-      r[0] = make_ulonglong2(0ull, 0ull);
-      r[1] = make_ulonglong2(0ull, 0ull);
+    if (!T) {
+      while (bits) {
+        const int64_t v = vb + v0 + __ffs(bits) - 1;
+        bits &= bits - 1;
+        const ulonglong2 x = s.acc2[2 * v], y = s.acc2[2 * v + 1];
+        s.acc2[2 * v] = make_ulonglong2(0ull, 0ull);
+        s.acc2[2 * v + 1] = make_ulonglong2(0ull, 0ull);
+        w2 += sq_abs((long long)x.x);
+        f2 += sq_abs((long long)x.y) + sq_abs((long long)y.x);
+      }
+      continue;
+    }
+    if (!bits) continue;
+    int64_t v = vb + v0 + __ffs(bits) - 1;
+    bits &= bits - 1;
+    ulonglong2 x = s.acc2[2 * v], y = s.acc2[2 * v + 1];
+    unsigned long long zi = s.accz[v];
+    for (;;) {
+      const bool more = bits != 0;
+      int64_t vn = 0;
+      ulonglong2 xn, yn;
+      unsigned long long zn = 0ull;
+      if (more) {
+        vn = vb + v0 + __ffs(bits) - 1;
+        bits &= bits - 1;
+        xn = s.acc2[2 * vn];
+        yn = s.acc2[2 * vn + 1];
+        zn = s.accz[vn];
+      }
+      s.acc2[2 * v] = make_ulonglong2(0ull, 0ull);
+      s.acc2[2 * v + 1] = make_ulonglong2(0ull, 0ull);
+      s.accz[v] = 0ull;
       w2 += sq_abs((long long)x.x);
       f2 += sq_abs((long long)x.y) + sq_abs((long long)y.x);
+      z2 += sq_abs((long long)y.y) + sq_abs((long long)zi);
+      if (!more) break;
+      v = vn;
+      x = xn;
+      y = yn;
+      zi = zn;
     }
   }
   long long none = 0;
-  block_sum3(none, w2, f2);
+  block_sums<T>(none, w2, f2, z2);
   if (threadIdx.x == 0) {
-    u128 x = ((u128)s.tile_sw2[2 * gt + 1] << 64) | s.tile_sw2[2 * gt];
-    u128 y = ((u128)s.tile_sf2[2 * gt + 1] << 64) | s.tile_sf2[2 * gt];
-    x += w2;
-    y += f2;
-    s.tile_sw2[2 * gt] = (unsigned long long)x;
-    s.tile_sw2[2 * gt + 1] = (unsigned long long)(x >> 64);
-    s.tile_sf2[2 * gt] = (unsigned long long)y;
-    s.tile_sf2[2 * gt + 1] = (unsigned long long)(y >> 64);
+    auto add = [&](unsigned long long *t, u128 v) {
+      u128 x = ((u128)t[2 * gt + 1] << 64) | t[2 * gt];
+      x += v;
+      t[2 * gt] = (unsigned long long)x;
+      t[2 * gt + 1] = (unsigned long long)(x >> 64);
+    };
+    add(s.tile_sw2, w2);
+    add(s.tile_sf2, f2);
+    add(s.tile_sz2, z2);
   }
 }
 
@@ -1364,13 +1450,14 @@ __global__ void __launch_bounds__(1024) k_final(DevChain *__restrict__ ch, Scrat
   if (halted(s)) return;
   DevChain &C = ch[blockIdx.x];
   int64_t roots = 0, nfree = 0;
-  u128 w2 = 0, f2 = 0;
+  u128 w2 = 0, f2 = 0, z2 = 0;
 #pragma unroll 4
   for (int i = threadIdx.x; i < C.ntile; i += blockDim.x) {
     const int64_t g = C.tile0 + i;
     roots += s.tile_roots[g];
     w2 += ((u128)s.tile_sw2[2 * g + 1] << 64) | s.tile_sw2[2 * g];
     f2 += ((u128)s.tile_sf2[2 * g + 1] << 64) | s.tile_sf2[2 * g];
+    z2 += ((u128)s.tile_sz2[2 * g + 1] << 64) | s.tile_sz2[2 * g];
   }
   for (int i = threadIdx.x; i < C.nsiteblk; i += blockDim.x) {
     const int64_t g = C.site0 + i;
@@ -1382,6 +1469,7 @@ __global__ void __launch_bounds__(1024) k_final(DevChain *__restrict__ ch, Scrat
   nfree = block_sum<int64_t>(nfree, sm);
   w2 = block_sum_u128(w2);
   f2 = block_sum_u128(f2);
+  z2 = block_sum_u128(z2);  // vertex-free loops are whole periods: no temporal term
   if (threadIdx.x != 0) return;
   lcqmc_record r;
   r.n = C.n;
@@ -1396,6 +1484,8 @@ __global__ void __launch_bounds__(1024) k_final(DevChain *__restrict__ ch, Scrat
   r.sw2_hi = (unsigned long long)(w2 >> 64);
   r.sf2_lo = (unsigned long long)f2;
   r.sf2_hi = (unsigned long long)(f2 >> 64);
+  r.sz2_lo = (unsigned long long)z2;
+  r.sz2_hi = (unsigned long long)(z2 >> 64);
   const double two64 = 18446744073709551616.0;
   const double dsw = __dadd_rn(__dmul_rn((double)r.sw2_hi, two64), (double)r.sw2_lo);
   const double dsf = __dadd_rn(__dmul_rn((double)r.sf2_hi, two64), (double)r.sf2_lo);
@@ -1404,17 +1494,24 @@ __global__ void __launch_bounds__(1024) k_final(DevChain *__restrict__ ch, Scrat
                        __ddiv_rn((double)C.n, __dmul_rn(C.beta, (double)C.L)));
   r.chi_s = __ddiv_rn(ldexp(dsw, -2 * C.F), bl);
   r.chi_q = __ddiv_rn(ldexp(dsf, -2 * C.F), bl);
+  // |int e^{i w1 t} dt|^2 = |Z|^2 2^-60 / w1^2 with w1 = 2 pi / beta:
+  // chi_w = sz2 2^-60 beta / (16 pi^2 L)
+  const double kPi = 3.14159265358979323846;
+  const double dsz = __dadd_rn(__dmul_rn((double)r.sz2_hi, two64), (double)r.sz2_lo);
+  r.chi_w = __ddiv_rn(__dmul_rn(ldexp(dsz, -60), C.beta),
+                      __dmul_rn(__dmul_rn(__dmul_rn(16.0, kPi), kPi), (double)C.L));
   C.ring[C.n_rec % C.ring_cap] = r;
   C.n_rec += 1;
-  const double v[8] = {r.energy,
-                       r.chi_s,
-                       r.chi_q,
-                       (double)r.n,
-                       (double)r.n_off_new,
-                       (double)r.n_seg,
-                       (double)r.n_clusters,
-                       (double)(r.n_seg + 2 * r.n)};
-  for (int k = 0; k < 8; ++k) {
+  const double v[NOBS] = {r.energy,
+                          r.chi_s,
+                          r.chi_q,
+                          (double)r.n,
+                          (double)r.n_off_new,
+                          (double)r.n_seg,
+                          (double)r.n_clusters,
+                          (double)(r.n_seg + 2 * r.n),
+                          r.chi_w};
+  for (int k = 0; k < NOBS; ++k) {
     C.sum[k] += v[k];
     C.sumsq[k] += v[k] * v[k];
   }
@@ -1462,17 +1559,55 @@ void launch_compress(const Launch &L, cudaStream_t st) {
   if (n) k_compress<<<g1(n), TILE, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
 }
 
-// Kernel attributes set once per process (none needed at present).
-int init_kernel_attributes() { return 0; }
+// Per-vertex staging of the loop-properties kernel: ticks and phase factors.
+constexpr size_t EST_DYN_SMEM = SMEM_CAP * (sizeof(long long) + sizeof(int2));
+
+// Device tables and kernel attributes, set once per process and device: the
+// phase factor table (cos and sin of 2 pi k / 2^16 rounded to 30 fractional
+// bits) and the loop-properties kernel's shared memory size.
+int init_kernel_attributes() {
+  static std::mutex mu;
+  static bool done[256];
+  static int2 tab[(1 << PHASE_BITS) + 1];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return -1;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return 0;
+  for (int k = 0; k <= (1 << PHASE_BITS); ++k) {
+    const double ang = (2.0 * M_PI * (double)k) / (double)(1 << PHASE_BITS);
+    tab[k] = make_int2((int)std::llrint(std::ldexp(std::cos(ang), 30)),
+                       (int)std::llrint(std::ldexp(std::sin(ang), 30)));
+  }
+  if (cudaMemcpyToSymbol(g_phase_tab, tab, sizeof(tab)) != cudaSuccess) return -1;
+  if (cudaFuncSetAttribute(k_est<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)EST_DYN_SMEM) != cudaSuccess ||
+      cudaFuncSetAttribute(k_est<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)EST_DYN_SMEM) != cudaSuccess)
+    return -1;
+  done[dev] = true;
+  return 0;
+}
 
 void launch_est(const Launch &L, cudaStream_t st) {
-  if (L.ntile[0]) k_est<1><<<g1(L.ntile[0]), TPB_EST, 0, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
-  if (L.ntile[1]) k_est<2><<<g1(L.ntile[1]), TPB_EST, 0, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
+  // without the temporal moment only the ticks are staged
+  const size_t dyn = L.temporal ? EST_DYN_SMEM : SMEM_CAP * sizeof(long long);
+  if (L.temporal) {
+    if (L.ntile[0]) k_est<1, true><<<g1(L.ntile[0]), TPB_EST, dyn, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
+    if (L.ntile[1]) k_est<2, true><<<g1(L.ntile[1]), TPB_EST, dyn, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
+  } else {
+    if (L.ntile[0]) k_est<1, false><<<g1(L.ntile[0]), TPB_EST, dyn, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
+    if (L.ntile[1]) k_est<2, false><<<g1(L.ntile[1]), TPB_EST, dyn, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
+  }
 }
 
 void launch_compact(const Launch &L, cudaStream_t st) {
   const int64_t n = L.ntile[0] + L.ntile[1];
-  if (n) k_compact<<<g1(n), TPB, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
+  if (n) {
+    if (L.temporal)
+      k_compact<true><<<g1(n), TPB, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
+    else
+      k_compact<false><<<g1(n), TPB, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
+  }
 }
 
 void launch_sites(const Launch &L, cudaStream_t st) {

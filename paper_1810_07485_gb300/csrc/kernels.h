@@ -15,6 +15,7 @@ struct Launch {
   int64_t ntile[2], tile0[2];
   int64_t nsiteblk[2], site0[2];
   int64_t nbondblk[2], bond0[2];
+  int temporal;  // measure the temporal moment chi(pi, 2 pi / beta) too
 };
 
 void set_full_table(const uint64_t *T, cudaStream_t st);

@@ -27,9 +27,13 @@ class LcqmcError(RuntimeError):
         self.code = code
 
 
+NOBS = 9  # E/L, chi_s, chi(pi+2pi/L), n, n_off, fragments, loops, V+E, chi(pi, 2pi/beta)
+
+
 class Obs(ctypes.Structure):
-    _fields_ = [("n_updates", ctypes.c_int64), ("sum", ctypes.c_double * 8),
-                ("sumsq", ctypes.c_double * 8), ("xi", ctypes.c_double)]
+    _fields_ = [("n_updates", ctypes.c_int64), ("sum", ctypes.c_double * NOBS),
+                ("sumsq", ctypes.c_double * NOBS), ("xi", ctypes.c_double),
+                ("xi_tau", ctypes.c_double), ("gap", ctypes.c_double)]
 
 
 class Record(ctypes.Structure):
@@ -38,14 +42,18 @@ class Record(ctypes.Structure):
                 ("F", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("sw2_lo", ctypes.c_uint64), ("sw2_hi", ctypes.c_uint64),
                 ("sf2_lo", ctypes.c_uint64), ("sf2_hi", ctypes.c_uint64),
-                ("energy", ctypes.c_double), ("chi_s", ctypes.c_double), ("chi_q", ctypes.c_double)]
+                ("sz2_lo", ctypes.c_uint64), ("sz2_hi", ctypes.c_uint64),
+                ("energy", ctypes.c_double), ("chi_s", ctypes.c_double), ("chi_q", ctypes.c_double),
+                ("chi_w", ctypes.c_double)]
 
 
 RECORD_DTYPE = np.dtype([("n", np.int64), ("n_off_old", np.int64), ("n_off_new", np.int64),
                          ("n_free", np.int64), ("n_clusters", np.int64), ("n_seg", np.int64),
                          ("F", np.int32), ("pad", np.int32), ("sw2_lo", np.uint64),
                          ("sw2_hi", np.uint64), ("sf2_lo", np.uint64), ("sf2_hi", np.uint64),
-                         ("energy", np.float64), ("chi_s", np.float64), ("chi_q", np.float64)])
+                         ("sz2_lo", np.uint64), ("sz2_hi", np.uint64),
+                         ("energy", np.float64), ("chi_s", np.float64), ("chi_q", np.float64),
+                         ("chi_w", np.float64)])
 assert RECORD_DTYPE.itemsize == ctypes.sizeof(Record)
 
 
@@ -104,11 +112,13 @@ def lib():
         "lcqmc_checkpoint": [vp, vp, P(ctypes.c_size_t)],
         "lcqmc_restore": [vp, vp, ctypes.c_size_t],
         "lcqmc_set_phase_timing": [vp, i32],
+        "lcqmc_set_temporal": [vp, i32],
         "lcqmc_get_phase_times": [vp, vp, i32],
         "lcqmc_destroy": [vp],
         "lcqmc_batch_create": [i64, vp, vp, P(vp)],
         "lcqmc_batch_update": [vp, i64],
         "lcqmc_batch_sync": [vp],
+        "lcqmc_batch_set_temporal": [vp, i32],
         "lcqmc_batch_measure": [vp, i64, P(Obs)],
         "lcqmc_batch_get_records": [vp, i64, vp, i64, P(i64)],
         "lcqmc_batch_destroy": [vp],
@@ -259,6 +269,10 @@ class Chain:
     def set_phase_timing(self, on=True):
         _check(lib().lcqmc_set_phase_timing(self.h, 1 if on else 0))
 
+    def set_temporal(self, on=True):
+        """Temporal moment chi(pi, 2 pi / beta) on or off (off after create)."""
+        _check(lib().lcqmc_set_temporal(self.h, 1 if on else 0))
+
     def phase_times(self):
         ms = np.zeros(NPHASE)
         _check(lib().lcqmc_get_phase_times(self.h, _p(ms), NPHASE))
@@ -295,6 +309,9 @@ class Batch:
 
     def sync(self):
         _check(lib().lcqmc_batch_sync(self.h))
+
+    def set_temporal(self, on=True):
+        _check(lib().lcqmc_batch_set_temporal(self.h, 1 if on else 0))
 
     def measure(self, i):
         o = Obs()

@@ -29,9 +29,9 @@ def gpu_state(ch):
 
 def assert_records_equal(rg, ro, ctx=""):
     for f in ("n", "n_off_old", "n_off_new", "n_free", "n_clusters", "n_seg", "F", "sw2_lo",
-              "sw2_hi", "sf2_lo", "sf2_hi"):
+              "sw2_hi", "sf2_lo", "sf2_hi", "sz2_lo", "sz2_hi"):
         assert int(rg[f]) == int(ro[f]), (ctx, f, int(rg[f]), int(ro[f]))
-    for f in ("energy", "chi_s", "chi_q"):
+    for f in ("energy", "chi_s", "chi_q", "chi_w"):
         a, b = float(rg[f]), float(ro[f])
         assert abs(a - b) <= REL_TOL * max(abs(a), abs(b), 1e-300), (ctx, f, a, b)
 
@@ -55,6 +55,7 @@ def run_parity(L, beta, Q=1, J=1.0, seed=1, nup=12, graph_every=1):
     p = orc.params(L, beta, J=J, Q=Q, seed=seed)
     st = orc.neel(p)
     ch = lc.Chain(L, beta, S=Q / 2, J=J, seed=seed)
+    ch.set_temporal(True)
     try:
         for t in range(nup):
             new, ro, go = orc.keyed_update(p, t, st, graph=(t % graph_every == 0))
@@ -115,6 +116,7 @@ def test_empty_and_tiny_beta():
     p = orc.params(16, 1e-6, seed=3)
     st = orc.neel(p)
     ch = lc.Chain(16, 1e-6, seed=3)
+    ch.set_temporal(True)
     orc_recs = orc.keyed_run(p, 0, 40, st)
     ch.update(40)
     rg = ch.records()
@@ -132,6 +134,7 @@ def test_import_thermalized_state():
     st = orc.neel(p)
     orc.keyed_run(p, 0, 40, st)
     ch = lc.Chain(L, beta, seed=11)
+    ch.set_temporal(True)
     ch.import_config(st.s0, st.op_ptr.astype(np.int32), st.op_tau, 40)
     assert_state_equal(gpu_state(ch), st)
     for t in range(40, 50):
@@ -179,6 +182,7 @@ def test_capacity_growth_replays_identically():
     st = orc.neel(p)
     recs = orc.keyed_run(p, 0, 30, st)
     ch = lc.Chain(12, 60.0, S=1.0, seed=4)
+    ch.set_temporal(True)
     ch.update(30)
     rg = ch.records()
     for a, b in zip(rg, recs):
@@ -189,6 +193,7 @@ def test_capacity_growth_replays_identically():
 def test_records_and_measure_consistent():
     lc = gpu()
     ch = lc.Chain(16, 8.0, seed=21)
+    ch.set_temporal(True)
     ch.update(100)
     r = ch.records()
     o = ch.measure()
@@ -196,6 +201,11 @@ def test_records_and_measure_consistent():
     assert o.sum[0] == pytest.approx(r["energy"].sum(), rel=1e-12)
     assert o.sum[1] == pytest.approx(r["chi_s"].sum(), rel=1e-12)
     assert o.sum[3] == pytest.approx(r["n"].sum(), rel=1e-12)
+    assert o.sum[8] == pytest.approx(r["chi_w"].sum(), rel=1e-12)
+    # imaginary-time second moment and the gap derived from the means
+    xt = 8.0 / (2 * np.pi) * np.sqrt(r["chi_s"].mean() / r["chi_w"].mean() - 1)
+    assert o.xi_tau == pytest.approx(xt, rel=1e-10)
+    assert o.gap == pytest.approx(1 / xt, rel=1e-10)
 
 
 @pytest.mark.parametrize("L,beta,Q", [(8, 4.0, 1), (12, 1.0, 1), (4, 1.0, 2)])
@@ -203,6 +213,7 @@ def test_gpu_vs_ed(L, beta, Q):
     # Estimators within 3 standard errors of exact diagonalization.
     lc = gpu()
     ch = lc.Chain(L, beta, S=Q / 2, seed=77)
+    ch.set_temporal(True)
     ch.update(1000)
     ch.records()
     parts = []
@@ -211,7 +222,7 @@ def test_gpu_vs_ed(L, beta, Q):
         parts.append(ch.records())
     r = np.concatenate(parts)
     ex = ed.thermal(L, beta, S=Q / 2)
-    for name in ("energy", "chi_s", "chi_q"):
+    for name in ("energy", "chi_s", "chi_q", "chi_w"):
         m, e = stats.mean_err(r[name], 100)
         assert stats.within_sigma(m, e, ex[name], 3.0), (name, m, e, ex[name])
 
@@ -227,3 +238,53 @@ def test_batch_matches_single_chains():
         ch = lc.Chain(s["L"], s["beta"], S=s.get("S", 0.5), seed=s["seed"])
         ch.update(25)
         assert np.array_equal(b.records(i), ch.records()), i
+
+
+def test_temporal_switch_leaves_standard_results_unchanged():
+    # The temporal moment is measured only when switched on; with it off the
+    # record's sz2 and chi_w are 0 and every other field and the state are
+    # bit-identical.  Switching mid-run takes effect at the next update.
+    lc = gpu()
+    a = lc.Chain(96, 30.0, seed=13)
+    b = lc.Chain(96, 30.0, seed=13)
+    b.set_temporal(True)
+    a.update(8)
+    b.update(8)
+    a.set_temporal(True)   # on from update 8
+    b.set_temporal(False)  # off from update 8
+    a.update(4)
+    b.update(4)
+    ra, rb = a.records(), b.records()
+    std = [f for f in ra.dtype.names if f not in ("sz2_lo", "sz2_hi", "chi_w")]
+    for f in std:
+        assert np.array_equal(ra[f], rb[f]), f
+    assert (ra["chi_w"][:8] == 0).all() and (ra["sz2_lo"][:8] == 0).all() and (ra["sz2_hi"][:8] == 0).all()
+    assert (rb["chi_w"][8:] == 0).all() and (rb["sz2_lo"][8:] == 0).all()
+    assert (ra["chi_w"][8:] > 0).all() and (rb["chi_w"][:8] > 0).all()
+    assert_state_equal(gpu_state(a), gpu_state(b))
+    # the measured half agrees with the oracle at the same updates
+    p = orc.params(96, 30.0, seed=13)
+    st = orc.neel(p)
+    ro = orc.keyed_run(p, 0, 12, st)
+    for t in range(12):
+        assert_records_equal(ra[t] if t >= 8 else rb[t], ro[t], f"sweep={t}")
+    oa, ob = a.measure(), b.measure()
+    assert oa.sum[0] == ob.sum[0]
+    assert oa.sum[8] == pytest.approx(ra["chi_w"].sum(), rel=1e-12)
+    a.close()
+    b.close()
+
+
+def test_batch_temporal_switch():
+    lc = gpu()
+    specs = [dict(L=8, beta=4.0, seed=1), dict(L=40, beta=20.0, S=1.0, seed=2)]
+    b = lc.Batch(specs)
+    b.set_temporal(True)
+    b.update(5)
+    for i, s in enumerate(specs):
+        p = orc.params(s["L"], s["beta"], Q=int(round(2 * s.get("S", 0.5))), seed=s["seed"])
+        ro = orc.keyed_run(p, 0, 5, orc.neel(p))
+        rg = b.records(i)
+        for t in range(5):
+            assert_records_equal(rg[t], ro[t], (i, t))
+    b.close()
