@@ -41,10 +41,12 @@ KERNELS_PER_UPDATE = 11
 # DRAM bytes per vertex of each phase's kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture at L=16384, beta=4096, divided by
 # that update's vertex count; profiles/topkernels_L16384_beta4096.md), valid
-# for the kernel source with this sha1 only.
-TRAFFIC_PER_VERTEX = {"insert": 13.1, "link_union": 26.8, "loop_ids": 7.5, "loop_props": 24.9,
+# for the kernel source with this sha1 only.  The second table is for the
+# kernels that differ with the temporal moment on.
+TRAFFIC_PER_VERTEX = {"insert": 13.1, "link_union": 26.8, "loop_ids": 7.5, "loop_props": 25.0,
                       "op_rewrite": 14.8}
-TRAFFIC_KERNELS_SHA1 = "d8bf4742c379e5b33c6c4798fbb7847926405f3b"
+TRAFFIC_PER_VERTEX_TEMPORAL = dict(TRAFFIC_PER_VERTEX, loop_props=25.8, op_rewrite=16.6)
+TRAFFIC_KERNELS_SHA1 = "533144529c2afbfdafdae8babcf2c4aaf6a1d928"
 
 
 def kernels_sha1():
@@ -261,8 +263,9 @@ def run_ours(args, world, rank, local):
     peak, peak_kind = load_peaks()
     achieved = nb[dom] / (ph[dom] * 1e-3) / 1e9 if ph[dom] > 0 else 0.0
     traffic = None  # bytes per launch, only while the kernels are the profiled ones
-    if kernels_sha1() == TRAFFIC_KERNELS_SHA1 and dom in TRAFFIC_PER_VERTEX:
-        traffic = TRAFFIC_PER_VERTEX[dom] * float(pr["n"].mean())
+    tpv = TRAFFIC_PER_VERTEX_TEMPORAL if args.temporal else TRAFFIC_PER_VERTEX
+    if kernels_sha1() == TRAFFIC_KERNELS_SHA1 and dom in tpv:
+        traffic = tpv[dom] * float(pr["n"].mean())
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "algorithmic_bytes": nb[dom] / nph, "kernel": dom, "peak_kind": peak_kind,
