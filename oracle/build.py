@@ -8,7 +8,7 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["common.c", "keyed.c", "serial.c"]
+SOURCES = ["common.c", "keyed.c", "serial.c", "sw.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

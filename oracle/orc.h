@@ -22,6 +22,9 @@
  *                         walking the loops of the segment graph (no
  *                         union-find).  Given the same state, seed and sweep it
  *                         defines every integer output of the update exactly.
+ *
+ * And the Swendsen-Wang update of the 2D Ising model on which the paper
+ * benchmarks its union-find (Sec. 4.1): orc_sw_update (sw.c).
  */
 #ifndef ORC_H
 #define ORC_H
@@ -45,6 +48,8 @@ extern "C" {
 #define ORC_TAG_FREE 3u
 #define ORC_TAG_PERM 4u
 #define ORC_TAG_SERIAL 9u
+#define ORC_TAG_SWBOND 5u
+#define ORC_TAG_SWFLIP 6u
 
 typedef struct {
   int64_t L;      /* original sites (even, >= 2) */
@@ -143,6 +148,39 @@ int orc_serial_update(const orc_params *p, uint32_t sweep, uint8_t *s0, int64_t 
 int orc_serial_run(const orc_params *p, uint32_t sweep0, int64_t n_updates, uint8_t *s0,
                    int64_t *n_ops, double *ops_tau, int64_t *ops_bond, int64_t op_cap,
                    orc_record *recs);
+
+/*
+ * Swendsen-Wang update of the L x L periodic Ising model (Sec. 4.1 benchmark).
+ * Site i = y L + x, spin s[i] in {0, 1} (sigma = 1 - 2 s).  Bonds R(i) = (i,
+ * right neighbour) and D(i) = (i, lower neighbour): 2N bonds, N = L^2.  The
+ * draws of site i are Philox(ctr = (ORC_TAG_SWBOND << 24, i, 0, sweep),
+ * key = seed): word 0 for R(i), word 1 for D(i).  A bond is active iff its two
+ * spins are equal and its draw w < T = orc_sw_threshold(K).  A cluster's id is
+ * its smallest site index r; its coin is bit (r mod 128) of Philox(ctr =
+ * (ORC_TAG_SWFLIP << 24, r / 128, 0, sweep)), words in order, low bit first.
+ */
+typedef struct {
+  int64_t n_eq;        /* bonds whose spins are equal, before the update */
+  int64_t n_act;       /* activated bonds */
+  int64_t n_clusters;  /* clusters (isolated sites included) */
+  int64_t max_cluster; /* sites of the largest cluster */
+  uint64_t sum_c2;     /* sum over clusters of size^2 (< 2^62 for N < 2^31) */
+  int64_t mag;         /* sum of sigma after the update */
+  double energy;       /* (2N - 2 n_eq) / N: energy per site before the update */
+  double chi;          /* sum_c2 / N: improved estimator of <M^2> / N */
+} orc_sw_record;
+
+uint64_t orc_sw_threshold(double K);
+
+/* One update in place on s[N].  Optional outputs (may be NULL): root_out[N]
+ * (cluster id of every site), bond_out[2N] (R(i) at 2i, D(i) at 2i+1).
+ * Returns 0, -1 (memory) or -2 (L < 2). */
+int orc_sw_update(int64_t L, double K, uint64_t seed, uint32_t sweep, uint8_t *s,
+                  int64_t *root_out, uint8_t *bond_out, orc_sw_record *rec);
+
+/* n updates in place, sweeps sweep0, sweep0+1, ... */
+int orc_sw_run(int64_t L, double K, uint64_t seed, uint32_t sweep0, int64_t n, uint8_t *s,
+               orc_sw_record *recs);
 
 #ifdef __cplusplus
 }

@@ -42,6 +42,19 @@ RECORD_DTYPE = np.dtype([(name, np.int64 if t in (ctypes.c_int64,) else
 assert RECORD_DTYPE.itemsize == ctypes.sizeof(Record)
 
 
+class SwRecord(ctypes.Structure):
+    _fields_ = [("n_eq", ctypes.c_int64), ("n_act", ctypes.c_int64),
+                ("n_clusters", ctypes.c_int64), ("max_cluster", ctypes.c_int64),
+                ("sum_c2", ctypes.c_uint64), ("mag", ctypes.c_int64),
+                ("energy", ctypes.c_double), ("chi", ctypes.c_double)]
+
+
+SW_RECORD_DTYPE = np.dtype([("n_eq", np.int64), ("n_act", np.int64), ("n_clusters", np.int64),
+                            ("max_cluster", np.int64), ("sum_c2", np.uint64), ("mag", np.int64),
+                            ("energy", np.float64), ("chi", np.float64)])
+assert SW_RECORD_DTYPE.itemsize == ctypes.sizeof(SwRecord)
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -73,6 +86,14 @@ def lib():
                                 P(ctypes.c_int64)]
         L.orc_phase_recip.argtypes = [ctypes.c_int64, P(ctypes.c_int)]
         L.orc_phase_recip.restype = ctypes.c_uint64
+        L.orc_sw_threshold.argtypes = [ctypes.c_double]
+        L.orc_sw_threshold.restype = ctypes.c_uint64
+        L.orc_sw_update.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
+                                    vp, vp, vp, P(SwRecord)]
+        L.orc_sw_update.restype = ctypes.c_int
+        L.orc_sw_run.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
+                                 ctypes.c_int64, vp, vp]
+        L.orc_sw_run.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -239,3 +260,35 @@ def phase(q, qbeta):
     rb = lib().orc_phase_recip(int(qbeta), ctypes.byref(sh))
     lib().orc_phase(int(q) & (2**64 - 1), rb, sh.value, ctypes.byref(c), ctypes.byref(sn))
     return c.value, sn.value
+
+
+# ---- Swendsen-Wang 2D Ising (Sec. 4.1 benchmark) ---------------------------------
+def sw_threshold(K):
+    return int(lib().orc_sw_threshold(float(K)))
+
+
+def sw_update(L, K, seed, sweep, s, roots=False, bonds=False):
+    """One Swendsen-Wang update in place on s (uint8, L*L, row-major).
+    Returns (record, roots or None, bonds or None)."""
+    assert s.dtype == np.uint8 and s.flags.c_contiguous and s.size == L * L
+    rt = np.zeros(L * L, np.int64) if roots else None
+    bd = np.zeros(2 * L * L, np.uint8) if bonds else None
+    rec = SwRecord()
+    rc = lib().orc_sw_update(int(L), float(K), int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.c_uint32(sweep),
+                             _ptr(s), None if rt is None else _ptr(rt), None if bd is None else _ptr(bd),
+                             ctypes.byref(rec))
+    if rc != 0:
+        raise RuntimeError(f"orc_sw_update failed: {rc}")
+    r = np.frombuffer(bytes(rec), dtype=SW_RECORD_DTYPE, count=1)[0]
+    return r, rt, bd
+
+
+def sw_run(L, K, seed, sweep0, n, s):
+    """n updates in place on s; returns the records."""
+    assert s.dtype == np.uint8 and s.flags.c_contiguous and s.size == L * L
+    recs = (SwRecord * max(1, n))()
+    rc = lib().orc_sw_run(int(L), float(K), int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.c_uint32(sweep0),
+                          int(n), _ptr(s), recs)
+    if rc != 0:
+        raise RuntimeError(f"orc_sw_run failed: {rc}")
+    return np.frombuffer(bytes(recs), dtype=SW_RECORD_DTYPE, count=n).copy()
