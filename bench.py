@@ -18,11 +18,14 @@ bounded sample of the same workload.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
 import sys
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -189,6 +192,26 @@ def run_reference(args, world, rank):
         "cpu_baseline": {"value": value, "unit": "V+E/s", "cores": 1, "kind": "oracle",
                          "sample": f"keyed oracle, L={ORACLE_SAMPLE_L}, beta={beta:g}, {steps} updates after {warm}"},
         "e2e": {"value": value, "unit": "V+E/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_sw_reference(args, world, rank):
+    """Reference arm of the Swendsen-Wang mode: the CPU oracle on rank 0."""
+    if rank != 0:
+        return
+    value, dt = sw_oracle_sample(args.steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": "Swendsen-Wang site updates/s (2D Ising, union-find benchmark)",
+        "value": value, "unit": "site updates/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps * (SW_L / SW_ORACLE_L) ** 2,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"Swendsen-Wang, L={SW_L}, K=K_c; CPU oracle sample L={SW_ORACLE_L}",
+                   "L": SW_L, "K": SW_K, "sample_L": SW_ORACLE_L},
+        "cpu_baseline": {"value": value, "unit": "site updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"Swendsen-Wang oracle, L={SW_ORACLE_L}, {args.steps} updates after "
+                                   f"{args.warmup}"},
+        "e2e": {"value": value, "unit": "site updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -435,6 +458,116 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
+# Swendsen-Wang 2D Ising benchmark of the paper's union-find (Sec. 4.1):
+# L = 8192 at K_c = ln(1 + sqrt 2)/2, 128 burn-in steps from the ordered state.
+SW_L = 8192
+SW_K = math.log(1.0 + math.sqrt(2.0)) / 2.0
+SW_BURN_IN = 128
+SW_ORACLE_L = 1024
+SW_KERNELS_PER_UPDATE = 5
+SW_TILE = (64, 32)
+
+
+def sw_phase_bytes(L):
+    """Algorithmic bytes of each phase of one update (every datum read or
+    written once): spins and the local-root word per site, the tile bitmaps,
+    edge masks and partial sums per tile, the open-root bitmap per 32 sites."""
+    N = L * L
+    nt = -(-L // SW_TILE[0]) * -(-L // SW_TILE[1])
+    tile_bits = 2 * 64 * 4  # local-root and open-component bitmaps
+    return {"tile_bonds_uf": N * (1 + 4) + nt * (tile_bits + 4 + 8 + 16),
+            "boundary_merge": nt * (4 + 8),
+            "roots_flip": N * (4 + 1 + 1) + nt * (tile_bits + 24),
+            "open_sizes_record": (N // 32 + 1) * 4 + nt * 48}
+
+
+def sw_oracle_sample(steps=5, warmup=2, L=SW_ORACLE_L):
+    from oracle import orc
+    s = np.zeros(L * L, np.uint8)
+    orc.sw_run(L, SW_K, 1, 0, warmup, s)
+    t0 = time.perf_counter()
+    orc.sw_run(L, SW_K, 1, warmup, steps, s)
+    dt = time.perf_counter() - t0
+    return L * L * steps / dt, dt
+
+
+def run_sw(args, world, rank, local):
+    import torch
+
+    from paper_1810_07485_gb300 import lcqmc
+
+    torch.cuda.set_device(local)
+    L, N = SW_L, SW_L * SW_L
+    stream = torch.cuda.Stream()
+    h = lcqmc.SWIsing(L, SW_K, seed=chain_seed(rank), stream=stream.cuda_stream)
+    h.update(SW_BURN_IN + args.warmup)
+    h.sync()
+    h.records()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h.update(args.steps)
+    e1.record(stream)
+    h.sync()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    recs = h.records()
+    ms_max, units = over_ranks(world, ms, float(N * args.steps), "cuda")
+    value = units / (ms_max * 1e-3)
+    # end to end through the public API: one update and its record per step
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        h.update(1)
+        h.records()
+    e2e_s = time.perf_counter() - t0
+    e2e_max, units2 = over_ranks(world, e2e_s, float(N * args.steps), "cuda")
+    # per-phase device times
+    nph = min(10, max(3, args.steps))
+    h.set_phase_timing(True)
+    h.update(nph)
+    ph = h.phase_times()
+    h.set_phase_timing(False)
+    nb = sw_phase_bytes(L)
+    peak, peak_kind = load_peaks()
+    dom = max(ph, key=lambda k: ph[k])
+    achieved = nb[dom] * nph / (ph[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "algorithmic_bytes": nb[dom], "kernel": dom, "peak_kind": peak_kind,
+                "phase_ms_per_update": {k: ph[k] / nph for k in ph},
+                "phase_frac_of_hbm": {k: (nb[k] * nph / (ph[k] * 1e-3) / 1e9) / peak if ph[k] > 0 else None
+                                      for k in ph}}
+    cpu = None
+    if rank == 0:
+        val, dt = sw_oracle_sample()
+        cpu = {"value": val, "unit": "site updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"Swendsen-Wang oracle, L={SW_ORACLE_L}, K=K_c, 5 updates after 2 ({dt:.1f} s)"}
+    uf_ms = (ph["tile_bonds_uf"] + ph["boundary_merge"]) / nph
+    line = {
+        "metric": "Swendsen-Wang site updates/s (2D Ising, union-find benchmark)", "value": value,
+        "unit": "site updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"Swendsen-Wang, L={L}, K=K_c=ln(1+sqrt2)/2, ordered start, "
+                               f"{SW_BURN_IN}+{args.warmup} untimed steps, seed 1+rank",
+                   "L": L, "K": SW_K, "mean_clusters": float(recs["n_clusters"].mean()),
+                   "mean_largest_cluster": float(recs["max_cluster"].mean()),
+                   "union_find_ms_per_step": uf_ms,
+                   "paper_union_find_s_per_step_1_thread": 0.097,
+                   "l2": "inputs larger than L2 (spins, forest and size arrays: 0.6 GB)"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": units2 / e2e_max, "unit": "site updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": lcqmc.SW_RECORD_DTYPE.itemsize},
+        "gpu_launches": SW_KERNELS_PER_UPDATE * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -442,7 +575,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="single", choices=["single", "batched", "served"])
+    ap.add_argument("--mode", default="single", choices=["single", "batched", "served", "sw"])
     ap.add_argument("--chains", type=int, default=512)
     ap.add_argument("--updates", type=int, default=20)
     ap.add_argument("--budget-gb", type=float, default=150.0)
@@ -461,6 +594,12 @@ def main():
         return
     if args.mode == "served":
         run_served(args)
+        return
+    if args.mode == "sw":
+        if args.impl == "reference":
+            run_sw_reference(args, world, rank)
+        else:
+            run_sw(args, world, rank, local)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -283,6 +283,85 @@ int lcqmc_selftest(int which, int64_t n, uint64_t seed, int64_t *mismatches);
 /* Message of the calling thread's last failure ("" if none). */
 const char *lcqmc_last_error(void);
 
+/* ---- Swendsen-Wang update of the 2D Ising model ----------------------------
+ * The benchmark on which the paper measures its union-find alone (Sec. 4.1):
+ * classical spins sigma = +-1 on an L x L periodic square lattice, a bond
+ * between equal nearest neighbours activated with probability
+ * p = 1 - exp(-2K), every cluster of active bonds flipped with probability
+ * 1/2 (Swendsen-Wang 1987); the paper's workload is L = 8192 at
+ * K_c = ln(1 + sqrt 2)/2.
+ *
+ * Keyed definition (bit-exact, as the CPU oracle's): site i = y L + x, spin
+ * s[i] in {0, 1} with sigma = 1 - 2 s.  Bonds R(i) = (i, (x+1 mod L, y)) and
+ * D(i) = (i, (x, y+1 mod L)): 2 L^2 bonds.  The draws of site i are
+ * Philox4x32-10(counter = (5 << 24, i, 0, sweep), key = seed): word 0 for
+ * R(i), word 1 for D(i).  A bond is active iff its spins are equal and its
+ * draw is below T = round(2^32 (1 - e^{-2K})).  A cluster is named by its
+ * smallest site index r; it flips iff bit (r mod 128) of Philox4x32-10(
+ * counter = (6 << 24, r / 128, 0, sweep), key = seed) is 1 (words in order,
+ * low bit first).  Update t of a lattice created (or set) at sweep t0 uses
+ * sweep t0 + t.  The handle owns all device memory (about 10.5 B per site);
+ * calls on one handle are not thread-safe. */
+typedef struct lcqmc_sw *lcqmc_sw_t;
+
+typedef struct {
+  int64_t sweep;        /* sweep counter of this update */
+  int64_t n_eq;         /* bonds with equal spins, before the update */
+  int64_t n_act;        /* active bonds */
+  int64_t n_clusters;   /* clusters, single sites included */
+  int64_t max_cluster;  /* sites of the largest cluster */
+  uint64_t sum_c2;      /* sum over clusters of size^2 (exact) */
+  int64_t mag;          /* sum of sigma after the update */
+  double energy;        /* (2N - 2 n_eq) / N: -(1/N) sum_bonds sigma sigma before the update */
+  double chi;           /* sum_c2 / N: improved estimator of <M^2> / N */
+} lcqmc_sw_record;
+
+#define LCQMC_SW_NOBS 4
+typedef struct {
+  int64_t n_updates;
+  /* running sums and sums of squares since create of: energy, chi,
+   * M^2 / N and |M| / N (M after each update) */
+  double sum[LCQMC_SW_NOBS], sumsq[LCQMC_SW_NOBS];
+} lcqmc_sw_obs;
+
+/* New lattice, every sigma = +1, sweep 0.  L in [2, 46340] (L^2 < 2^31), K
+ * >= 0 finite (LCQMC_E_INVAL otherwise).  cuda_stream: the stream all work of
+ * the handle runs on (NULL: a stream of its own). */
+int lcqmc_sw_create(int64_t L, double K, uint64_t seed, void *cuda_stream, lcqmc_sw_t *out);
+/* Enqueues n updates (stream-ordered, no wait).  Each appends one record to a
+ * ring of 4096 on the device. */
+int lcqmc_sw_update(lcqmc_sw_t h, int64_t n);
+/* Waits for the enqueued updates; LCQMC_E_DEVICE_TIMEOUT if a bounded
+ * union-find walk ran out (the update stops and the spins are left as they
+ * were before it). */
+int lcqmc_sw_sync(lcqmc_sw_t h);
+/* Waits, then copies up to max_n records not read before (oldest first) to
+ * out (host, caller-owned); *n_out = their number.  Records older than the
+ * last 4096 are lost. */
+int lcqmc_sw_get_records(lcqmc_sw_t h, lcqmc_sw_record *out, int64_t max_n, int64_t *n_out);
+/* Waits, then the running sums since create. */
+int lcqmc_sw_measure(lcqmc_sw_t h, lcqmc_sw_obs *out);
+/* Waits, then replaces the spins (host array of L^2 bytes, each 0 or 1, else
+ * LCQMC_E_STATE) and sets the next update's sweep counter. */
+int lcqmc_sw_set_spins(lcqmc_sw_t h, const uint8_t *spins, uint32_t sweep);
+/* Waits, then copies the spins (L^2 bytes, row-major) to the host. */
+int lcqmc_sw_get_spins(lcqmc_sw_t h, uint8_t *spins);
+/* Waits, then the cluster name of every site (L^2 int32, host) in the last
+ * update (LCQMC_E_STATE before the first). */
+int lcqmc_sw_get_roots(lcqmc_sw_t h, int32_t *roots);
+/* Per-phase device times (CUDA events, off by default; on: updates run
+ * without the captured graph).  Phases: [0] bond draws and union-find inside
+ * each 64 x 32 tile, [1] tile-boundary bonds in the global forest, [2] roots,
+ * coins and flips, [3] open clusters' sizes and the record.  ms: summed
+ * milliseconds since timing was switched on. */
+#define LCQMC_SW_NPHASE 4
+int lcqmc_sw_set_phase_timing(lcqmc_sw_t h, int enable);
+int lcqmc_sw_get_phase_times(lcqmc_sw_t h, double *ms, int nphase);
+/* The handle's CUDA stream (for events around updates). */
+void *lcqmc_sw_stream(lcqmc_sw_t h);
+/* Waits for the handle's work and frees everything it owns. */
+int lcqmc_sw_destroy(lcqmc_sw_t h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblcqmc.so")
-SOURCES = ["kernels.cu", "engine.cu", "api.cu", "server.cu", "noalloc.cu"]
+SOURCES = ["kernels.cu", "engine.cu", "api.cu", "server.cu", "noalloc.cu", "sw.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -36,6 +36,21 @@ class Obs(ctypes.Structure):
                 ("xi_tau", ctypes.c_double), ("gap", ctypes.c_double)]
 
 
+SW_NOBS = 4  # energy per site, sum_c |c|^2 / N, M^2 / N, |M| / N
+SW_NPHASE = 4
+SW_PHASES = ("tile_bonds_uf", "boundary_merge", "roots_flip", "open_sizes_record")
+
+
+class SwObs(ctypes.Structure):
+    _fields_ = [("n_updates", ctypes.c_int64), ("sum", ctypes.c_double * SW_NOBS),
+                ("sumsq", ctypes.c_double * SW_NOBS)]
+
+
+SW_RECORD_DTYPE = np.dtype([("sweep", np.int64), ("n_eq", np.int64), ("n_act", np.int64),
+                            ("n_clusters", np.int64), ("max_cluster", np.int64), ("sum_c2", np.uint64),
+                            ("mag", np.int64), ("energy", np.float64), ("chi", np.float64)])
+
+
 class Record(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_off_old", ctypes.c_int64), ("n_off_new", ctypes.c_int64),
                 ("n_free", ctypes.c_int64), ("n_clusters", ctypes.c_int64), ("n_seg", ctypes.c_int64),
@@ -130,6 +145,17 @@ def lib():
         "lcqmc_footprint": [i64, dbl, dbl, dbl, P(ctypes.c_size_t)],
         "lcqmc_selftest": [i32, i64, u64, P(i64)],
         "lcqmc_loops_noalloc": [vp, vp, i64, vp, vp],
+        "lcqmc_sw_create": [i64, dbl, u64, vp, P(vp)],
+        "lcqmc_sw_update": [vp, i64],
+        "lcqmc_sw_sync": [vp],
+        "lcqmc_sw_get_records": [vp, vp, i64, P(i64)],
+        "lcqmc_sw_measure": [vp, P(SwObs)],
+        "lcqmc_sw_set_spins": [vp, vp, u32],
+        "lcqmc_sw_get_spins": [vp, vp],
+        "lcqmc_sw_get_roots": [vp, vp],
+        "lcqmc_sw_set_phase_timing": [vp, i32],
+        "lcqmc_sw_get_phase_times": [vp, vp, i32],
+        "lcqmc_sw_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -139,6 +165,8 @@ def lib():
     L.lcqmc_last_error.argtypes = []
     L.lcqmc_stream.restype = vp
     L.lcqmc_stream.argtypes = [vp]
+    L.lcqmc_sw_stream.restype = vp
+    L.lcqmc_sw_stream.argtypes = [vp]
     _lib = L
     return L
 
@@ -366,3 +394,68 @@ class Server:
 
     def cancel(self, ticket):
         _check(lib().lcqmc_cancel(self.h, int(ticket)))
+
+
+class SWIsing:
+    """Swendsen-Wang updates of the L x L periodic Ising model (lcqmc_sw_*)."""
+
+    def __init__(self, L, K, seed=1, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib().lcqmc_sw_create(int(L), float(K), int(seed) & (2**64 - 1),
+                                     ctypes.c_void_p(int(stream)) if stream else None, ctypes.byref(h)))
+        self.h = h
+        self.L, self.K, self.seed = int(L), float(K), int(seed)
+
+    def close(self):
+        if self.h:
+            lib().lcqmc_sw_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, n=1):
+        _check(lib().lcqmc_sw_update(self.h, int(n)))
+
+    def sync(self):
+        _check(lib().lcqmc_sw_sync(self.h))
+
+    def records(self, max_n=4096):
+        buf = np.zeros(max(1, max_n), dtype=SW_RECORD_DTYPE)
+        cnt = ctypes.c_int64()
+        _check(lib().lcqmc_sw_get_records(self.h, _p(buf), int(max_n), ctypes.byref(cnt)))
+        return buf[: cnt.value].copy()
+
+    def measure(self):
+        o = SwObs()
+        _check(lib().lcqmc_sw_measure(self.h, ctypes.byref(o)))
+        return o
+
+    def set_spins(self, spins, sweep=0):
+        a = np.ascontiguousarray(spins, dtype=np.uint8).reshape(-1)
+        assert a.size == self.L * self.L
+        _check(lib().lcqmc_sw_set_spins(self.h, _p(a), ctypes.c_uint32(int(sweep))))
+
+    def spins(self):
+        a = np.zeros(self.L * self.L, np.uint8)
+        _check(lib().lcqmc_sw_get_spins(self.h, _p(a)))
+        return a
+
+    def roots(self):
+        a = np.zeros(self.L * self.L, np.int32)
+        _check(lib().lcqmc_sw_get_roots(self.h, _p(a)))
+        return a
+
+    def set_phase_timing(self, on=True):
+        _check(lib().lcqmc_sw_set_phase_timing(self.h, 1 if on else 0))
+
+    def phase_times(self):
+        ms = np.zeros(SW_NPHASE)
+        _check(lib().lcqmc_sw_get_phase_times(self.h, _p(ms), SW_NPHASE))
+        return dict(zip(SW_PHASES, ms.tolist()))
+
+    def stream(self):
+        return lib().lcqmc_sw_stream(self.h)

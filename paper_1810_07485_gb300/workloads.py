@@ -1,8 +1,10 @@
-"""Seeded synthetic workloads for the batched and served forms.
+"""Seeded synthetic workloads for the batched and served forms, and initial
+Ising configurations.
 
-Only parameter draws live here (no part of the update's arithmetic): chain
-sizes and temperatures for a batch of independent chains, and a Poisson
-stream of simulation requests.  Benchmarks and tests draw from the same
+Only parameter and input draws live here (no part of any update's
+arithmetic): chain sizes and temperatures for a batch of independent chains,
+a Poisson stream of simulation requests, and random spin configurations for
+the Swendsen-Wang lattice.  Benchmarks and tests draw from the same
 generators.
 """
 import numpy as np
@@ -40,3 +42,9 @@ def request_stream(n_requests, rate, L_min=64, L_max=65536, U_min=0.25, U_max=4.
         U = float(np.exp(rng.uniform(np.log(U_min), np.log(U_max))))
         out.append((t, dict(L=L, beta=L * U, S=S, J=1.0, seed=1000 + i, n_updates=n_updates)))
     return out
+
+
+def ising_spins(L, seed, up_fraction=0.5):
+    """L x L spins in {0, 1} (row-major), each 1 with probability 1 - up_fraction."""
+    rng = np.random.default_rng(seed)
+    return (rng.random(L * L) >= up_fraction).astype(np.uint8)
