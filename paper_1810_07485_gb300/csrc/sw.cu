@@ -18,7 +18,7 @@
 //   k_sw_merge  boundary bonds united in the global forest (same min-root rule,
 //               path halving), one warp per tile: the paper's two-step
 //               local/global union-find (Sec. 3.2) inside one GPU
-//   k_sw_flip   root of every local root (read-only walk), one coin per local
+//   k_sw_flip   root of every local root (path halving), one coin per local
 //               root, spins flipped; sizes of clusters closed in the tile
 //               squared here, sizes of open ones added at their global root
 //   k_sw_sizes  open clusters' sizes squared, cleared for the next update
@@ -180,14 +180,18 @@ __global__ void __launch_bounds__(SW_TPB) k_sw_local(SwScratch s) {
   const int t = blockIdx.x, L = D.L;
   int x0, y0, w, h;
   sw_tile(D, t, x0, y0, w, h);
-  for (int i = threadIdx.x; i < (h + 2) * (w + 2); i += SW_TPB) {
-    const int r = i / (w + 2), c = i - r * (w + 2);
-    int gy = y0 - 1 + r, gx = x0 - 1 + c;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int r = wid; r < h + 2; r += SW_TPB / 32) {  // a warp per row, no division
+    int gy = y0 - 1 + r;
     gy += (gy < 0) ? L : 0;
     gy -= (gy >= L) ? L : 0;
-    gx += (gx < 0) ? L : 0;
-    gx -= (gx >= L) ? L : 0;
-    sp[r][c] = s.spin[(int64_t)gy * L + gx];
+    const uint8_t *row = s.spin + (int64_t)gy * L;
+    for (int c = lane; c < w + 2; c += 32) {
+      int gx = x0 - 1 + c;
+      gx += (gx < 0) ? L : 0;
+      gx -= (gx >= L) ? L : 0;
+      sp[r][c] = row[gx];
+    }
   }
   if (threadIdx.x < SW_WORDS) ob[threadIdx.x] = 0u;
   if (threadIdx.x == 0) {
@@ -197,7 +201,6 @@ __global__ void __launch_bounds__(SW_TPB) k_sw_local(SwScratch s) {
   __syncthreads();
   const uint32_t k0 = (uint32_t)D.seed, k1 = (uint32_t)(D.seed >> 32), sweep = D.sweep;
   const uint64_t T = D.T;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   long long cnt[2] = {0, 0};  // equal bonds, active bonds
 #pragma unroll 2
   for (int k = 0; k < SW_PER; ++k) {
@@ -332,6 +335,7 @@ __global__ void __launch_bounds__(SW_TPB) k_sw_flip(SwScratch s) {
   __syncthreads();
   const uint32_t k0 = (uint32_t)D.seed, k1 = (uint32_t)(D.seed >> 32), sweep = D.sweep;
   const uint32_t *lrw = s.lroot + (int64_t)t * SW_WORDS;
+  const float invL = 1.0f / (float)L;
   int lr[SW_PER], gr[SW_PER];
   uint32_t isroot = 0u;
 #pragma unroll
@@ -344,12 +348,23 @@ __global__ void __launch_bounds__(SW_TPB) k_sw_flip(SwScratch s) {
     if ((lrw[l >> 5] >> (l & 31)) & 1u) {
       isroot |= 1u << k;
       lr[k] = l;
-      gr[k] = uf_root(s.par, (int)g, s.status);
+      // path halving on the way and the root stored at the start: every
+      // entry still points to an ancestor, and only local roots' entries
+      // change (non-roots keep pointing at their local root)
+      gr[k] = uf_find(s.par, (int)g, s.status);
+      if (gr[k] != (int)g) s.par[g] = gr[k];
       coin_s[l] = (uint8_t)coin_from(philox(TAG_SWFLIP << 24, (uint32_t)gr[k] >> 7, 0u, sweep, k0, k1),
                                      (uint32_t)gr[k]);
     } else {
       const int p = __ldcg(s.par + g);  // the site's local root, in this tile
-      const int py = p / L, px = p - py * L;
+      int py = __float2int_rz((float)p * invL), px = p - py * L;  // quotient within 1, corrected
+      if (px < 0) {
+        --py;
+        px += L;
+      } else if (px >= L) {
+        ++py;
+        px -= L;
+      }
       if (py < y0 || py >= y0 + h || px < x0 || px >= x0 + w) {  // cannot happen: merges
         atomicOr(s.status, ST_INTERNAL);                         // write local roots only
         lr[k] = -1;
