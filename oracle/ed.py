@@ -135,3 +135,14 @@ def s1_dimer_closed_form(beta, J=1.0):
     g = np.array([1, 3, 5])
     w = g * np.exp(-beta * lv)
     return {"energy": float((lv * w).sum() / w.sum()) / 2}
+
+
+def spin_dimer_closed_form(beta, S, J=1.0):
+    """L=2 periodic spin-S chain: two bonds between the same pair, H = 2J S1.S2
+    = J (T(T+1) - 2S(S+1)), total spin T = 0 .. 2S with multiplicity 2T+1.
+    Energy per site."""
+    T = np.arange(0, int(round(2 * S)) + 1)
+    lv = J * (T * (T + 1) - 2 * S * (S + 1))
+    g = 2 * T + 1
+    w = g * np.exp(-beta * (lv - lv.min()))
+    return {"energy": float((lv * w).sum() / w.sum()) / 2}

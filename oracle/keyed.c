@@ -404,11 +404,49 @@ int orc_keyed_update(const orc_params *p, uint32_t sweep, const uint8_t *s0,
     }
   }
 
-  /* Cut at tau = 0: permutation of subspins per site (identity for Q = 1). */
+  /* Cut at tau = 0: permutation of subspins per site (identity for Q = 1),
+     drawn uniformly among those that join every top to a bottom of the same
+     spin (heat bath of the symmetrization, Sec. 5). */
   int64_t *perm = (int64_t *)malloc(sizeof(int64_t) * (size_t)NS); /* top subsite -> bottom subsite */
   for (int64_t i = 0; i < L; ++i) {
     if (Q == 1) {
       perm[i] = i;
+      continue;
+    }
+    if (Q > 2) {
+      /* Tops and bottoms of spin 1, then of spin 0, in subspin order; a
+         uniform shuffle of each bottom list (Fisher-Yates from the last
+         place down, place j drawn as floor(w (j+1) / 2^32) with w the next
+         word of Philox(ctr = ((ORC_TAG_PERM << 24) | 1, i, 0, sweep))); the
+         m-th top of each spin continues into the m-th shuffled bottom. */
+      int64_t tops[2][ORC_QMAX], bots[2][ORC_QMAX];
+      int nt[2] = {0, 0}, nb[2] = {0, 0};
+      for (int a = 0; a < Q; ++a) {
+        int64_t u = i * Q + a;
+        int t = s0[u] ^ (int)((ev_cnt[u + 1] - ev_cnt[u]) & 1);
+        int g = t ? 0 : 1; /* group 0: spin 1 */
+        tops[g][nt[g]++] = a;
+        int gb = s0[u] ? 0 : 1;
+        bots[gb][nb[gb]++] = a;
+      }
+      if (nt[0] != nb[0]) {
+        rc = -2;
+        goto done2;
+      }
+      uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
+      uint32_t ctr[4] = {(ORC_TAG_PERM << 24) | 1u, (uint32_t)i, 0u, sweep};
+      uint32_t w[4];
+      orc_philox4x32_10(ctr, key, w);
+      int d = 0;
+      for (int g = 0; g < 2; ++g) {
+        for (int j = nb[g] - 1; j >= 1; --j) {
+          int r = (int)(((uint64_t)w[d++] * (uint64_t)(j + 1)) >> 32);
+          int64_t tmp = bots[g][j];
+          bots[g][j] = bots[g][r];
+          bots[g][r] = tmp;
+        }
+        for (int m = 0; m < nt[g]; ++m) perm[i * Q + tops[g][m]] = i * Q + bots[g][m];
+      }
       continue;
     }
     int64_t u0 = i * Q, u1 = i * Q + 1;

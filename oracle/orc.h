@@ -41,6 +41,8 @@ extern "C" {
 #define ORC_CELL_MEAN 8.0
 /* Windows per time block in the canonical cell order. */
 #define ORC_TW 4
+/* Largest 2S (S = 2). */
+#define ORC_QMAX 4
 
 /* Philox tags (high byte of counter word 0). */
 #define ORC_TAG_INSERT 1u
@@ -53,7 +55,7 @@ extern "C" {
 
 typedef struct {
   int64_t L;      /* original sites (even, >= 2) */
-  int Q;          /* 2S subspins per site: 1 or 2 */
+  int Q;          /* 2S subspins per site: 1 to ORC_QMAX */
   double J;       /* coupling, > 0 */
   double beta;    /* inverse temperature, > 0 */
   uint64_t seed;  /* Philox key */

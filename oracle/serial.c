@@ -204,6 +204,31 @@ int orc_serial_update(const orc_params *p, uint32_t sweep, uint8_t *s0, int64_t 
       uf_union(&uf, cur[i], first[i]);
       continue;
     }
+    if (Q > 2) {
+      /* uniform among the permutations joining equal spins: shuffle the
+         bottoms of each spin value (Fisher-Yates) and pair them in order */
+      int64_t tops[2][ORC_QMAX], bots[2][ORC_QMAX];
+      int nt[2] = {0, 0}, nb[2] = {0, 0};
+      for (int a = 0; a < Q; ++a) {
+        int64_t u = i * Q + a;
+        tops[s[u] ? 0 : 1][nt[s[u] ? 0 : 1]++] = u;
+        bots[s0[u] ? 0 : 1][nb[s0[u] ? 0 : 1]++] = u;
+      }
+      if (nt[0] != nb[0]) {
+        rc = -2;
+        goto out;
+      }
+      for (int g = 0; g < 2; ++g) {
+        for (int j = nb[g] - 1; j >= 1; --j) {
+          int r = (int)(next_u64(&rs) % (uint64_t)(j + 1));
+          int64_t tmp = bots[g][j];
+          bots[g][j] = bots[g][r];
+          bots[g][r] = tmp;
+        }
+        for (int m = 0; m < nt[g]; ++m) uf_union(&uf, cur[tops[g][m]], first[bots[g][m]]);
+      }
+      continue;
+    }
     int64_t u0 = i * Q, u1 = i * Q + 1;
     int ok_id = (s[u0] == s0[u0]) && (s[u1] == s0[u1]);
     int ok_sw = (s[u0] == s0[u1]) && (s[u1] == s0[u0]);

@@ -33,14 +33,23 @@ def test_s1_dimer(beta):
                                                                  rel=1e-12)
 
 
-@pytest.mark.parametrize("L,S", [(8, 0.5), (6, 1.0)])
+@pytest.mark.parametrize("S", [0.5, 1.0, 1.5, 2.0])
+@pytest.mark.parametrize("beta", [0.3, 1.0, 4.0])
+def test_spin_dimer_closed_form(S, beta):
+    # the L = 2 spectrum from the total spin of two spins S
+    assert ed.thermal(2, beta, S=S)["energy"] == pytest.approx(ed.spin_dimer_closed_form(beta, S)["energy"],
+                                                               rel=1e-12)
+
+
+@pytest.mark.parametrize("L,S", [(8, 0.5), (6, 1.0), (4, 1.5), (4, 2.0)])
 def test_curie_limit(L, S):
-    # beta -> 0: chi(q) -> beta S(S+1)/3 for every q, E/L -> 0.
+    # beta -> 0: chi(q) -> beta S(S+1)/3 for every q.
     beta = 1e-4
     t = ed.thermal(L, beta, S=S)
     assert t["chi_s"] == pytest.approx(beta * S * (S + 1) / 3, rel=1e-3)
     assert t["chi_q"] == pytest.approx(beta * S * (S + 1) / 3, rel=1e-3)
-    assert abs(t["energy"]) < 1e-3
+    # leading high-temperature term: E/L = -beta <(S_i.S_j)^2> = -beta (S(S+1))^2 / 3
+    assert t["energy"] == pytest.approx(-beta * (S * (S + 1)) ** 2 / 3, rel=1e-3)
 
 
 def test_coupling_scale():

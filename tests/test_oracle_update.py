@@ -114,7 +114,8 @@ def brute_partition(n, pl, pr):
     return root
 
 
-@pytest.mark.parametrize("L,beta,Q", [(2, 3.0, 1), (6, 5.0, 1), (10, 40.0, 1), (4, 3.0, 2), (2, 20.0, 2)])
+@pytest.mark.parametrize("L,beta,Q", [(2, 3.0, 1), (6, 5.0, 1), (10, 40.0, 1), (4, 3.0, 2), (2, 20.0, 2),
+                                      (4, 3.0, 3), (2, 6.0, 4)])
 def test_keyed_invariants(orc, L, beta, Q):
     p = orc.params(L, beta, Q=Q, seed=101)
     st = orc.neel(p)
@@ -216,7 +217,9 @@ def test_curie_limit_empty(orc):
 
 @pytest.mark.parametrize("form", ["keyed", "serial"])
 @pytest.mark.parametrize("L,beta,Q,seed", [(2, 1.0, 1, 21), (4, 2.0, 1, 22), (8, 4.0, 1, 23),
-                                           (12, 1.0, 1, 24), (4, 1.0, 2, 25), (2, 2.0, 2, 26)])
+                                           (12, 1.0, 1, 24), (4, 1.0, 2, 25), (2, 2.0, 2, 26),
+                                           (2, 1.0, 3, 27), (4, 0.7, 3, 28), (2, 0.8, 4, 29),
+                                           (4, 0.5, 4, 30)])
 def test_vs_ed(orc, form, L, beta, Q, seed):
     p = orc.params(L, beta, Q=Q, seed=seed)
     n = 200000
@@ -233,15 +236,16 @@ def test_vs_ed(orc, form, L, beta, Q, seed):
         assert stats.within_sigma(m, e, ex[name], 3.0), (name, m, e, ex[name])
 
 
-@pytest.mark.parametrize("Q", [1, 2])
+@pytest.mark.parametrize("Q", [1, 2, 3, 4])
 def test_curie_limit_statistics(orc, Q):
-    beta = 0.01
-    p = orc.params(8, beta, Q=Q, seed=31)
+    S = Q / 2
+    beta = 0.01 * 0.75 / (S * (S + 1))  # the same expansion parameter beta S(S+1) for every S
+    L = 8 if Q <= 2 else 4  # exact diagonalization size
+    p = orc.params(L, beta, Q=Q, seed=31)
     st = orc.neel(p)
     orc.keyed_run(p, 0, 100, st)
     r = orc.keyed_run(p, 100, 20000, st)
-    S = Q / 2
-    ex = ed.thermal(8, beta, S=S)
+    ex = ed.thermal(L, beta, S=S)
     m, e = stats.mean_err(r["chi_s"], 50)
     assert stats.within_sigma(m, e, ex["chi_s"], 3.0)
     assert ex["chi_s"] == pytest.approx(beta * S * (S + 1) / 3, rel=2e-2)
