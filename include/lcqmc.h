@@ -7,9 +7,11 @@
  * (arXiv:1810.07485).  The model is H = J sum_j S_j . S_{j+1} with periodic
  * boundaries (Eq. 1, Sec. 2); one update is the continuous-time loop step of
  * Sec. 2 (labeling, cluster identification, flip, rewrite, measurement) with the
- * cluster identification done by a lock-free union-find (Sec. 3.2).  S = 1 is
- * handled by the subspin representation of Sec. 5 (two S=1/2 subspins per site,
- * four sub-bonds per bond).
+ * cluster identification done by a lock-free union-find (Sec. 3.2).  S = 1,
+ * 3/2 and 2 are handled by the subspin representation of Sec. 5 (Q = 2S
+ * S=1/2 subspins per site, Q^2 sub-bonds per bond, the subspins joined at
+ * tau = 0 by a permutation drawn uniformly among those that join equal
+ * spins).
  *
  * Conventions shared by every entry point:
  *   - Return value: LCQMC_OK (0) on success, LCQMC_PENDING (1) where stated,
@@ -46,7 +48,7 @@ extern "C" {
 
 #define LCQMC_OK 0
 #define LCQMC_PENDING 1
-#define LCQMC_E_INVAL (-1)          /* bad argument: L < 2 or odd, beta <= 0, J <= 0, 2S not 1 or 2 */
+#define LCQMC_E_INVAL (-1)          /* bad argument: L < 2 or odd, beta <= 0, J <= 0, 2S not in 1..4 */
 #define LCQMC_E_NOMEM (-2)          /* device or host allocation failed */
 #define LCQMC_E_TOO_LARGE (-3)      /* footprint above the budget / the server's HBM budget */
 #define LCQMC_E_ID_OVERFLOW (-4)    /* more than 2^31-4096 graph vertices, or 2^31 cells, in one chain */
@@ -114,7 +116,7 @@ typedef struct {
 
 /* --- single chain (Sec. 2 MC step on one chain) ----------------------------- */
 
-/* Creates a chain of L sites (even, >= 2), spin S (0.5 or 1.0, checked exactly),
+/* Creates a chain of L sites (even, >= 2), spin S (0.5, 1, 1.5 or 2, checked exactly),
  * coupling J > 0, inverse temperature beta > 0, Philox seed.  Starts from the
  * Neel state with no operators, sweep 0, on device 0's default stream. */
 int lcqmc_create(int64_t L, double S, double J, double beta, uint64_t seed, lcqmc_handle *out);

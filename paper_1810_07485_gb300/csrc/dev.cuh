@@ -10,6 +10,7 @@
 namespace lcq {
 
 constexpr int KMAX = 48;          // Poisson count table length (K <= KMAX-1)
+constexpr int QMAX = 4;           // largest 2S: subspins per site (S <= 2)
 constexpr int TW = LCQMC_TW;      // windows per time block of the cell order
 constexpr int64_t VTX_ID_LIMIT = 0x7ffff000;  // largest vertex count of one chain
 constexpr int NOBS = 9;         // running averages per chain (lcqmc_obs.sum)

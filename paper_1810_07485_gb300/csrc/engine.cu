@@ -53,8 +53,8 @@ int validate_spec(int64_t L, double S, double J, double beta, ChainSpec &out) {
     set_error("L must be even and >= 2 (odd L frustrates the periodic antiferromagnet)");
     return LCQMC_E_INVAL;
   }
-  if (!(twoS == 1.0 || twoS == 2.0)) {
-    set_error("2S must be 1 or 2");
+  if (!(twoS == 1.0 || twoS == 2.0 || twoS == 3.0 || twoS == 4.0)) {
+    set_error("2S must be 1, 2, 3 or 4");
     return LCQMC_E_INVAL;
   }
   if (!(J > 0.0) || !std::isfinite(J) || !(beta > 0.0) || !std::isfinite(beta)) {
@@ -272,7 +272,7 @@ int Engine::open(void *stream, const lcqmc_allocator *alloc, int ring_cap) {
   poisson_table(CELL_MEAN, T.data());
   set_full_table(T.data(), st_);
   DALLOC(s_.status, int, 1);
-  DALLOC(s_.tickets, unsigned int, 2);
+  DALLOC(s_.tickets, unsigned int, QMAX);
   DALLOC(s_.need, int64_t, 4);
   DALLOC(s_.dbg, long long, 8);
   CK(cudaMemsetAsync(s_.status, 0, sizeof(int), st_));
@@ -411,7 +411,7 @@ int Engine::layout() {
   hch.assign(nc, DevChain{});
   std::vector<int2> ttab, stab, btab;
   int64_t cell_off = 0, bpar_off = 0, sub_off = 0, vest = 0;
-  for (int q = 0; q < 2; ++q) {
+  for (int q = 0; q < QMAX; ++q) {
     L_.tile0[q] = (int64_t)ttab.size();
     L_.site0[q] = (int64_t)stab.size();
     L_.bond0[q] = (int64_t)btab.size();
@@ -547,7 +547,7 @@ int Engine::enqueue_one(bool timed, int slot) {
   mark(0);  // [0] labeling: random numbers, insertion, vertex offsets (one pass)
   launch_bond_parity(L_, st_);
   CK(cudaMemsetAsync(s_.tile_state, 0, 8 * (size_t)cap_tiles_, st_));
-  CK(cudaMemsetAsync(s_.tickets, 0, 2 * sizeof(unsigned int), st_));
+  CK(cudaMemsetAsync(s_.tickets, 0, QMAX * sizeof(unsigned int), st_));
   CK(cudaMemsetAsync(s_.openmark, 0, 4 * nw, st_));
   CK(cudaMemsetAsync(s_.openroot, 0, 4 * nw, st_));
   CK(cudaMemsetAsync(s_.flipbits, 0, 4 * nw, st_));

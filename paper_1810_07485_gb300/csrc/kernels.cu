@@ -468,10 +468,30 @@ __device__ void ins_write(const DevChain &C, InsSmem<Q> &S, const long long *ota
 }
 
 template <int Q>
+__device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict__ ch,
+                                            const int2 *__restrict__ tab, int64_t blk0, int group,
+                                            Scratch s);
+
+// The staging area is static shared memory for Q <= 2 and dynamic shared
+// memory (above the 48 KB static limit) for the larger neighbour tables of
+// Q = 3, 4.
+template <int Q>
 __global__ void __launch_bounds__(TILE) k_insert(DevChain *__restrict__ ch,
                                                  const int2 *__restrict__ tab, int64_t blk0,
                                                  int group, Scratch s) {
-  __shared__ InsSmem<Q> S;
+  if constexpr (Q <= 2) {
+    __shared__ InsSmem<Q> S;
+    insert_tile<Q>(S, ch, tab, blk0, group, s);
+  } else {
+    extern __shared__ __align__(16) unsigned char ins_dyn[];
+    insert_tile<Q>(*reinterpret_cast<InsSmem<Q> *>(ins_dyn), ch, tab, blk0, group, s);
+  }
+}
+
+template <int Q>
+__device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict__ ch,
+                                            const int2 *__restrict__ tab, int64_t blk0, int group,
+                                            Scratch s) {
   if (halted(s)) return;
   if (threadIdx.x == 0) S.gt = blk0 + (int64_t)atomicAdd(s.tickets + group, 1u);
   __syncthreads();
@@ -718,8 +738,42 @@ __global__ void __launch_bounds__(SITE_BLOCK) k_cut(const DevChain *__restrict__
   int perm[Q];
   if (Q == 1) {
     perm[0] = 0;
+  } else if (Q > 2) {
+    // Uniform among the permutations that join every top to a bottom of the
+    // same spin (heat bath of the symmetrization, Sec. 5): tops and bottoms of
+    // spin 1, then of spin 0, in subspin order; each bottom list shuffled by
+    // Fisher-Yates from the last place down, place j drawn as
+    // floor(w (j+1) / 2^32) with w the next word of
+    // Philox(((TAG_PERM << 24) | 1, i, 0, sweep)); the m-th top of each spin
+    // continues into the m-th shuffled bottom.
+    int tops[2][Q], bots[2][Q], nt[2] = {0, 0}, nb[2] = {0, 0};
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      const int gt = top[a] ? 0 : 1, gb = (s0[i * Q + a] & 1) ? 0 : 1;
+      tops[gt][nt[gt]++] = a;
+      bots[gb][nb[gb]++] = a;
+    }
+#pragma unroll
+    for (int a = 0; a < Q; ++a) perm[a] = a;
+    if (nt[0] != nb[0]) {
+      atomicOr(s.status, ST_BADSTATE);
+    } else {
+      const U4 o = philox((TAG_PERM << 24) | 1u, (uint32_t)i, 0u, C.sweep, (uint32_t)C.seed,
+                          (uint32_t)(C.seed >> 32));
+      const uint32_t w[4] = {o.x, o.y, o.z, o.w};
+      int d = 0;
+      for (int g = 0; g < 2; ++g) {
+        for (int j = nb[g] - 1; j >= 1; --j) {
+          const int r = (int)__umulhi(w[d++ & 3], (uint32_t)(j + 1));
+          const int tmp = bots[g][j];
+          bots[g][j] = bots[g][r];
+          bots[g][r] = tmp;
+        }
+        for (int m = 0; m < nt[g]; ++m) perm[tops[g][m]] = bots[g][m];
+      }
+    }
   } else {
-    const int b0 = s0[i * Q] & 1, b1 = s0[i * Q + 1] & 1;
+    const int b0 = s0[i * Q] & 1, b1 = s0[i * Q + (Q > 1 ? 1 : 0)] & 1;
     const bool ok_id = (top[0] == b0) && (top[1] == b1);
     const bool ok_sw = (top[0] == b1) && (top[1] == b0);
     int sw;
@@ -1527,15 +1581,30 @@ void set_full_table(const uint64_t *T, cudaStream_t st) {
 
 static inline dim3 g1(int64_t n) { return dim3((unsigned)n); }
 
+// One launch per Q group (Q = 2S = 1 .. QMAX); the tile-wide kernels that do
+// not depend on Q run over the tiles of every group at once.
+#define FOR_EACH_Q(M) M(1) M(2) M(3) M(4)
+static_assert(QMAX == 4, "FOR_EACH_Q lists every Q");
+
+static int64_t all_tiles(const Launch &L) {
+  int64_t n = 0;
+  for (int q = 0; q < QMAX; ++q) n += L.ntile[q];
+  return n;
+}
+
 void launch_bond_parity(const Launch &L, cudaStream_t st) {
-  for (int q = 0; q < 2; ++q)
+  for (int q = 0; q < QMAX; ++q)
     if (L.nbondblk[q])
       k_bond_parity<<<g1(L.nbondblk[q]), BOND_BLOCK, 0, st>>>(L.ch, L.bond_tab, L.bond0[q], L.s);
 }
 
 void launch_insert(const Launch &L, cudaStream_t st) {
-  if (L.ntile[0]) k_insert<1><<<g1(L.ntile[0]), TILE, 0, st>>>(L.ch, L.tile_tab, L.tile0[0], 0, L.s);
-  if (L.ntile[1]) k_insert<2><<<g1(L.ntile[1]), TILE, 0, st>>>(L.ch, L.tile_tab, L.tile0[1], 1, L.s);
+#define INSERT_Q(Q)                                                                              \
+  if (L.ntile[Q - 1])                                                                            \
+    k_insert<Q><<<g1(L.ntile[Q - 1]), TILE, Q <= 2 ? 0 : sizeof(InsSmem<Q>), st>>>(L.ch, L.tile_tab, \
+                                                                                  L.tile0[Q - 1], Q - 1, L.s);
+  FOR_EACH_Q(INSERT_Q)
+#undef INSERT_Q
 }
 
 void launch_scan_ops(const Launch &L, cudaStream_t st) {
@@ -1543,19 +1612,23 @@ void launch_scan_ops(const Launch &L, cudaStream_t st) {
 }
 
 void launch_cut(const Launch &L, cudaStream_t st) {
-  if (L.nsiteblk[0]) k_cut<1><<<g1(L.nsiteblk[0]), SITE_BLOCK, 0, st>>>(L.ch, L.site_tab, L.site0[0], L.s);
-  if (L.nsiteblk[1]) k_cut<2><<<g1(L.nsiteblk[1]), SITE_BLOCK, 0, st>>>(L.ch, L.site_tab, L.site0[1], L.s);
+#define CUT_Q(Q) \
+  if (L.nsiteblk[Q - 1]) k_cut<Q><<<g1(L.nsiteblk[Q - 1]), SITE_BLOCK, 0, st>>>(L.ch, L.site_tab, L.site0[Q - 1], L.s);
+  FOR_EACH_Q(CUT_Q)
+#undef CUT_Q
 }
 
 void launch_link(const Launch &L, cudaStream_t st) {
-  if (L.ntile[0]) k_link<1><<<g1(L.ntile[0]), TPB, 0, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
-  if (L.ntile[1]) k_link<2><<<g1(L.ntile[1]), TPB, 0, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
-  const int64_t n = L.ntile[0] + L.ntile[1];
+#define LINK_Q(Q) \
+  if (L.ntile[Q - 1]) k_link<Q><<<g1(L.ntile[Q - 1]), TPB, 0, st>>>(L.ch, L.tile_tab, L.tile0[Q - 1], L.s);
+  FOR_EACH_Q(LINK_Q)
+#undef LINK_Q
+  const int64_t n = all_tiles(L);
   if (n) k_link_x<<<g1((n + TPB_X / 32 - 1) / (TPB_X / 32)), TPB_X, 0, st>>>(L.ch, L.tile_tab, n, L.s);
 }
 
 void launch_compress(const Launch &L, cudaStream_t st) {
-  const int64_t n = L.ntile[0] + L.ntile[1];
+  const int64_t n = all_tiles(L);
   if (n) k_compress<<<g1(n), TILE, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
 }
 
@@ -1579,10 +1652,16 @@ int init_kernel_attributes() {
                        (int)std::llrint(std::ldexp(std::sin(ang), 30)));
   }
   if (cudaMemcpyToSymbol(g_phase_tab, tab, sizeof(tab)) != cudaSuccess) return -1;
-  if (cudaFuncSetAttribute(k_est<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)EST_DYN_SMEM) != cudaSuccess ||
-      cudaFuncSetAttribute(k_est<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)EST_DYN_SMEM) != cudaSuccess)
+#define EST_ATTR_Q(Q)                                                                 \
+  if (cudaFuncSetAttribute(k_est<Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                           (int)EST_DYN_SMEM) != cudaSuccess)                           \
+    return -1;
+  FOR_EACH_Q(EST_ATTR_Q)
+#undef EST_ATTR_Q
+  if (cudaFuncSetAttribute(k_insert<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(InsSmem<3>)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_insert<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(InsSmem<4>)) != cudaSuccess)
     return -1;
   done[dev] = true;
   return 0;
@@ -1591,17 +1670,19 @@ int init_kernel_attributes() {
 void launch_est(const Launch &L, cudaStream_t st) {
   // without the temporal moment only the ticks are staged
   const size_t dyn = L.temporal ? EST_DYN_SMEM : SMEM_CAP * sizeof(long long);
-  if (L.temporal) {
-    if (L.ntile[0]) k_est<1, true><<<g1(L.ntile[0]), TPB_EST, dyn, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
-    if (L.ntile[1]) k_est<2, true><<<g1(L.ntile[1]), TPB_EST, dyn, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
-  } else {
-    if (L.ntile[0]) k_est<1, false><<<g1(L.ntile[0]), TPB_EST, dyn, st>>>(L.ch, L.tile_tab, L.tile0[0], L.s);
-    if (L.ntile[1]) k_est<2, false><<<g1(L.ntile[1]), TPB_EST, dyn, st>>>(L.ch, L.tile_tab, L.tile0[1], L.s);
+#define EST_Q(Q)                                                                                       \
+  if (L.ntile[Q - 1]) {                                                                                \
+    if (L.temporal)                                                                                    \
+      k_est<Q, true><<<g1(L.ntile[Q - 1]), TPB_EST, dyn, st>>>(L.ch, L.tile_tab, L.tile0[Q - 1], L.s);  \
+    else                                                                                               \
+      k_est<Q, false><<<g1(L.ntile[Q - 1]), TPB_EST, dyn, st>>>(L.ch, L.tile_tab, L.tile0[Q - 1], L.s); \
   }
+  FOR_EACH_Q(EST_Q)
+#undef EST_Q
 }
 
 void launch_compact(const Launch &L, cudaStream_t st) {
-  const int64_t n = L.ntile[0] + L.ntile[1];
+  const int64_t n = all_tiles(L);
   if (n) {
     if (L.temporal)
       k_compact<true><<<g1(n), TPB, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
@@ -1611,8 +1692,10 @@ void launch_compact(const Launch &L, cudaStream_t st) {
 }
 
 void launch_sites(const Launch &L, cudaStream_t st) {
-  if (L.nsiteblk[0]) k_sites<1><<<g1(L.nsiteblk[0]), SITE_BLOCK, 0, st>>>(L.ch, L.site_tab, L.site0[0], L.s);
-  if (L.nsiteblk[1]) k_sites<2><<<g1(L.nsiteblk[1]), SITE_BLOCK, 0, st>>>(L.ch, L.site_tab, L.site0[1], L.s);
+#define SITES_Q(Q) \
+  if (L.nsiteblk[Q - 1]) k_sites<Q><<<g1(L.nsiteblk[Q - 1]), SITE_BLOCK, 0, st>>>(L.ch, L.site_tab, L.site0[Q - 1], L.s);
+  FOR_EACH_Q(SITES_Q)
+#undef SITES_Q
 }
 
 void launch_final(const Launch &L, cudaStream_t st) {

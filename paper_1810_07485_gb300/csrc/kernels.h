@@ -4,17 +4,17 @@
 
 namespace lcq {
 
-// One batch's launch geometry.  Tiles, site blocks and bond blocks are ordered
-// with every Q=1 chain's blocks before every Q=2 chain's blocks; index [q]
+// One batch's launch geometry.  Tiles, site blocks and bond blocks are grouped
+// by Q = 2S (every Q=1 chain's blocks first, then Q=2, ...); index [q]
 // addresses the Q = q+1 group.
 struct Launch {
   DevChain *ch;
   int nchains;
   Scratch s;
   const int2 *tile_tab, *site_tab, *bond_tab;
-  int64_t ntile[2], tile0[2];
-  int64_t nsiteblk[2], site0[2];
-  int64_t nbondblk[2], bond0[2];
+  int64_t ntile[QMAX], tile0[QMAX];
+  int64_t nsiteblk[QMAX], site0[QMAX];
+  int64_t nbondblk[QMAX], bond0[QMAX];
   int temporal;  // measure the temporal moment chi(pi, 2 pi / beta) too
 };
 

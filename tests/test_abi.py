@@ -50,7 +50,7 @@ def test_invalid_arguments_rejected_on_host(built_lib):
     L = lcqmc.lib()
     h = ctypes.c_void_p()
     for args in [(3, 0.5, 1.0, 1.0), (0, 0.5, 1.0, 1.0), (8, 0.75, 1.0, 1.0), (8, 0.5, -1.0, 1.0),
-                 (8, 0.5, 1.0, 0.0), (8, 1.5, 1.0, 1.0)]:
+                 (8, 0.5, 1.0, 0.0), (8, 2.5, 1.0, 1.0), (8, 3.0, 1.0, 1.0)]:
         rc = L.lcqmc_create(args[0], args[1], args[2], args[3], 1, ctypes.byref(h))
         assert rc == -1, args
 

@@ -89,6 +89,12 @@ CASES = [
     (2, 10.0, 2, 1.0),
     (16, 20.0, 2, 1.0),
     (64, 8.0, 2, 0.5),
+    (4, 3.0, 3, 1.0),        # S = 3/2: 9 sub-bonds per bond, shuffled tau = 0 joins
+    (6, 5.0, 3, 1.0),
+    (34, 10.0, 3, 1.0),      # 306 cells: 3 tiles
+    (2, 4.0, 4, 1.0),        # S = 2
+    (8, 6.0, 4, 0.7),
+    (20, 40.0, 4, 1.0),      # 960 cells: 8 tiles
 ]
 
 
@@ -208,7 +214,8 @@ def test_records_and_measure_consistent():
     assert o.gap == pytest.approx(1 / xt, rel=1e-10)
 
 
-@pytest.mark.parametrize("L,beta,Q", [(8, 4.0, 1), (12, 1.0, 1), (4, 1.0, 2)])
+@pytest.mark.parametrize("L,beta,Q", [(8, 4.0, 1), (12, 1.0, 1), (4, 1.0, 2), (4, 0.7, 3), (2, 0.8, 4),
+                                      (4, 0.5, 4)])
 def test_gpu_vs_ed(L, beta, Q):
     # Estimators within 3 standard errors of exact diagonalization.
     lc = gpu()
@@ -231,7 +238,8 @@ def test_batch_matches_single_chains():
     # Chains updated together in one batch give the same records as alone.
     lc = gpu()
     specs = [dict(L=8, beta=4.0, seed=1), dict(L=34, beta=51.0, seed=2), dict(L=4, beta=2.0, S=1.0, seed=3),
-             dict(L=128, beta=16.0, seed=4), dict(L=10, beta=0.001, seed=5)]
+             dict(L=128, beta=16.0, seed=4), dict(L=10, beta=0.001, seed=5), dict(L=6, beta=5.0, S=1.5, seed=6),
+             dict(L=10, beta=12.0, S=2.0, seed=7)]
     b = lc.Batch(specs)
     b.update(25)
     for i, s in enumerate(specs):
