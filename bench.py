@@ -49,12 +49,19 @@ KERNELS_PER_UPDATE = 11
 TRAFFIC_PER_VERTEX = {"insert": 13.1, "link_union": 26.8, "loop_ids": 7.5, "loop_props": 25.0,
                       "op_rewrite": 14.8}
 TRAFFIC_PER_VERTEX_TEMPORAL = dict(TRAFFIC_PER_VERTEX, loop_props=25.8, op_rewrite=16.6)
-TRAFFIC_KERNELS_SHA1 = "533144529c2afbfdafdae8babcf2c4aaf6a1d928"
+TRAFFIC_KERNELS_SHA1 = "7ebd630de0d79dfd549a877118bf2bab88dac209"
 
 
-def kernels_sha1():
+# DRAM bytes per launch of each Swendsen-Wang phase at L = 8192, K = K_c (one
+# ncu capture; profiles/sw_L8192_Kc.md), valid for sw.cu with this sha1 only.
+SW_TRAFFIC = {"tile_bonds_uf": 294.7e6, "boundary_merge": 173.4e6, "roots_flip": 444.8e6,
+              "open_sizes_record": 24.4e6}
+SW_TRAFFIC_SHA1 = "4d06f2cca15f4fea3cc7f70aa8ac15f7ddae1fe4"
+
+
+def kernels_sha1(name="kernels.cu"):
     import hashlib
-    with open(os.path.join(ROOT, "paper_1810_07485_gb300", "csrc", "kernels.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_1810_07485_gb300", "csrc", name), "rb") as f:
         return hashlib.sha1(f.read()).hexdigest()
 
 
@@ -533,8 +540,9 @@ def run_sw(args, world, rank, local):
     peak, peak_kind = load_peaks()
     dom = max(ph, key=lambda k: ph[k])
     achieved = nb[dom] * nph / (ph[dom] * 1e-3) / 1e9
+    traffic = SW_TRAFFIC.get(dom) if kernels_sha1("sw.cu") == SW_TRAFFIC_SHA1 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "algorithmic_bytes": nb[dom], "kernel": dom, "peak_kind": peak_kind,
+                "traffic": traffic, "algorithmic_bytes": nb[dom], "kernel": dom, "peak_kind": peak_kind,
                 "phase_ms_per_update": {k: ph[k] / nph for k in ph},
                 "phase_frac_of_hbm": {k: (nb[k] * nph / (ph[k] * 1e-3) / 1e9) / peak if ph[k] > 0 else None
                                       for k in ph}}
