@@ -1061,6 +1061,7 @@ __global__ void __launch_bounds__(TILE) k_compress(const DevChain *__restrict__ 
                                                    Scratch s) {
   __shared__ U4 coins[MAX_COIN_GROUPS];
   __shared__ int64_t sm[33];
+  __shared__ int spar[SMEM_CAP];  // the tile's parent words: walks stay here until they leave it
   if (halted(s)) return;
   const int64_t gt = blk0 + blockIdx.x;
   const int2 t = tab[gt];
@@ -1076,6 +1077,10 @@ __global__ void __launch_bounds__(TILE) k_compress(const DevChain *__restrict__ 
   const uint32_t k0 = (uint32_t)C.seed, k1 = (uint32_t)(C.seed >> 32);
   for (int g = threadIdx.x; g < ng && g < MAX_COIN_GROUPS; g += blockDim.x)
     coins[g] = philox(TAG_FLIP << 24, (uint32_t)(g0 + g), 0u, C.sweep, k0, k1);
+  // Only this block writes parent words of [a, e) in this kernel, and every
+  // word it writes is an ancestor of the old one: the copy stays a valid forest.
+  if (!oversized)
+    for (int i = threadIdx.x; i < e - a; i += blockDim.x) spar[i] = __ldcg(par + a + i);
   __syncthreads();
   int64_t roots = 0;
   for (int v0 = a; v0 < e; v0 += blockDim.x) {  // whole warps, reconverged per step
@@ -1084,7 +1089,20 @@ __global__ void __launch_bounds__(TILE) k_compress(const DevChain *__restrict__ 
       __syncwarp();
       continue;
     }
-    const int r = uf_root(par, v, s.status);
+    int r;
+    if (oversized) {
+      r = uf_root(par, v, s.status);
+    } else {
+      // parents are never larger than their children: the walk leaves the
+      // tile only downwards (below a), and then finishes in global memory
+      r = v;
+      int p = spar[v - a];
+      for (int it = 0; p != r && p >= a && it < SMEM_CAP; ++it) {
+        r = p;
+        p = spar[p - a];
+      }
+      if (p != r) r = uf_root(par, p, s.status);
+    }
     if (r != v) par[v] = r;
     if (r == v) {
       ++roots;
