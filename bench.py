@@ -65,6 +65,21 @@ def kernels_sha1(name="kernels.cu"):
         return hashlib.sha1(f.read()).hexdigest()
 
 
+def host_cpu():
+    """The host's CPU model and logical core count (for the CPU baseline)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    import platform
+    return {"model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count()}
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -196,7 +211,7 @@ def run_reference(args, world, rank):
         "config": {"workload": f"S=1/2 AFM Heisenberg chain, J=1, L={L}, beta={beta:g}, single chain; "
                                f"CPU oracle sample L={ORACLE_SAMPLE_L} at the same beta",
                    "L": L, "beta": beta, "sample_L": ORACLE_SAMPLE_L},
-        "cpu_baseline": {"value": value, "unit": "V+E/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "V+E/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
                          "sample": f"keyed oracle, L={ORACLE_SAMPLE_L}, beta={beta:g}, {steps} updates after {warm}"},
         "e2e": {"value": value, "unit": "V+E/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -215,7 +230,7 @@ def run_sw_reference(args, world, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": f"Swendsen-Wang, L={SW_L}, K=K_c; CPU oracle sample L={SW_ORACLE_L}",
                    "L": SW_L, "K": SW_K, "sample_L": SW_ORACLE_L},
-        "cpu_baseline": {"value": value, "unit": "site updates/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "site updates/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
                          "sample": f"Swendsen-Wang oracle, L={SW_ORACLE_L}, {args.steps} updates after "
                                    f"{args.warmup}"},
         "e2e": {"value": value, "unit": "site updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -305,7 +320,7 @@ def run_ours(args, world, rank, local):
     cpu = None
     if rank == 0:
         val, dt, _ = oracle_sample(beta, 4, 2)
-        cpu = {"value": val, "unit": "V+E/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": val, "unit": "V+E/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": f"keyed oracle, L={ORACLE_SAMPLE_L}, beta={beta:g}, 4 updates after 2 ({dt:.1f} s)"}
     mean_n = float(recs["n"].mean())
     line = {
@@ -549,7 +564,7 @@ def run_sw(args, world, rank, local):
     cpu = None
     if rank == 0:
         val, dt = sw_oracle_sample()
-        cpu = {"value": val, "unit": "site updates/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": val, "unit": "site updates/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": f"Swendsen-Wang oracle, L={SW_ORACLE_L}, K=K_c, 5 updates after 2 ({dt:.1f} s)"}
     uf_ms = (ph["tile_bonds_uf"] + ph["boundary_merge"]) / nph
     line = {
