@@ -49,7 +49,7 @@ KERNELS_PER_UPDATE = 11
 TRAFFIC_PER_VERTEX = {"insert": 13.1, "link_union": 26.8, "loop_ids": 7.5, "loop_props": 25.0,
                       "op_rewrite": 14.8}
 TRAFFIC_PER_VERTEX_TEMPORAL = dict(TRAFFIC_PER_VERTEX, loop_props=25.8, op_rewrite=16.6)
-TRAFFIC_KERNELS_SHA1 = "7ebd630de0d79dfd549a877118bf2bab88dac209"
+TRAFFIC_KERNELS_SHA1 = "3b3b8ae50b83d65daa116fa632091ac53cf9e356"
 
 
 # DRAM bytes per launch of each Swendsen-Wang phase at L = 8192, K = K_c (one
