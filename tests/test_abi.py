@@ -55,6 +55,19 @@ def test_invalid_arguments_rejected_on_host(built_lib):
         assert rc == -1, args
 
 
+def test_sw_invalid_arguments_rejected_on_host(built_lib):
+    # The Swendsen-Wang handle validates L and K before any CUDA call.
+    from paper_1810_07485_gb300 import lcqmc
+    L = lcqmc.lib()
+    h = ctypes.c_void_p()
+    for Lx, K in [(1, 0.4), (0, 0.4), (46341, 0.4), (8, -1.0), (8, float("nan")), (8, float("inf"))]:
+        assert L.lcqmc_sw_create(Lx, K, 1, None, ctypes.byref(h)) == -1, (Lx, K)
+        assert h.value is None
+    assert L.lcqmc_sw_update(None, 1) == -1
+    assert L.lcqmc_sw_sync(None) == -1
+    assert b"null handle" in L.lcqmc_last_error()
+
+
 @pytest.mark.parametrize("which", [0, 1])
 def test_integer_rounding_forms_match_libm(built_lib, which):
     # The kernels evaluate fma(t_end - t0, u, t0) and rint(x 2^F) with integer
