@@ -54,9 +54,9 @@ TRAFFIC_KERNELS_SHA1 = "3b3b8ae50b83d65daa116fa632091ac53cf9e356"
 
 # DRAM bytes per launch of each Swendsen-Wang phase at L = 8192, K = K_c (one
 # ncu capture; profiles/sw_L8192_Kc.md), valid for sw.cu with this sha1 only.
-SW_TRAFFIC = {"tile_bonds_uf": 294.7e6, "boundary_merge": 173.4e6, "roots_flip": 444.8e6,
+SW_TRAFFIC = {"tile_bonds_uf": 294.5e6, "boundary_merge": 173.2e6, "roots_flip": 444.6e6,
               "open_sizes_record": 24.4e6}
-SW_TRAFFIC_SHA1 = "4d06f2cca15f4fea3cc7f70aa8ac15f7ddae1fe4"
+SW_TRAFFIC_SHA1 = "dadb5c42ae8fdb32d88e4c88ee578722234bd1c4"
 
 
 def kernels_sha1(name="kernels.cu"):

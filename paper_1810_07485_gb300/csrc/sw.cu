@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(256) k_sw_merge(SwScratch s) {
 }
 
 // ---- roots, coins, flips, cluster sizes ---------------------------------------------
-__global__ void __launch_bounds__(SW_TPB) k_sw_flip(SwScratch s) {
+__global__ void __launch_bounds__(SW_TPB, 6) k_sw_flip(SwScratch s) {
   __shared__ int cnt[SW_TS];
   __shared__ uint8_t coin_s[SW_TS];
   if (__ldcg(s.status)) return;
