@@ -49,7 +49,7 @@ KERNELS_PER_UPDATE = 11
 TRAFFIC_PER_VERTEX = {"insert": 13.1, "link_union": 26.8, "loop_ids": 7.5, "loop_props": 25.0,
                       "op_rewrite": 14.8}
 TRAFFIC_PER_VERTEX_TEMPORAL = dict(TRAFFIC_PER_VERTEX, loop_props=25.8, op_rewrite=16.6)
-TRAFFIC_KERNELS_SHA1 = "3b3b8ae50b83d65daa116fa632091ac53cf9e356"
+TRAFFIC_KERNELS_SHA1 = "fa4001f21f027ccb15dd41a712fca6ac8db77c09"
 
 
 # DRAM bytes per launch of each Swendsen-Wang phase at L = 8192, K = K_c (one
@@ -253,8 +253,11 @@ def run_ours(args, world, rank, local):
     if args.temporal:
         ch.set_temporal(True)
     geo = ch.geometry()
-    # thermalization from the Neel state, then W warm-up updates (untimed)
-    ch.update(therm + args.warmup)
+    # thermalization from the Neel state, the block sizes of the union-find
+    # phases tuned (8 trials of 2 updates), then W warm-up updates (untimed)
+    ch.update(therm)
+    tuning = ch.autotune(2)
+    ch.update(args.warmup)
     ch.sync()
     ch.records()
 
@@ -329,9 +332,10 @@ def run_ours(args, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": f"S=1/2 AFM Heisenberg chain, J=1, L={L}, beta={beta:g}, one chain per GPU "
-                               f"(seed 1+rank), Neel start, {therm}+{args.warmup} untimed updates",
+                               f"(seed 1+rank), Neel start, {therm}+16+{args.warmup} untimed updates "
+                               f"(16: autotuning trials)",
                    "L": L, "beta": beta, "vertices_per_update": mean_n,
-                   "temporal_moment": bool(args.temporal),
+                   "temporal_moment": bool(args.temporal), "tuning": tuning,
                    "l2": "inputs larger than L2 (state and per-update graph are several GB)"},
         "roofline": roofline,
         "cpu_baseline": cpu,

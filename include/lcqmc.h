@@ -194,6 +194,26 @@ int lcqmc_set_phase_timing(lcqmc_handle h, int enable);
  * imaginary time).  Off, those are 0 and every other result is unchanged.
  * Waits for enqueued updates; applies to the following ones. */
 int lcqmc_set_temporal(lcqmc_handle h, int enable);
+
+/* Block sizes of the union-find phases (Sec. 3.2 on the GPU): threads per
+ * block of the tile linking and local union-find (128 or 256), warps per block
+ * of the union of tile-crossing edges (1..8, one tile each) and threads per
+ * block of the compression (32..128 in steps of 32).  Defaults 256, 8, 128.
+ * Any choice gives bit-identical results; only the time changes. */
+typedef struct {
+  int32_t link_threads, link_x_warps, compress_threads, pad;
+} lcqmc_tuning;
+/* Current block sizes (host struct, caller-owned). */
+int lcqmc_get_tuning(lcqmc_handle h, lcqmc_tuning *out);
+/* Waits for enqueued updates, then sets the block sizes; LCQMC_E_INVAL out of
+ * range. */
+int lcqmc_set_tuning(lcqmc_handle h, const lcqmc_tuning *cfg);
+/* Autotuner: times each candidate with the phase events over
+ * updates_per_trial updates (a coordinate search: 128/256 x 2/4/8 for the
+ * linking phase, then 64/128 for the compression; 8 trials) and keeps the
+ * fastest.  The trial updates are ordinary updates of the chain (records and
+ * running sums included).  out (may be NULL) receives the choice. */
+int lcqmc_autotune(lcqmc_handle h, int64_t updates_per_trial, lcqmc_tuning *out);
 int lcqmc_get_phase_times(lcqmc_handle h, double *ms, int nphase);
 
 /* Raw CUDA stream of the handle (cudaStream_t as void*). */
@@ -217,6 +237,11 @@ int lcqmc_batch_create(int64_t nchains, const lcqmc_chain_spec *specs, void *cud
 int lcqmc_batch_update(lcqmc_batch_t b, int64_t n);
 int lcqmc_batch_sync(lcqmc_batch_t b);
 int lcqmc_batch_set_temporal(lcqmc_batch_t b, int enable); /* as lcqmc_set_temporal, all chains */
+/* As lcqmc_get_tuning / lcqmc_set_tuning / lcqmc_autotune for a batch (one
+ * choice for all its chains; trial updates update every chain). */
+int lcqmc_batch_get_tuning(lcqmc_batch_t b, lcqmc_tuning *out);
+int lcqmc_batch_set_tuning(lcqmc_batch_t b, const lcqmc_tuning *cfg);
+int lcqmc_batch_autotune(lcqmc_batch_t b, int64_t updates_per_trial, lcqmc_tuning *out);
 int lcqmc_batch_measure(lcqmc_batch_t b, int64_t chain, lcqmc_obs *out);
 int lcqmc_batch_get_records(lcqmc_batch_t b, int64_t chain, lcqmc_record *out, int64_t max,
                             int64_t *count);

@@ -256,6 +256,27 @@ int lcqmc_set_temporal(lcqmc_handle h, int enable) {
   NEED(h);
   return h->eng.set_temporal(enable);
 }
+int lcqmc_get_tuning(lcqmc_handle h, lcqmc_tuning *out) {
+  NEED(h);
+  if (!out) {
+    lcq::set_error("null output");
+    return LCQMC_E_INVAL;
+  }
+  h->eng.get_tuning(out);
+  return LCQMC_OK;
+}
+int lcqmc_set_tuning(lcqmc_handle h, const lcqmc_tuning *cfg) {
+  NEED(h);
+  if (!cfg) {
+    lcq::set_error("null tuning");
+    return LCQMC_E_INVAL;
+  }
+  return h->eng.set_tuning(*cfg);
+}
+int lcqmc_autotune(lcqmc_handle h, int64_t updates_per_trial, lcqmc_tuning *out) {
+  NEED(h);
+  return h->eng.autotune(updates_per_trial, out);
+}
 int lcqmc_get_phase_times(lcqmc_handle h, double *ms, int nphase) {
   NEED(h);
   if (!ms) return LCQMC_E_INVAL;
@@ -314,6 +335,19 @@ int lcqmc_batch_get_records(lcqmc_batch_t b, int64_t chain, lcqmc_record *out, i
 int lcqmc_batch_set_temporal(lcqmc_batch_t b, int enable) {
   if (!b) return LCQMC_E_INVAL;
   return b->eng.set_temporal(enable);
+}
+int lcqmc_batch_get_tuning(lcqmc_batch_t b, lcqmc_tuning *out) {
+  if (!b || !out) return LCQMC_E_INVAL;
+  b->eng.get_tuning(out);
+  return LCQMC_OK;
+}
+int lcqmc_batch_set_tuning(lcqmc_batch_t b, const lcqmc_tuning *cfg) {
+  if (!b || !cfg) return LCQMC_E_INVAL;
+  return b->eng.set_tuning(*cfg);
+}
+int lcqmc_batch_autotune(lcqmc_batch_t b, int64_t updates_per_trial, lcqmc_tuning *out) {
+  if (!b) return LCQMC_E_INVAL;
+  return b->eng.autotune(updates_per_trial, out);
 }
 int lcqmc_batch_destroy(lcqmc_batch_t b) {
   delete b;

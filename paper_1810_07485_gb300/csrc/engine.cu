@@ -964,6 +964,87 @@ int Engine::set_temporal(int enable) {
   return LCQMC_OK;
 }
 
+void Engine::get_tuning(lcqmc_tuning *out) const {
+  out->link_threads = L_.link_threads;
+  out->link_x_warps = L_.link_x_warps;
+  out->compress_threads = L_.compress_threads;
+  out->pad = 0;
+}
+
+int Engine::set_tuning(const lcqmc_tuning &t) {
+  if (!(t.link_threads == 128 || t.link_threads == 256) || t.link_x_warps < 1 || t.link_x_warps > 8 ||
+      t.compress_threads < 32 || t.compress_threads > 128 || t.compress_threads % 32 != 0) {
+    set_error("tuning out of range: link_threads 128 or 256, link_x_warps 1..8, "
+              "compress_threads 32..128 in steps of 32");
+    return LCQMC_E_INVAL;
+  }
+  int rc = sync();
+  if (rc) return rc;
+  L_.link_threads = t.link_threads;
+  L_.link_x_warps = t.link_x_warps;
+  L_.compress_threads = t.compress_threads;
+  if (gexec_) {  // the captured launches carry the block sizes
+    cudaGraphExecDestroy(gexec_);
+    gexec_ = nullptr;
+  }
+  return LCQMC_OK;
+}
+
+// Coordinate search over the block sizes of the union-find phases, each
+// candidate timed by the phase events over n updates: linking + global unions
+// (phase 2) over link_threads x link_x_warps, then compression (phase 3) over
+// compress_threads.  The trial updates are ordinary updates of every chain;
+// the block sizes do not change any result.
+int Engine::autotune(int64_t n, lcqmc_tuning *out) {
+  if (n < 1) {
+    set_error("autotune needs at least one update per trial");
+    return LCQMC_E_INVAL;
+  }
+  const bool was_timing = timing_;
+  lcqmc_tuning best;
+  get_tuning(&best);
+  auto trial = [&](const lcqmc_tuning &t, int phase, double *ms) -> int {
+    int rc = set_tuning(t);
+    if (!rc) rc = set_phase_timing(1);
+    if (!rc) rc = update(n);
+    if (!rc) rc = sync();
+    if (!rc) *ms = phase_ms_[phase];
+    return rc;
+  };
+  double best_ms = 1e300;
+  static const int link_threads[] = {128, 256}, link_x_warps[] = {2, 4, 8}, compress_threads[] = {64, 128};
+  lcqmc_tuning cur = best;
+  for (int lt : link_threads)
+    for (int xw : link_x_warps) {
+      cur.link_threads = lt;
+      cur.link_x_warps = xw;
+      double ms = 0.0;
+      int rc = trial(cur, 2, &ms);
+      if (rc) return rc;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = cur;
+      }
+    }
+  best_ms = 1e300;
+  cur = best;
+  for (int ct : compress_threads) {
+    cur.compress_threads = ct;
+    double ms = 0.0;
+    int rc = trial(cur, 3, &ms);
+    if (rc) return rc;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best.compress_threads = ct;
+    }
+  }
+  int rc = set_tuning(best);
+  if (!rc) rc = set_phase_timing(was_timing ? 1 : 0);
+  if (rc) return rc;
+  if (out) *out = best;
+  return LCQMC_OK;
+}
+
 int Engine::phase_times(double *ms, int nphase) {
   int rc = sync();
   if (rc) return rc;

@@ -73,6 +73,11 @@ class Engine {
   int export_cells(int64_t chain, int32_t *vptr, int64_t cap);
   int set_phase_timing(int enable);
   int set_temporal(int enable);  // temporal moment chi(pi, 2 pi/beta) for every chain
+  // block sizes of the union-find phases: read, set (checked), or tuned by
+  // timing each candidate over n updates of the batch (ordinary updates)
+  void get_tuning(lcqmc_tuning *out) const;
+  int set_tuning(const lcqmc_tuning &t);
+  int autotune(int64_t n, lcqmc_tuning *out);
   int phase_times(double *ms, int nphase);
   size_t footprint() const;  // device bytes held
   static size_t estimate_footprint(const std::vector<ChainSpec> &specs, int ring_cap);

@@ -1027,7 +1027,7 @@ __global__ void __launch_bounds__(TPB_X) k_link_x(const DevChain *__restrict__ c
                                                 Scratch s) {
   if (halted(s)) return;
   const int lane = threadIdx.x & 31;
-  const int64_t gt = (int64_t)blockIdx.x * (TPB_X / 32) + (threadIdx.x >> 5);
+  const int64_t gt = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (gt >= ntiles) return;
   const int2 t = tab[gt];
   const DevChain &C = ch[t.x];
@@ -1637,17 +1637,19 @@ void launch_cut(const Launch &L, cudaStream_t st) {
 }
 
 void launch_link(const Launch &L, cudaStream_t st) {
-#define LINK_Q(Q) \
-  if (L.ntile[Q - 1]) k_link<Q><<<g1(L.ntile[Q - 1]), TPB, 0, st>>>(L.ch, L.tile_tab, L.tile0[Q - 1], L.s);
+#define LINK_Q(Q)     \
+  if (L.ntile[Q - 1]) \
+    k_link<Q><<<g1(L.ntile[Q - 1]), L.link_threads, 0, st>>>(L.ch, L.tile_tab, L.tile0[Q - 1], L.s);
   FOR_EACH_Q(LINK_Q)
 #undef LINK_Q
   const int64_t n = all_tiles(L);
-  if (n) k_link_x<<<g1((n + TPB_X / 32 - 1) / (TPB_X / 32)), TPB_X, 0, st>>>(L.ch, L.tile_tab, n, L.s);
+  const int wpb = L.link_x_warps;
+  if (n) k_link_x<<<g1((n + wpb - 1) / wpb), 32 * wpb, 0, st>>>(L.ch, L.tile_tab, n, L.s);
 }
 
 void launch_compress(const Launch &L, cudaStream_t st) {
   const int64_t n = all_tiles(L);
-  if (n) k_compress<<<g1(n), TILE, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
+  if (n) k_compress<<<g1(n), L.compress_threads, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
 }
 
 // Per-vertex staging of the loop-properties kernel: ticks and phase factors.

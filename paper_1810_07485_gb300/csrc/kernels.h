@@ -16,6 +16,10 @@ struct Launch {
   int64_t nsiteblk[QMAX], site0[QMAX];
   int64_t nbondblk[QMAX], bond0[QMAX];
   int temporal;  // measure the temporal moment chi(pi, 2 pi / beta) too
+  // block sizes of the union-find phases (any choice gives the same results)
+  int link_threads = 256;     // k_link: 128 or 256
+  int link_x_warps = 8;       // k_link_x: 1 .. 8 warps (one tile each) per block
+  int compress_threads = 128; // k_compress: 32, 64, 96 or 128
 };
 
 void set_full_table(const uint64_t *T, cudaStream_t st);

@@ -36,6 +36,15 @@ class Obs(ctypes.Structure):
                 ("xi_tau", ctypes.c_double), ("gap", ctypes.c_double)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("link_threads", ctypes.c_int32), ("link_x_warps", ctypes.c_int32),
+                ("compress_threads", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {"link_threads": self.link_threads, "link_x_warps": self.link_x_warps,
+                "compress_threads": self.compress_threads}
+
+
 SW_NOBS = 4  # energy per site, sum_c |c|^2 / N, M^2 / N, |M| / N
 SW_NPHASE = 4
 SW_PHASES = ("tile_bonds_uf", "boundary_merge", "roots_flip", "open_sizes_record")
@@ -128,6 +137,12 @@ def lib():
         "lcqmc_restore": [vp, vp, ctypes.c_size_t],
         "lcqmc_set_phase_timing": [vp, i32],
         "lcqmc_set_temporal": [vp, i32],
+        "lcqmc_get_tuning": [vp, P(Tuning)],
+        "lcqmc_set_tuning": [vp, P(Tuning)],
+        "lcqmc_autotune": [vp, i64, P(Tuning)],
+        "lcqmc_batch_get_tuning": [vp, P(Tuning)],
+        "lcqmc_batch_set_tuning": [vp, P(Tuning)],
+        "lcqmc_batch_autotune": [vp, i64, P(Tuning)],
         "lcqmc_get_phase_times": [vp, vp, i32],
         "lcqmc_destroy": [vp],
         "lcqmc_batch_create": [i64, vp, vp, P(vp)],
@@ -301,6 +316,20 @@ class Chain:
         """Temporal moment chi(pi, 2 pi / beta) on or off (off after create)."""
         _check(lib().lcqmc_set_temporal(self.h, 1 if on else 0))
 
+    def tuning(self):
+        t = Tuning()
+        _check(lib().lcqmc_get_tuning(self.h, ctypes.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, link_threads=256, link_x_warps=8, compress_threads=128):
+        _check(lib().lcqmc_set_tuning(self.h, ctypes.byref(Tuning(link_threads, link_x_warps,
+                                                                  compress_threads, 0))))
+
+    def autotune(self, updates_per_trial=2):
+        t = Tuning()
+        _check(lib().lcqmc_autotune(self.h, int(updates_per_trial), ctypes.byref(t)))
+        return t.as_dict()
+
     def phase_times(self):
         ms = np.zeros(NPHASE)
         _check(lib().lcqmc_get_phase_times(self.h, _p(ms), NPHASE))
@@ -340,6 +369,20 @@ class Batch:
 
     def set_temporal(self, on=True):
         _check(lib().lcqmc_batch_set_temporal(self.h, 1 if on else 0))
+
+    def tuning(self):
+        t = Tuning()
+        _check(lib().lcqmc_batch_get_tuning(self.h, ctypes.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, link_threads=256, link_x_warps=8, compress_threads=128):
+        _check(lib().lcqmc_batch_set_tuning(self.h, ctypes.byref(Tuning(link_threads, link_x_warps,
+                                                                        compress_threads, 0))))
+
+    def autotune(self, updates_per_trial=1):
+        t = Tuning()
+        _check(lib().lcqmc_batch_autotune(self.h, int(updates_per_trial), ctypes.byref(t)))
+        return t.as_dict()
 
     def measure(self, i):
         o = Obs()

@@ -296,3 +296,50 @@ def test_batch_temporal_switch():
         for t in range(5):
             assert_records_equal(rg[t], ro[t], (i, t))
     b.close()
+
+
+def test_tuning_gives_identical_results():
+    # The block sizes of the union-find phases change no result.
+    lc = gpu()
+    L, beta = 1024, 40.0
+    a = lc.Chain(L, beta, seed=3)
+    b = lc.Chain(L, beta, seed=3)
+    assert a.tuning() == {"link_threads": 256, "link_x_warps": 8, "compress_threads": 128}
+    b.set_tuning(link_threads=128, link_x_warps=2, compress_threads=64)
+    assert b.tuning() == {"link_threads": 128, "link_x_warps": 2, "compress_threads": 64}
+    a.update(10)
+    b.update(10)
+    assert np.array_equal(a.records(), b.records())
+    assert_state_equal(gpu_state(a), gpu_state(b))
+    with pytest.raises(lc.LcqmcError):
+        b.set_tuning(link_threads=192)
+    with pytest.raises(lc.LcqmcError):
+        b.set_tuning(compress_threads=160)
+    # autotune: 8 trials of 2 ordinary updates; the chain goes on as an
+    # untuned chain advanced by the same 16 updates
+    c = lc.Chain(L, beta, seed=3)
+    t = c.autotune(2)
+    assert t["link_threads"] in (128, 256) and t["link_x_warps"] in (2, 4, 8) and t["compress_threads"] in (64, 128)
+    d = lc.Chain(L, beta, seed=3)
+    d.update(16)
+    c.update(5)
+    d.update(5)
+    rc, rd = c.records(), d.records()
+    assert len(rc) == len(rd) == 21 and np.array_equal(rc, rd)
+    assert_state_equal(gpu_state(c), gpu_state(d))
+    for h in (a, b, c, d):
+        h.close()
+
+
+def test_batch_autotune_identical():
+    lc = gpu()
+    specs = [dict(L=64, beta=16.0, seed=1), dict(L=200, beta=30.0, S=1.0, seed=2)]
+    b1, b2 = lc.Batch(specs), lc.Batch(specs)
+    b1.autotune(1)
+    b2.update(8)
+    b1.update(3)
+    b2.update(3)
+    for i in range(len(specs)):
+        assert np.array_equal(b1.records(i), b2.records(i))
+    b1.close()
+    b2.close()
