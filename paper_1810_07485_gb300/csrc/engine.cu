@@ -11,7 +11,17 @@
 
 #include "engine.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace lcq {
+
+// NVTX range for profilers (no-op unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 static thread_local std::string g_err;
 void set_error(const std::string &msg) { g_err = msg; }
@@ -257,6 +267,8 @@ int Engine::open(void *stream, const lcqmc_allocator *alloc, int ring_cap) {
     set_error("device table initialization failed");
     return LCQMC_E_CUDA;
   }
+  // Debug: verify the loop forest after every compression.
+  if (const char *e = std::getenv("LCQMC_CHECK_FOREST")) L_.check_forest = std::atoi(e) != 0;
   if (alloc && alloc->alloc && alloc->free) {
     alloc_ = *alloc;
     has_alloc_ = true;
@@ -541,8 +553,16 @@ int Engine::init(const std::vector<ChainSpec> &specs, void *stream, const lcqmc_
 // ---- update sequence ---------------------------------------------------------------------
 int Engine::enqueue_one(bool timed, int slot) {
   const int64_t nw = vcap_ / 32 + 1;
+  // phases as in the paper's Table 3 rows: event pairs and NVTX ranges
+  static const char *const kPhase[LCQMC_NPHASE] = {"lcqmc.insert",    "lcqmc.cut",
+                                                   "lcqmc.link_union", "lcqmc.loop_ids",
+                                                   "lcqmc.loop_props", "lcqmc.op_offsets",
+                                                   "lcqmc.op_rewrite", "lcqmc.spin_rewrite"};
   auto mark = [&](int k) {
-    if (timed) cudaEventRecord(ev_[slot * (LCQMC_NPHASE + 1) + k], st_);
+    if (!timed) return;
+    cudaEventRecord(ev_[slot * (LCQMC_NPHASE + 1) + k], st_);
+    if (k > 0) nvtxRangePop();
+    if (k < LCQMC_NPHASE) nvtxRangePushA(kPhase[k]);
   };
   mark(0);  // [0] labeling: random numbers, insertion, vertex offsets (one pass)
   launch_bond_parity(L_, st_);
@@ -559,6 +579,7 @@ int Engine::enqueue_one(bool timed, int slot) {
   launch_link(L_, st_);
   mark(3);  // [3] loop ids (compression, coins)
   launch_compress(L_, st_);
+  if (L_.check_forest) launch_check_forest(L_, st_);
   mark(4);  // [4] loop properties, new flags
   launch_est(L_, st_);
   mark(5);  // [5] operator offsets
@@ -592,6 +613,7 @@ int Engine::update(int64_t n) {
     return LCQMC_E_INVAL;
   }
   if (n == 0) return LCQMC_OK;
+  NvtxRange range("lcqmc_update");
   if (pending_ == 0) pending_sweep0_ = hch[0].sweep;
   if (timing_) {
     const int per = LCQMC_NPHASE + 1;

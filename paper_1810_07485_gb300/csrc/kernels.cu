@@ -1118,6 +1118,26 @@ __global__ void __launch_bounds__(TILE) k_compress(const DevChain *__restrict__ 
   if (threadIdx.x == 0) s.tile_roots[gt] = tot;
 }
 
+// ---- opt-in check of the loop forest after compression ----------------------------
+// Every node's word is its loop's root, a root is its own parent and no parent
+// is larger than its child (min-root rule).  The first violation is reported
+// as consistency check 10 (chain, node, word, word of the word).
+__global__ void __launch_bounds__(TILE) k_check_forest(const DevChain *__restrict__ ch,
+                                                       const int2 *__restrict__ tab, Scratch s) {
+  if (halted(s)) return;
+  const int2 t = tab[blockIdx.x];
+  const DevChain &C = ch[t.x];
+  const int c0 = t.y * TILE, c1 = min(C.ncell, c0 + TILE);
+  const int32_t *vp = s.vptr + C.cell_off;
+  const int a = vp[c0], e = vp[c1];
+  const int32_t *par = s.parent + C.vtx_base;
+  for (int v = a + threadIdx.x; v < e; v += blockDim.x) {
+    const int r = __ldcg(par + v);
+    const int rr = (r >= 0 && r <= v) ? __ldcg(par + r) : -1;
+    if (r < 0 || r > v || rr != r) fail_check(s, 10, t.x, v, r, rr, 0);
+  }
+}
+
 // ---- loop properties, new flags ---------------------------------------------------
 // Exact 64-bit two's-complement sums kept in shared memory as two 32-bit words
 // and added with native 32-bit atomics (a 64-bit shared-memory add would be a
@@ -1650,6 +1670,11 @@ void launch_link(const Launch &L, cudaStream_t st) {
 void launch_compress(const Launch &L, cudaStream_t st) {
   const int64_t n = all_tiles(L);
   if (n) k_compress<<<g1(n), L.compress_threads, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
+}
+
+void launch_check_forest(const Launch &L, cudaStream_t st) {
+  const int64_t n = all_tiles(L);
+  if (n) k_check_forest<<<g1(n), TILE, 0, st>>>(L.ch, L.tile_tab, L.s);
 }
 
 // Per-vertex staging of the loop-properties kernel: ticks and phase factors.

@@ -33,6 +33,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dev.cuh"
 #include "engine.h"
 #include "uf.cuh"
@@ -570,6 +572,13 @@ class SwEngine {
       set_error("n must be >= 0");
       return LCQMC_E_INVAL;
     }
+    nvtxRangePushA("lcqmc_sw_update");  // profiler range (no-op without a tool)
+    const int rc = update_n(n);
+    nvtxRangePop();
+    return rc;
+  }
+
+  int update_n(int64_t n) {
     for (int64_t i = 0; i < n; ++i) {
       if (timing_) {
         int rc = enqueue(true);
