@@ -111,3 +111,18 @@ def test_rank_seeds_distinct():
     import bench
     seeds = [bench.chain_seed(r) for r in range(8)]
     assert len(set(seeds)) == 8
+
+
+@pytest.mark.timeout(300)
+def test_oracle_all_cores_sample(orc):
+    # The all-core oracle baseline: independent chains in spawned processes,
+    # each the same as the chain run alone with its seed.
+    import bench
+    val, procs = bench.oracle_sample_all_cores(4.0, 2, 1, L=16, procs=2)
+    assert procs == 2 and val > 0
+    ve, dt = bench._oracle_chain_worker((16, 4.0, 2, 1, 2))
+    p = orc.params(16, 4.0, seed=2)
+    st = orc.neel(p)
+    orc.keyed_run(p, 0, 1, st)
+    r = orc.keyed_run(p, 1, 2, st)
+    assert ve == float((r["n_seg"] + 2 * r["n"]).sum())
