@@ -199,27 +199,11 @@ def oracle_sample(beta, steps, warmup, L=ORACLE_SAMPLE_L):
     return ve / dt, dt, recs
 
 
-def _oracle_chain_worker(job):
-    """One independent oracle chain (run in a spawned process)."""
-    L, beta, seed, warmup, steps = job
-    from oracle import orc
-    p = orc.params(L, beta, seed=seed)
-    st = orc.neel(p)
-    orc.keyed_run(p, 0, warmup, st)
-    t0 = time.perf_counter()
-    recs = orc.keyed_run(p, warmup, steps, st)
-    return float((recs["n_seg"] + 2 * recs["n"]).sum()), time.perf_counter() - t0
-
-
 def oracle_sample_all_cores(beta, steps, warmup, L=ORACLE_SAMPLE_L, procs=None):
     """The oracle on every host core at once, one independent chain per core
-    (the paper's independent-chain strategy): V+E of all chains / the slowest
-    chain's time.  A spawned pool: the parent has already used the GPU."""
-    import multiprocessing as mp
-    procs = procs or os.cpu_count() or 1
-    with mp.get_context("spawn").Pool(procs) as pool:
-        out = pool.map(_oracle_chain_worker, [(L, beta, 1 + k, warmup, steps) for k in range(procs)])
-    return sum(v for v, _ in out) / max(t for _, t in out), procs
+    (the paper's independent-chain strategy)."""
+    from oracle import timing
+    return timing.all_cores_sample(L, beta, steps, warmup, procs)
 
 
 def run_reference(args, world, rank):

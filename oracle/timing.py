@@ -1,0 +1,31 @@
+"""Timing of the CPU oracle on every host core (test infrastructure: used by
+the benchmark's CPU-baseline leg only).
+
+One independent keyed-oracle chain per core, as the paper runs independent
+chains side by side: the rate is the V+E of all chains over the slowest
+chain's time.  Workers start by spawn (the caller may already hold a GPU
+context, which a forked child must not inherit).
+"""
+import multiprocessing as mp
+import os
+import time
+
+
+def chain_sample(job):
+    """One chain: (L, beta, seed, warmup, steps) -> (V+E of the timed updates, seconds)."""
+    L, beta, seed, warmup, steps = job
+    from oracle import orc
+    p = orc.params(L, beta, seed=seed)
+    st = orc.neel(p)
+    orc.keyed_run(p, 0, warmup, st)
+    t0 = time.perf_counter()
+    recs = orc.keyed_run(p, warmup, steps, st)
+    return float((recs["n_seg"] + 2 * recs["n"]).sum()), time.perf_counter() - t0
+
+
+def all_cores_sample(L, beta, steps, warmup, procs=None):
+    """(V+E/s over procs chains run at once, procs)."""
+    procs = procs or os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(procs) as pool:
+        out = pool.map(chain_sample, [(L, beta, 1 + k, warmup, steps) for k in range(procs)])
+    return sum(v for v, _ in out) / max(t for _, t in out), procs

@@ -120,7 +120,8 @@ def test_oracle_all_cores_sample(orc):
     import bench
     val, procs = bench.oracle_sample_all_cores(4.0, 2, 1, L=16, procs=2)
     assert procs == 2 and val > 0
-    ve, dt = bench._oracle_chain_worker((16, 4.0, 2, 1, 2))
+    from oracle import timing
+    ve, dt = timing.chain_sample((16, 4.0, 2, 1, 2))
     p = orc.params(16, 4.0, seed=2)
     st = orc.neel(p)
     orc.keyed_run(p, 0, 1, st)
