@@ -23,9 +23,19 @@ def chain_sample(job):
     return float((recs["n_seg"] + 2 * recs["n"]).sum()), time.perf_counter() - t0
 
 
+def _memory_cap(bytes_per_chain=1.5e9):
+    """Chains that fit the host's available memory (a chain of the default
+    sample, L = 1024 at beta = 4096, peaks near 0.7 GB)."""
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+        return max(1, int(avail // bytes_per_chain))
+    except (ValueError, OSError):
+        return 1
+
+
 def all_cores_sample(L, beta, steps, warmup, procs=None):
     """(V+E/s over procs chains run at once, procs)."""
-    procs = procs or os.cpu_count() or 1
+    procs = procs or min(os.cpu_count() or 1, _memory_cap())
     with mp.get_context("spawn").Pool(procs) as pool:
         out = pool.map(chain_sample, [(L, beta, 1 + k, warmup, steps) for k in range(procs)])
     return sum(v for v, _ in out) / max(t for _, t in out), procs
