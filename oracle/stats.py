@@ -37,5 +37,13 @@ def xi_second_moment(L):
     return f
 
 
+def xi_tau(beta):
+    """xi_tau = (beta / 2 pi) sqrt(chi(pi, 0) / chi(pi, 2 pi / beta) - 1): the
+    imaginary-time second moment (Sec. 5); the gap is 1 / xi_tau."""
+    def f(chi_s, chi_w):
+        return beta / (2 * np.pi) * np.sqrt(max(chi_s / chi_w - 1.0, 0.0))
+    return f
+
+
 def within_sigma(value, err, ref, nsigma=3.0, ref_err=0.0):
     return abs(value - ref) <= nsigma * np.sqrt(err ** 2 + ref_err ** 2)
