@@ -127,3 +127,19 @@ def test_oracle_all_cores_sample(orc):
     orc.keyed_run(p, 0, 1, st)
     r = orc.keyed_run(p, 1, 2, st)
     assert ve == float((r["n_seg"] + 2 * r["n"]).sum())
+
+
+def test_sw_reference_arm_line(capsys):
+    # bench.py --impl reference --mode sw: the oracle on rank 0 only, with the
+    # contract's keys; the other ranks print nothing.
+    import json
+
+    import bench
+    args = argparse.Namespace(steps=3, warmup=3, gpus=2)
+    bench.run_sw_reference(args, 2, 1)
+    assert capsys.readouterr().out == ""
+    bench.run_sw_reference(args, 2, 0)
+    line = json.loads(capsys.readouterr().out.strip())
+    assert line["impl"] == "reference" and line["unit"] == "site updates/s" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["config"]["L"] == bench.SW_L
