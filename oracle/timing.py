@@ -33,9 +33,12 @@ def _memory_cap(bytes_per_chain=1.5e9):
         return 1
 
 
+MAX_PROCS = 32  # bounds the sample's start-up time on large hosts
+
+
 def all_cores_sample(L, beta, steps, warmup, procs=None):
     """(V+E/s over procs chains run at once, procs)."""
-    procs = procs or min(os.cpu_count() or 1, _memory_cap())
+    procs = procs or min(os.cpu_count() or 1, _memory_cap(), MAX_PROCS)
     with mp.get_context("spawn").Pool(procs) as pool:
         out = pool.map(chain_sample, [(L, beta, 1 + k, warmup, steps) for k in range(procs)])
     return sum(v for v, _ in out) / max(t for _, t in out), procs
