@@ -24,6 +24,28 @@ def test_header_declares_core_api():
         assert n in names
 
 
+def test_header_compiles_as_c(tmp_path):
+    # The boundary is a C ABI: the header must compile as plain C11.
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "use.c"
+    src.write_text(
+        '#include "lcqmc.h"\n'
+        "int use(void) {\n"
+        "  lcqmc_handle h = 0; lcqmc_obs o; lcqmc_record r; lcqmc_sw_t sw = 0; lcqmc_tuning t;\n"
+        "  int64_t n = 0; (void)o; (void)r; (void)t;\n"
+        "  if (lcqmc_create(64, 0.5, 1.0, 8.0, 1, &h) != LCQMC_OK) return 1;\n"
+        "  lcqmc_update(h, 1); lcqmc_get_records(h, &r, 1, &n); lcqmc_destroy(h);\n"
+        "  lcqmc_sw_create(64, 0.44, 1, 0, &sw); lcqmc_sw_destroy(sw);\n"
+        "  return (int)n;\n"
+        "}\n")
+    import subprocess
+    r = subprocess.run([gcc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        "-c", str(src), "-o", str(tmp_path / "use.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 @pytest.fixture(scope="module")
 def built_lib():
     if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
