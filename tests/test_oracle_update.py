@@ -17,6 +17,7 @@ import numpy as np
 import pytest
 
 from oracle import ed, stats
+from oracle import orc as _orc
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -300,3 +301,196 @@ def test_phase_factor(orc):
             c, s = orc.phase(int(q), qbeta)
             ang = 2 * np.pi * (int(q) / qbeta)
             assert abs(c - np.cos(ang) * 2**30) < 4.0 and abs(s - np.sin(ang) * 2**30) < 4.0, (qbeta, q)
+
+
+def cut_permutation_q2(p, sweep, s0, nlegs):
+    """tau = 0 joins of an S = 1 chain (2 subspins per site): the top of
+    subsite u continues into the bottom of perm[u].  A join must connect equal
+    spins (top spin = s0 xor the parity of the subsite's off-diagonal
+    operators, nlegs[u]); where both
+    joins are allowed, the coin of tag 4 at the site index decides (swap on 1).
+    Philox itself is pinned against cuRAND (test_oracle_rng.py)."""
+    L, seed = int(p.L), int(p.seed)
+    perm = np.arange(2 * L)
+    for i in range(L):
+        u0, u1 = 2 * i, 2 * i + 1
+        t0, t1 = int(s0[u0]) ^ (nlegs[u0] & 1), int(s0[u1]) ^ (nlegs[u1] & 1)
+        ok_id = t0 == s0[u0] and t1 == s0[u1]
+        ok_sw = t0 == s0[u1] and t1 == s0[u0]
+        if ok_id and ok_sw:
+            w = _orc.philox([4 << 24, i >> 7, 0, sweep], [seed & 0xFFFFFFFF, seed >> 32])
+            swap = (int(w[(i & 127) >> 5]) >> (i & 31)) & 1
+        else:
+            assert ok_id or ok_sw
+            swap = int(ok_sw)
+        if swap:
+            perm[u0], perm[u1] = u1, u0
+    return perm
+
+
+def plain_loop_moments(p, gr, perm=None):
+    """The estimators' plain definitions (Sec. 2 improved estimators, Sec. 5
+    moment estimators), in fp64 from the exported vertices, with none of the
+    oracle's fixed-point arithmetic: per loop c, W_c = sum of its fragments'
+    lengths, C_c + i S_c = sum of len e^{i k x} (k = 2 pi / L, x the fragment's
+    site) and Z_c = sum over fragments of e^{i w1 tau_top} - e^{i w1 tau_bottom}
+    (w1 = 2 pi / beta, so that Z_c / (i w1) is the loop's integral of
+    e^{i w1 tau}).
+
+    The fragments are rebuilt here: on every subsite the legs are ordered by
+    (tau, vertex id); a fragment runs from one leg up to the next, and from the
+    last leg up through tau = beta into the bottom of perm[u] (the tau = 0
+    join; the identity for S = 1/2), on through every empty subspin it meets
+    (one more period each), to the next leg.  A fragment belongs to the loop
+    of the vertex at its lower end (node = the pair of fragments above a
+    vertex).  Cycles of perm through empty subsites only are vertex-free loops
+    of m periods.  With perm = None (S >= 3/2 here) the tau = 0 joins are read
+    off the exported predecessors, which is exact when no subsite is empty.
+
+    Returns (per-loop W, C, S, Z, fragment counts, total length, free loops)."""
+    L, Q, beta = int(p.L), int(p.Q), float(p.beta)
+    tau = np.asarray(gr["tau"], np.float64)
+    bond = np.asarray(gr["bond"], np.int64)
+    root = np.asarray(gr["root"], np.int64)
+    n = len(tau)
+    ul = (bond // (Q * Q)) * Q + (bond // Q) % Q
+    ur = ((bond // (Q * Q) + 1) % L) * Q + bond % Q
+    legs = [[] for _ in range(L * Q)]
+    for v in range(n):
+        legs[int(ul[v])].append((tau[v], v))
+        legs[int(ur[v])].append((tau[v], v))
+    for lst in legs:
+        lst.sort()
+    if perm is None:
+        assert Q == 1 or all(legs), "perm needed where a subsite is empty"
+        perm = np.arange(L * Q)
+        if Q > 1:
+            first = {lst[0][1]: u for u, lst in enumerate(legs)}  # unique ids per subsite's first leg
+            for u, lst in enumerate(legs):
+                v = lst[-1][1]
+                # the fragment above u's last leg ends at the first leg w of
+                # some subsite of the same site whose predecessor there is v
+                for w_u in range((u // Q) * Q, (u // Q + 1) * Q):
+                    w = legs[w_u][0][1]
+                    pred = gr["pl"][w] if int(ul[w]) == w_u else gr["pr"][w]
+                    if int(pred) == v and first.get(w) is not None:
+                        perm[u] = w_u
+                        break
+            assert sorted(perm) == list(range(L * Q))
+    k, w1 = 2 * np.pi / L, 2 * np.pi / beta
+    acc = {}
+    total = 0.0
+
+    def add(r, length, x, tb, tt):
+        a = acc.setdefault(r, [0.0, 0.0, 0.0, 0j, 0])
+        a[0] += length
+        a[1] += length * np.cos(k * x)
+        a[2] += length * np.sin(k * x)
+        a[3] += np.exp(1j * w1 * tt) - np.exp(1j * w1 * tb)
+        a[4] += 1
+
+    for u, lst in enumerate(legs):
+        x = u // Q
+        for (ta, va), (tb_, _) in zip(lst[:-1], lst[1:]):
+            add(int(root[va]), tb_ - ta, x, ta, tb_)
+            total += tb_ - ta
+        if lst:
+            t_last, v_last = lst[-1]
+            c, nxt = 1, int(perm[u])
+            while not legs[nxt]:
+                c += 1
+                nxt = int(perm[nxt])
+                assert c <= Q
+            t_first = legs[nxt][0][0]
+            add(int(root[v_last]), t_first - t_last + c * beta, x, t_last, t_first)
+            total += t_first - t_last + c * beta
+    seen = np.zeros(L * Q, bool)
+    n_free = 0
+    for u in range(L * Q):
+        if legs[u] or seen[u]:
+            continue
+        cyc, y = [], u
+        while not seen[y] and not legs[y]:
+            seen[y] = True
+            cyc.append(y)
+            y = int(perm[y])
+        if y == u:  # a cycle of empty subsites: one vertex-free loop
+            m = len(cyc)
+            acc[("free", u)] = [m * beta, m * beta * np.cos(k * (u // Q)), m * beta * np.sin(k * (u // Q)), 0j, 1]
+            total += m * beta
+            n_free += 1
+    vals = list(acc.values())
+    W = np.array([a[0] for a in vals])
+    C = np.array([a[1] for a in vals])
+    S = np.array([a[2] for a in vals])
+    Z = np.array([a[3] for a in vals])
+    nf = np.array([a[4] for a in vals], np.float64)
+    return W, C, S, Z, nf, total, n_free
+
+
+def _square_sum_bound(X, delta):
+    """Largest |sum |X_c|^2 - sum |X_c + e_c|^2| over |e_c| <= delta_c."""
+    return float(np.sum(2 * np.abs(X) * delta + delta * delta))
+
+
+@pytest.mark.parametrize("L,beta,Q", [(2, 3.0, 1), (8, 6.0, 1), (16, 0.5, 1), (64, 16.0, 1),
+                                      (250, 70.0, 1), (8, 10.0, 2), (12, 0.4, 2), (4, 8.0, 3),
+                                      (4, 8.0, 4)])
+def test_estimators_vs_plain_fp64(orc, L, beta, Q):
+    """The oracle's estimators (ticks of 2^-F, 32-bit Fourier weights, the
+    interpolated phase table, exact integer sums) against their plain fp64
+    definitions, within the bound their arithmetic implies:
+      * a fragment's length in ticks is off by at most one tick 2^-F (two
+        roundings of half a tick);
+      * its Fourier term adds at most len 2^-33 (the 32-bit cos/sin weight) and
+        half a tick (the rounding of the product);
+      * a phase factor is off by at most 4 units of 2^-30 (pinned against numpy
+        in test_phase_factor) plus w1 times half a tick (the rounded time);
+    summed per loop into delta_c and carried through the squares.  A dropped
+    term, a wrong sign, a wrong site or exponent F, or a wrong crossing count
+    each miss by orders of magnitude more."""
+    p = orc.params(L, beta, Q=Q, seed=4000 + L + Q)
+    st = orc.neel(p)
+    F = orc.geometry(p)["F"]
+    tick = 2.0 ** -F
+    w1 = 2 * np.pi / beta
+    checked = 0
+    saw_free = saw_wrap = False
+    for t in range(12):
+        new, rec, gr = orc.keyed_update(p, t, st, graph=True)
+        perm = None
+        if Q == 2:
+            ob = gr["bond"][gr["flag"] != 0]  # off-diagonal operators flip spins, diagonal ones do not
+            ends = np.concatenate([(ob // 4) * 2 + (ob // 2) % 2, ((ob // 4 + 1) % L) * 2 + ob % 2])
+            perm = cut_permutation_q2(p, t, st.s0, np.bincount(ends, minlength=2 * L))
+        st = new
+        W, C, S, Z, nf, total, n_free = plain_loop_moments(p, gr, perm)
+        # crossings: the fragments and free loops cover every subsite's period once
+        assert total == pytest.approx(Q * L * beta, rel=1e-12), (t, total)
+        assert int(rec["n_free"]) == n_free
+        saw_free |= n_free > 0
+        saw_wrap |= bool(np.any(nf > 1))
+        norm = 4.0 * beta * L
+        chi_s, chi_q = np.sum(W * W) / norm, np.sum(C * C + S * S) / norm
+        chi_w = np.sum(np.abs(Z) ** 2) / (w1 * w1) / norm
+        dW = nf * tick
+        dF = nf * (1.5 * tick) + np.abs(W) * 2.0 ** -33
+        dZ = nf * 2 * (4 * 2.0 ** -30 + w1 * 0.5 * tick)
+        fp = 1e-13  # fp64 rounding of the plain sums
+        tol_s = _square_sum_bound(W, dW) / norm + fp * chi_s
+        tol_q = (_square_sum_bound(C, dF) + _square_sum_bound(S, dF)) / norm + fp * chi_q
+        tol_w = _square_sum_bound(Z, dZ) / (w1 * w1) / norm + fp * chi_w
+        assert abs(float(rec["chi_s"]) - chi_s) <= tol_s, (t, rec["chi_s"], chi_s, tol_s)
+        assert abs(float(rec["chi_q"]) - chi_q) <= tol_q, (t, rec["chi_q"], chi_q, tol_q)
+        assert abs(float(rec["chi_w"]) - chi_w) <= tol_w, (t, rec["chi_w"], chi_w, tol_w)
+        # the bounds are tight enough to matter: far below the loop moments
+        # themselves (chi_q may vanish: at L = 2, q = 2 pi is the conserved
+        # uniform magnetization)
+        assert tol_s <= 1e-8 * chi_s and tol_q <= 1e-8 * chi_s
+        n = int(rec["n"])
+        assert float(rec["energy"]) == pytest.approx(Q * Q * p.J / 4 - n / (beta * L), rel=1e-14, abs=1e-15)
+        assert int(rec["n_clusters"]) == len(W)
+        checked += 1
+    assert checked == 12
+    if (L, beta, Q) in ((16, 0.5, 1), (12, 0.4, 2)):
+        assert saw_free
