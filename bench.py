@@ -3,12 +3,16 @@
 loop-cluster update of the S=1/2 antiferromagnetic Heisenberg chain.
 
 One step = one loop update (insertion, linking, union-find, flip, rewrite,
-measurement) of a single chain with L = 2^16 sites at beta = 2^12 (about
-1.9e8 graph vertices, 3.7e8 world-line fragments per update).  V+E counts the
-paper's graph: fragments + 2 x vertices (Sec. 4.4).
+measurement) of a single chain with L = 2^20 sites at beta = 2^10 (about
+7.4e8 graph vertices, 1.5e9 world-line fragments per update), the largest
+single-chain configuration of the benchmark list.  V+E counts the paper's
+graph: fragments + 2 x vertices (Sec. 4.4).  The same line carries the
+batched form beside it: 4096 uneven chains, 100 updates each, packed per
+phase and replayed from a CUDA graph, against the same chains launched one
+at a time (per-chain completion p50/p99, results identical).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-  python bench.py --mode batched [--chains C --updates U]   (many uneven chains)
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-batched]
+  python bench.py --mode batched [--chains C --updates U]   (the batched form alone)
   python bench.py --mode served [--requests R --rate Hz]    (request stream)
 
 Under torchrun each rank runs its own chain (seed 1 + rank): independent Markov
@@ -37,9 +41,13 @@ WORKLOADS = {
     "L64_beta16": (64, 16.0, 1000),
     "L16384_beta4096": (1 << 14, float(1 << 12), 6),
 }
-DEFAULT_WORKLOAD = "L65536_beta4096"
-# Oracle sample of the same workload: same beta, fewer sites.
-ORACLE_SAMPLE_L = 1024
+DEFAULT_WORKLOAD = "L1048576_beta1024"
+# Oracle sample of the same workload: the same beta, fewer sites, started from
+# a thermalized state (its resident set, about 1 GB, is far beyond the caches).
+ORACLE_SAMPLE_L = 8192
+# The batched form beside the single chain (the benchmark list's batched
+# configuration): chains, updates per chain, device budget of one wave.
+BATCH_CHAINS, BATCH_UPDATES, BATCH_BUDGET_GB = 4096, 100, 150.0
 KERNELS_PER_UPDATE = 11
 # DRAM bytes per vertex of each phase's kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture at L=16384, beta=4096, divided by
@@ -188,42 +196,68 @@ def over_ranks(world, elapsed, units, device):
     return float(t.item()), float(v.item())
 
 
-def oracle_sample(beta, steps, warmup, L=ORACLE_SAMPLE_L):
-    """Times the keyed CPU oracle on L sites at the workload's beta."""
+def oracle_sample(beta, steps, warmup, L=ORACLE_SAMPLE_L, state=None):
+    """Times the keyed CPU oracle on L sites at the workload's beta: `steps`
+    updates after `warmup` untimed ones, from the Neel state or from
+    state = (s0, op_ptr, op_tau, sweep)."""
     from oracle import orc
     p = orc.params(L, beta, seed=1)
-    st = orc.neel(p)
-    orc.keyed_run(p, 0, warmup, st)
+    if state is None:
+        st, sweep0 = orc.neel(p), 0
+    else:
+        st, sweep0 = orc.State(state[0], state[1], state[2]), int(state[3])
+    orc.keyed_run(p, sweep0, warmup, st)
     t0 = time.perf_counter()
-    recs = orc.keyed_run(p, warmup, steps, st)
+    recs = orc.keyed_run(p, sweep0 + warmup, steps, st)
     dt = time.perf_counter() - t0
     ve = float((recs["n_seg"] + 2 * recs["n"]).sum())
     return ve / dt, dt, recs
 
 
-def oracle_sample_all_cores(beta, steps, warmup, L=ORACLE_SAMPLE_L, procs=None):
+def oracle_sample_all_cores(beta, steps, warmup, L=ORACLE_SAMPLE_L, procs=None, state=None):
     """The oracle on every host core at once, one independent chain per core
     (the paper's independent-chain strategy)."""
     from oracle import timing
-    return timing.all_cores_sample(L, beta, steps, warmup, procs)
+    return timing.all_cores_sample(L, beta, steps, warmup, procs, state=state)
+
+
+def gpu_thermalized_sample(beta, L=ORACLE_SAMPLE_L, updates=20, seed=1):
+    """A thermalized state of the oracle's sample chain (L sites at the
+    workload's beta), made by the GPU update: (s0, op_ptr, op_tau, sweep)."""
+    from paper_1810_07485_gb300 import lcqmc
+    ch = lcqmc.Chain(L, beta, seed=seed)
+    try:
+        ch.update(updates)
+        s0, ptr, tau = ch.export_config()
+        return s0, ptr.astype(np.int64), tau, int(ch.geometry().sweep)
+    finally:
+        ch.close()
+
+
+def workload_name(L, beta):
+    return f"S=1/2 AFM Heisenberg chain, J=1, L={L}, beta={beta:g}, single chain, FP64 tau, int32 vertex ids"
 
 
 def run_reference(args, world, rank):
+    """The CPU oracle on the host cores, rank 0 only: W untimed updates from
+    the Neel state (thermalization), then K timed ones, on the sample chain."""
     L, beta, _ = WORKLOADS[args.workload]
     if rank != 0:
         return
     steps, warm = args.steps, args.warmup
-    value, dt, recs = oracle_sample(beta, steps, warm)
+    sL = min(L, ORACLE_SAMPLE_L)
+    value, dt, recs = oracle_sample(beta, steps, warm, L=sL)
+    sample = (f"keyed oracle on one core, L={sL} at beta={beta:g} (a bounded sample of the workload), "
+              f"{steps} timed updates after {warm} from the Neel state")
     line = {
         "impl": "reference", "metric": "space-time vertices+edges/s per loop update", "value": value,
         "unit": "V+E/s", "n_gpus": args.gpus, "steps": steps, "warmup": warm,
         "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"S=1/2 AFM Heisenberg chain, J=1, L={L}, beta={beta:g}, single chain; "
-                               f"CPU oracle sample L={ORACLE_SAMPLE_L} at the same beta",
-                   "L": L, "beta": beta, "sample_L": ORACLE_SAMPLE_L},
+        "config": {"workload": workload_name(L, beta) + f"; CPU oracle sample L={sL} at the same beta",
+                   "L": L, "beta": beta, "sample_L": sL},
         "cpu_baseline": {"value": value, "unit": "V+E/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
-                         "sample": f"keyed oracle, L={ORACLE_SAMPLE_L}, beta={beta:g}, {steps} updates after {warm}"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "V+E/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -278,17 +312,30 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
 
     # -- device-timed region: K updates on the chain's stream -----------------
+    # An update that outgrows its buffers stops, and lcqmc_sync grows them and
+    # runs it again after the end event: the window would miss that work.  The
+    # window is timed again (with the grown buffers) if that happened.
     clk = Clocks(local)
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    ch.update(args.steps)
-    e1.record(stream)
-    ch.sync()
-    barrier()
+    retimed = 0
+    for attempt in range(3):
+        r0 = ch.geometry().replays
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ch.update(args.steps)
+        e1.record(stream)
+        ch.sync()
+        barrier()
+        recs = ch.records()[-args.steps:]
+        if ch.geometry().replays == r0:
+            break
+        retimed += 1
+        log(f"bench: {ch.geometry().replays - r0} update(s) re-run after buffer growth inside the timed "
+            f"window; timing again")
+    else:
+        raise SystemExit("bench: buffer growth inside every timed window")
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
-    recs = ch.records()
     ve_local = float((recs["n_seg"] + 2 * recs["n"]).sum())
     ms_max, ve_tot = over_ranks(world, ms, ve_local, "cuda")
     value = ve_tot / (ms_max * 1e-3)
@@ -325,46 +372,62 @@ def run_ours(args, world, rank, local):
     tpv = TRAFFIC_PER_VERTEX_TEMPORAL if args.temporal else TRAFFIC_PER_VERTEX
     if kernels_sha1() in TRAFFIC_KERNELS_SHA1 and dom in tpv:
         traffic = tpv[dom] * float(pr["n"].mean())
+    upd_ms = sum(ph.values())
+    upd_achieved = sum(nb.values()) / (upd_ms * 1e-3) / 1e9 if upd_ms > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "algorithmic_bytes": nb[dom] / nph, "kernel": dom, "peak_kind": peak_kind,
+                "scope": "frac is the dominant phase's; whole_update covers every phase of the update",
+                "whole_update": {"achieved": upd_achieved, "frac": upd_achieved / peak,
+                                 "algorithmic_bytes": sum(nb.values()) / nph, "ms": upd_ms / nph},
                 "phase_ms_per_update": {k: ph[k] / nph for k in ph},
                 "phase_frac_of_hbm": {k: (nb[k] / (ph[k] * 1e-3) / 1e9) / peak if ph[k] > 0 else None for k in ph}}
+    mean_n = float(recs["n"].mean())
+    ch.close()
 
     cpu = None
     if rank == 0:
-        val, dt, _ = oracle_sample(beta, 4, 2)
+        sL = min(L, ORACLE_SAMPLE_L)
+        state = gpu_thermalized_sample(beta, L=sL)
+        val, dt, _ = oracle_sample(beta, 4, 0, L=sL, state=state)
         cpu = {"value": val, "unit": "V+E/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
-               "sample": f"keyed oracle, L={ORACLE_SAMPLE_L}, beta={beta:g}, 4 updates after 2 ({dt:.1f} s)"}
+               "sample": f"keyed oracle on one core, L={sL} at beta={beta:g} (the workload's beta and "
+                         f"vertex density), 4 updates from a state thermalized by 20 GPU updates "
+                         f"({dt:.1f} s)"}
         try:
-            allv, procs = oracle_sample_all_cores(beta, 4, 2)
+            allv, procs = oracle_sample_all_cores(beta, 4, 0, L=sL, state=state)
             cpu["all_cores"] = {"value": allv, "cores": procs,
-                                "sample": f"{procs} independent keyed-oracle chains, one per core, "
-                                          f"the same sample each"}
+                                "sample": f"{procs} independent keyed-oracle chains at once (seeds 1..{procs}), "
+                                          f"one per core, each the same sample"}
         except Exception as e:  # the one-core figure stands alone
             cpu["all_cores"] = {"value": None, "error": repr(e)[:200]}
-    mean_n = float(recs["n"].mean())
+    batched = None
+    if world == 1 and not args.no_batched and args.workload == DEFAULT_WORKLOAD:
+        batched = batched_record(BATCH_CHAINS, BATCH_UPDATES, BATCH_BUDGET_GB)
     line = {
         "metric": "space-time vertices+edges/s per loop update", "value": value, "unit": "V+E/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"S=1/2 AFM Heisenberg chain, J=1, L={L}, beta={beta:g}, one chain per GPU "
-                               f"(seed 1+rank), Neel start, {therm}+16+{args.warmup} untimed updates "
-                               f"(16: autotuning trials)",
+        "config": {"workload": workload_name(L, beta) + f", one chain per GPU (seed 1+rank), Neel start, "
+                               f"{therm}+16+{args.warmup} untimed updates (16: autotuning trials)",
                    "L": L, "beta": beta, "vertices_per_update": mean_n,
-                   "temporal_moment": bool(args.temporal), "tuning": tuning,
-                   "l2": "inputs larger than L2 (state and per-update graph are several GB)"},
+                   "temporal_moment": bool(args.temporal), "tuning": tuning, "retimed_windows": retimed,
+                   "l2": "inputs larger than L2 (state and per-update graph are tens of GB)"},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "V+E/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": lcqmc.RECORD_DTYPE.itemsize},
+                "d2h_bytes_per_step": lcqmc.RECORD_DTYPE.itemsize,
+                "note": "each step is lcqmc_update(h, 1) plus the readback of its record; the chain's "
+                        "world-line state lives on the device by design (the paper's nodes keep their "
+                        "world lines), so no input is copied in per step"},
         "gpu_launches": KERNELS_PER_UPDATE * args.steps,
         "clocks": clocks,
     }
+    if batched is not None:
+        line["batched"] = batched
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ch.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -378,18 +441,18 @@ def _pct(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
 
 
-def run_batched(args):
+def batched_record(n_chains, updates, budget_gb):
     """Many independent uneven chains (L log-uniform in [32, 4096], beta = L U,
-    U log-uniform in [1/4, 4]): batched launches (chains packed per phase,
-    CUDA-graph replay, memory-bounded waves in footprint order) vs the same
-    kernels launched chain by chain.  Per-chain results must be identical."""
+    U log-uniform in [1/4, 4], seeds 0..n-1): batched launches (chains packed
+    per phase, CUDA-graph replay, memory-bounded waves in footprint order) vs
+    the same kernels launched chain by chain.  Per-chain results must be
+    identical.  Completion times count from the start of each leg."""
     import torch
     from paper_1810_07485_gb300 import lcqmc, workloads
-    torch.cuda.set_device(0)
-    specs = workloads.batch_specs(args.chains, seed=0)
+    specs = workloads.batch_specs(n_chains, seed=0)
     foot = [lcqmc.footprint(s["L"], s["beta"]) for s in specs]
     order = sorted(range(len(specs)), key=lambda i: foot[i])
-    budget = args.budget_gb * 1e9
+    budget = budget_gb * 1e9
     waves, cur, used = [], [], 0.0
     for i in order:
         if cur and used + foot[i] > budget:
@@ -405,7 +468,7 @@ def run_batched(args):
     done_b, obs_b = {}, {}
     for wave in waves:
         bt = lcqmc.Batch([specs[i] for i in wave])
-        bt.update(args.updates)
+        bt.update(updates)
         bt.sync()
         tw = time.perf_counter() - t0
         for j, i in enumerate(wave):
@@ -418,7 +481,7 @@ def run_batched(args):
     for i in order:
         s = specs[i]
         ch = lcqmc.Chain(s["L"], s["beta"], seed=s["seed"])
-        ch.update(args.updates)
+        ch.update(updates)
         obs_1[i] = ch.measure()
         done_1[i] = time.perf_counter() - t0
         ch.close()
@@ -426,18 +489,28 @@ def run_batched(args):
     same = sum(1 for i in obs_b if list(obs_b[i].sum) == list(obs_1[i].sum) and
                list(obs_b[i].sumsq) == list(obs_1[i].sumsq))
     ve = float(sum(o.sum[7] for o in obs_b.values()))
-    line = {
-        "metric": "batched chains: V+E/s and per-chain completion p50/p99 vs one-by-one", "mode": "batched",
-        "value": ve / tb, "unit": "V+E/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
-        "config": {"workload": f"{args.chains} S=1/2 chains, L log-uniform [32,4096], beta=L*U, U log-uniform "
-                               f"[1/4,4], seeds 0..{args.chains - 1}, {args.updates} updates each",
-                   "waves": len(waves), "budget_gb": args.budget_gb},
+    return {
+        "workload": f"{n_chains} S=1/2 chains, L log-uniform [32,4096], beta=L*U, U log-uniform [1/4,4], "
+                    f"seeds 0..{n_chains - 1}, {updates} updates each",
+        "waves": len(waves), "budget_gb": budget_gb, "vertices_edges": ve,
         "batched": {"seconds": tb, "ve_per_s": ve / tb, "p50_s": _pct(list(done_b.values()), 50),
                     "p99_s": _pct(list(done_b.values()), 99)},
         "one_by_one": {"seconds": t1, "ve_per_s": ve / t1, "p50_s": _pct(list(done_1.values()), 50),
                        "p99_s": _pct(list(done_1.values()), 99)},
         "speedup": t1 / tb, "identical_results": f"{same}/{len(specs)}",
     }
+
+
+def run_batched(args):
+    """The batched form alone (see batched_record)."""
+    import torch
+    torch.cuda.set_device(0)
+    rec = batched_record(args.chains, args.updates, args.budget_gb)
+    line = {"metric": "batched chains: V+E/s and per-chain completion p50/p99 vs one-by-one", "mode": "batched",
+            "value": rec["batched"]["ve_per_s"], "unit": "V+E/s", "n_gpus": 1, "higher_is_better": True,
+            "data": "synthetic", "config": {"workload": rec["workload"], "waves": rec["waves"],
+                                            "budget_gb": rec["budget_gb"]}}
+    line.update({k: rec[k] for k in ("batched", "one_by_one", "speedup", "identical_results")})
     print(json.dumps(line), flush=True)
 
 
@@ -616,13 +689,15 @@ def run_sw(args, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--mode", default="single", choices=["single", "batched", "served", "sw"])
-    ap.add_argument("--chains", type=int, default=512)
-    ap.add_argument("--updates", type=int, default=20)
+    ap.add_argument("--chains", type=int, default=BATCH_CHAINS)
+    ap.add_argument("--updates", type=int, default=BATCH_UPDATES)
+    ap.add_argument("--no-batched", action="store_true",
+                    help="leave the batched form out of the single-chain line")
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=10.0)

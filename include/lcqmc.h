@@ -101,8 +101,11 @@ typedef struct {
   int32_t Q, F;
   double J, beta, w;
   uint64_t seed;
-  uint32_t sweep; /* updates completed (the Philox sweep counter) */
-  uint32_t pad;
+  uint32_t sweep;   /* updates completed (the Philox sweep counter) */
+  uint32_t replays; /* updates re-run after a buffer had to grow, since the
+                       handle was created (saturates at 2^32 - 1); a timer
+                       that brackets updates sees such re-runs outside its
+                       window only if it stops before lcqmc_sync */
 } lcqmc_geometry;
 
 /* Device memory allocator supplied by the caller (e.g. a framework's caching
@@ -195,6 +198,16 @@ int lcqmc_set_phase_timing(lcqmc_handle h, int enable);
  * Waits for enqueued updates; applies to the following ones. */
 int lcqmc_set_temporal(lcqmc_handle h, int enable);
 
+/* Debug: bound of the global union-find walks and compare-and-swap retries
+ * (Sec. 3.2) of the following updates: 1 .. 2^22 steps, 0 restores the default
+ * 2^22.  A walk that needs more steps stops the update on the device with the
+ * chain's state untouched (neither the spins, the operators nor the sweep
+ * counter change), and lcqmc_sync returns LCQMC_E_DEVICE_TIMEOUT.  With a tiny
+ * bound this exercises that failure path on a correct chain; the next update
+ * at the default bound is the one that would have run.  Waits for enqueued
+ * updates; LCQMC_E_INVAL out of range. */
+int lcqmc_set_wait_limit(lcqmc_handle h, int64_t limit);
+
 /* Block sizes of the union-find phases (Sec. 3.2 on the GPU): threads per
  * block of the tile linking and local union-find (128 or 256), warps per block
  * of the union of tile-crossing edges (1..8, one tile each) and threads per
@@ -282,21 +295,24 @@ int lcqmc_cancel(lcqmc_server_t s, uint64_t ticket);
 int lcqmc_server_destroy(lcqmc_server_t s);
 
 /* Loop labelling with no device allocation.  The paper has no counterpart:
- * this entry point exists for callers that must not call cudaMalloc (it
- * synchronizes the device, is refused on a thread that is capturing a CUDA
- * graph, and may break a memory budget fixed in advance, e.g. inside another
- * framework's pool).  Input: n graph vertices, pl[n] / pr[n] = node of the
- * fragment below each vertex on its left / right subsite (device pointers,
- * node ids in [0, n), as lcqmc_export_graph returns them).  Output: root[n]
- * (device pointer) = smallest node id of each node's loop.  The union-find
- * forest lives in a fixed device array of 2^22 int32 parents compiled into
- * the library (reserved on every GPU that loads it, until exit); n above
- * 2^22 returns LCQMC_E_TOO_LARGE.  The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress): make it before any stream
- * capture.  Work runs on cuda_stream (NULL = legacy default) and the call
- * waits for it.  All calls share the array and each call resets what it
- * uses; calls that overlap on the GPU race and must be serialized by the
- * caller.  LCQMC_E_INVAL if an id is outside [0, n). */
+ * this entry point exists for callers that must not call cudaMalloc: code
+ * that runs inside another framework's memory pool or under a device-memory
+ * budget fixed when it started, which may not grow its footprint, and code
+ * whose other streams must not be stalled by the device-wide synchronization
+ * that cudaMalloc implies.  Input: n graph vertices, pl[n] / pr[n] = node of
+ * the fragment below each vertex on its left / right subsite (device
+ * pointers, node ids in [0, n), as lcqmc_export_graph returns them).
+ * Output: root[n] (device pointer) = smallest node id of each node's loop.
+ * The union-find forest lives in a fixed device array of 2^22 int32 parents
+ * compiled into the library (reserved on every GPU that loads it, until
+ * exit); n above 2^22 returns LCQMC_E_TOO_LARGE.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) and keeps it:
+ * make that first call before any stream capture, and make no call after
+ * cudaDeviceReset on that device (the kept address would be stale).  Work
+ * runs on cuda_stream (NULL = legacy default); the call then waits for that
+ * stream, to read back a status word.  All calls share the array and each
+ * call resets what it uses; calls that overlap on the GPU race and must be
+ * serialized by the caller.  LCQMC_E_INVAL if an id is outside [0, n). */
 int lcqmc_loops_noalloc(const int32_t *pl, const int32_t *pr, int64_t n, int32_t *root,
                         void *cuda_stream);
 

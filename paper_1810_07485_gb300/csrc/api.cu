@@ -256,6 +256,10 @@ int lcqmc_set_temporal(lcqmc_handle h, int enable) {
   NEED(h);
   return h->eng.set_temporal(enable);
 }
+int lcqmc_set_wait_limit(lcqmc_handle h, int64_t limit) {
+  NEED(h);
+  return h->eng.set_wait_limit(limit);
+}
 int lcqmc_get_tuning(lcqmc_handle h, lcqmc_tuning *out) {
   NEED(h);
   if (!out) {

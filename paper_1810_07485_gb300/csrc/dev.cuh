@@ -43,6 +43,10 @@ struct DevChain {
   // geometry
   int32_t L, Q, nsub, nbond, nwin, nblk, ncell, ntile, nsiteblk, F, ring_cap;
   int32_t ins_span;  // candidate slots per insertion group (0: the default)
+  // test hooks that force the fallback paths (0: the defaults): vertices a
+  // tile may hold in shared memory (1 .. SMEM_CAP), and slots of the per-tile
+  // loop table (a power of 2, 1 .. 256)
+  int32_t local_cap, loop_slots;
   double beta, J, w;
   uint64_t seed;
   // tables
@@ -100,6 +104,7 @@ struct Scratch {
   unsigned long long *tile_state;  // per tile: insertion look-back word (flag << 62 | count)
   unsigned int *tickets;           // per Q group: next tile of the insertion launch
   int *status;
+  int uf_limit;   // bound of the global union-find walks and retries (UF_MAX_ITERS)
   int64_t *need;  // [0] vertex capacity needed by the last update
   long long *dbg; // first failed consistency check: code, then 7 details
 };
@@ -151,6 +156,12 @@ __device__ __forceinline__ int coin_from(const U4 &o, uint32_t idx) {
 __device__ __forceinline__ int coin(const DevChain &C, uint32_t tag, uint32_t idx) {
   U4 o = philox(tag << 24, idx >> 7, 0u, C.sweep, (uint32_t)C.seed, (uint32_t)(C.seed >> 32));
   return coin_from(o, idx);
+}
+
+// Vertices of a tile that its kernels keep in shared memory: a tile with more
+// takes the global-memory paths.
+__device__ __forceinline__ int local_cap(const DevChain &C) {
+  return (C.local_cap > 0 && C.local_cap < SMEM_CAP) ? C.local_cap : SMEM_CAP;
 }
 
 // ---- cell order ----------------------------------------------------------

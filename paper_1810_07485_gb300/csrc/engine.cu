@@ -284,6 +284,7 @@ int Engine::open(void *stream, const lcqmc_allocator *alloc, int ring_cap) {
   poisson_table(CELL_MEAN, T.data());
   set_full_table(T.data(), st_);
   DALLOC(s_.status, int, 1);
+  s_.uf_limit = UF_MAX_ITERS;
   DALLOC(s_.tickets, unsigned int, QMAX);
   DALLOC(s_.need, int64_t, 4);
   DALLOC(s_.dbg, long long, 8);
@@ -443,6 +444,14 @@ int Engine::layout() {
       // insertion takes the multi-group path (count, then draw again to write).
       d.ins_span = 0;
       if (const char *e = std::getenv("LCQMC_INSERT_GROUP_SLOTS")) d.ins_span = std::atoi(e);
+      // Test hooks: fewer vertices per tile in shared memory (tiles above it
+      // take the global-memory paths of linking, union-find, compression and
+      // loop sums), and a smaller per-tile loop table (loops that do not fit
+      // spill to their global records).
+      d.local_cap = 0;
+      if (const char *e = std::getenv("LCQMC_LOCAL_CAP")) d.local_cap = std::atoi(e);
+      d.loop_slots = 0;
+      if (const char *e = std::getenv("LCQMC_LOOP_SLOTS")) d.loop_slots = std::atoi(e);
       cell_off += g.ncell + 1;
       bpar_off += (g.nblk + 1) * g.nbond;
       sub_off += g.nsub;
@@ -747,6 +756,7 @@ int Engine::sync() {
     CK(cudaMemsetAsync(s_.status, 0, sizeof(int), st_));
     pending_ = 0;
     if (remaining > 0) {
+      replays_ += remaining;
       rc = update(remaining);
       if (rc) return rc;
     }
@@ -823,7 +833,7 @@ int Engine::geometry(int64_t c, lcqmc_geometry *out) {
   out->w = d.w;
   out->seed = d.seed;
   out->sweep = d.sweep;
-  out->pad = 0;
+  out->replays = (uint32_t)std::min<int64_t>(replays_, 0xffffffffll);
   return LCQMC_OK;
 }
 
@@ -970,6 +980,22 @@ int Engine::set_phase_timing(int enable) {
   if (rc) return rc;
   timing_ = enable != 0;
   for (double &x : phase_ms_) x = 0.0;
+  return LCQMC_OK;
+}
+
+int Engine::set_wait_limit(int64_t limit) {
+  if (limit < 0 || limit > UF_MAX_ITERS) {
+    set_error("wait limit out of range: 1 .. 2^22, or 0 for the default");
+    return LCQMC_E_INVAL;
+  }
+  int rc = sync();
+  if (rc) return rc;
+  s_.uf_limit = limit ? (int)limit : UF_MAX_ITERS;
+  L_.s = s_;
+  if (gexec_) {  // the captured launches carry the scratch descriptor
+    cudaGraphExecDestroy(gexec_);
+    gexec_ = nullptr;
+  }
   return LCQMC_OK;
 }
 

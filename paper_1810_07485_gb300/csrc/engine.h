@@ -73,6 +73,7 @@ class Engine {
   int export_cells(int64_t chain, int32_t *vptr, int64_t cap);
   int set_phase_timing(int enable);
   int set_temporal(int enable);  // temporal moment chi(pi, 2 pi/beta) for every chain
+  int set_wait_limit(int64_t limit);  // bound of the global union-find walks (0: default)
   // block sizes of the union-find phases: read, set (checked), or tuned by
   // timing each candidate over n updates of the batch (ordinary updates)
   void get_tuning(lcqmc_tuning *out) const;
@@ -122,6 +123,7 @@ class Engine {
   double phase_ms_[LCQMC_NPHASE] = {0};
   int64_t pending_ = 0;
   uint32_t pending_sweep0_ = 0;
+  int64_t replays_ = 0;  // updates re-run after capacity growth
 };
 
 }  // namespace lcq

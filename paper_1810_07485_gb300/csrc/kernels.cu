@@ -926,7 +926,7 @@ __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
   }
   __syncthreads();
   const int a = cvp[0], e = cvp[ncl], nv = e - a;
-  const bool local = nv <= SMEM_CAP;
+  const bool local = nv <= local_cap(C);
   if (local)
     for (int i = threadIdx.x; i < nv; i += blockDim.x) lp[i] = i;
   __syncthreads();
@@ -1034,11 +1034,11 @@ __global__ void __launch_bounds__(TPB_X) k_link_x(const DevChain *__restrict__ c
   const int c0 = t.y * TILE, c1 = min(C.ncell, c0 + TILE);
   const int32_t *vp = s.vptr + C.cell_off;
   const int a = vp[c0], e = vp[c1];
-  const bool local = e - a <= SMEM_CAP;
+  const bool local = e - a <= local_cap(C);
   const int64_t vb = C.vtx_base;
   int32_t *par = s.parent + vb;
   if (!local) {
-    for (int w = a + lane; w < e; w += 32) uf_union(par, s.pl[vb + w], s.pr[vb + w], s.status);
+    for (int w = a + lane; w < e; w += 32) uf_union(par, s.pl[vb + w], s.pr[vb + w], s.status, s.uf_limit);
     return;
   }
   const int64_t wfirst = (vb + a) >> 5, wlast = (vb + e - 1) >> 5;
@@ -1050,7 +1050,7 @@ __global__ void __launch_bounds__(TPB_X) k_link_x(const DevChain *__restrict__ c
     while (bits) {
       const int w = (int)v0 + __ffs(bits) - 1;
       bits &= bits - 1;
-      uf_union(par, s.pl[vb + w], s.pr[vb + w], s.status);
+      uf_union(par, s.pl[vb + w], s.pr[vb + w], s.status, s.uf_limit);
     }
   }
 }
@@ -1071,7 +1071,7 @@ __global__ void __launch_bounds__(TILE) k_compress(const DevChain *__restrict__ 
   const int a = vp[c0], e = vp[c1];
   const int64_t vb = C.vtx_base, wb = vb >> 5;
   int32_t *par = s.parent + vb;
-  const bool oversized = (e - a) > SMEM_CAP;
+  const bool oversized = (e - a) > local_cap(C);
   const int g0 = a >> 7;
   const int ng = (e > a) ? ((e - 1) >> 7) - g0 + 1 : 0;
   const uint32_t k0 = (uint32_t)C.seed, k1 = (uint32_t)(C.seed >> 32);
@@ -1091,7 +1091,7 @@ __global__ void __launch_bounds__(TILE) k_compress(const DevChain *__restrict__ 
     }
     int r;
     if (oversized) {
-      r = uf_root(par, v, s.status);
+      r = uf_root(par, v, s.status, s.uf_limit);
     } else {
       // parents are never larger than their children: the walk leaves the
       // tile only downwards (below a), and then finishes in global memory
@@ -1101,7 +1101,7 @@ __global__ void __launch_bounds__(TILE) k_compress(const DevChain *__restrict__ 
         r = p;
         p = spar[p - a];
       }
-      if (p != r) r = uf_root(par, p, s.status);
+      if (p != r) r = uf_root(par, p, s.status, s.uf_limit);
     }
     if (r != v) par[v] = r;
     if (r == v) {
@@ -1175,11 +1175,12 @@ __device__ __forceinline__ void acc_add(const Scratch &s, int64_t v, const long 
 }
 
 // NS: how many of the sums are carried (3 without the temporal moment).
+// mask = slots in use - 1 (LOOP_SLOTS - 1 unless a test shrinks the table).
 template <int NS>
 __device__ __forceinline__ void loop_add(int *keys, unsigned *vals, int key, const LoopSums &x,
-                                         const Scratch &s, int64_t vb) {
-  unsigned h = ((unsigned)key * 2654435761u) >> 24;  // top 8 bits: LOOP_SLOTS = 256
-  for (int probe = 0; probe < LOOP_SLOTS; ++probe) {
+                                         const Scratch &s, int64_t vb, unsigned mask) {
+  unsigned h = (((unsigned)key * 2654435761u) >> 24) & mask;  // top 8 bits: LOOP_SLOTS = 256
+  for (unsigned probe = 0; probe <= mask; ++probe) {
     int k = keys[h];
     if (k == -1) {
       k = atomicCAS(keys + h, -1, key);
@@ -1190,7 +1191,7 @@ __device__ __forceinline__ void loop_add(int *keys, unsigned *vals, int key, con
       for (int i = 0; i < NS; ++i) sadd64(vals + 2 * (LOOP_SUMS * h + i), x.v[i]);
       return;
     }
-    h = (h + 1) & (LOOP_SLOTS - 1);
+    h = (h + 1) & mask;
   }
   acc_add<NS>(s, vb + key, x.v);
   set_bit(s.openroot, vb >> 5, key);
@@ -1256,7 +1257,11 @@ __global__ void __launch_bounds__(TPB_EST, T ? 3 : 4) k_est(const DevChain *__re
   // Their phase factors too (temporal moment, w1 = 2 pi / beta).
   const uint64_t phR = C.phR;
   const int phS = C.phS;
-  const int nq = min(e - a, SMEM_CAP);
+  const int nq = min(e - a, local_cap(C));
+  const unsigned slot_mask =
+      (C.loop_slots > 0 && C.loop_slots <= LOOP_SLOTS && !(C.loop_slots & (C.loop_slots - 1)))
+          ? (unsigned)C.loop_slots - 1u
+          : (unsigned)LOOP_SLOTS - 1u;
   for (int i = threadIdx.x; i < nq; i += blockDim.x) {
     const long long q = q_time(vt[a + i], F);
     qv[i] = q;
@@ -1307,7 +1312,7 @@ __global__ void __launch_bounds__(TPB_EST, T ? 3 : 4) k_est(const DevChain *__re
         // two fragments are the two below w: the loop's sums are complete here.
         loop_squares<T>(x.v, w2, f2, z2);
       } else {
-        loop_add<T ? LOOP_SUMS : 3>(lkeys, lvals, rb, x, s, vb);
+        loop_add<T ? LOOP_SUMS : 3>(lkeys, lvals, rb, x, s, vb, slot_mask);
       }
     }
     __syncwarp();

@@ -6,13 +6,13 @@
 // scratch is the parent forest, kept in a fixed array compiled into this
 // library instead of being allocated per call.
 //
-// Why: some callers must not call cudaMalloc.  cudaMalloc synchronizes the
-// device, which stalls every other stream of an application that overlaps
-// work; it is not allowed on a thread that is capturing a CUDA graph; and
-// callers that live inside another framework's memory pool, or on a device
-// whose footprint is budgeted in advance, may not grow their allocation at
-// all.  Such callers pass inputs and outputs they own and get a result with
-// no allocation on the library's side.
+// Why: some callers must not call cudaMalloc.  Callers that live inside
+// another framework's memory pool, or on a device whose footprint was
+// budgeted when they started, may not grow their allocation at all; and
+// cudaMalloc synchronizes the device, which stalls every other stream of an
+// application that overlaps work.  Such callers pass inputs and outputs they
+// own and get a result with no allocation on the library's side.  The call
+// does wait for its own stream, to read back the status word.
 //
 // The fixed array holds NOALLOC_MAX_NODES int32 parents (16 MiB plus one status
 // word).  Every process that loads the library reserves it on every GPU it
@@ -114,6 +114,12 @@ extern "C" int lcqmc_loops_noalloc(const int32_t *pl, const int32_t *pr, int64_t
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
+    // Forget the device address: a later call looks it up again (a context
+    // that has failed may be replaced by a new one with a new address).
+    {
+      std::lock_guard<std::mutex> lk(g_na_mu);
+      g_na_ptr[dev] = nullptr;
+    }
     set_error(std::string("lcqmc_loops_noalloc: ") + cudaGetErrorString(e));
     return LCQMC_E_CUDA;
   }

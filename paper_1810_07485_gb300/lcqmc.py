@@ -86,7 +86,7 @@ class Geometry(ctypes.Structure):
                 ("nwin", ctypes.c_int64), ("ncell", ctypes.c_int64), ("Q", ctypes.c_int32),
                 ("F", ctypes.c_int32), ("J", ctypes.c_double), ("beta", ctypes.c_double),
                 ("w", ctypes.c_double), ("seed", ctypes.c_uint64), ("sweep", ctypes.c_uint32),
-                ("pad", ctypes.c_uint32)]
+                ("replays", ctypes.c_uint32)]
 
 
 class ChainSpec(ctypes.Structure):
@@ -137,6 +137,7 @@ def lib():
         "lcqmc_restore": [vp, vp, ctypes.c_size_t],
         "lcqmc_set_phase_timing": [vp, i32],
         "lcqmc_set_temporal": [vp, i32],
+        "lcqmc_set_wait_limit": [vp, i64],
         "lcqmc_get_tuning": [vp, P(Tuning)],
         "lcqmc_set_tuning": [vp, P(Tuning)],
         "lcqmc_autotune": [vp, i64, P(Tuning)],
@@ -311,6 +312,9 @@ class Chain:
 
     def set_phase_timing(self, on=True):
         _check(lib().lcqmc_set_phase_timing(self.h, 1 if on else 0))
+
+    def set_wait_limit(self, limit=0):
+        _check(lib().lcqmc_set_wait_limit(self.h, int(limit)))
 
     def set_temporal(self, on=True):
         """Temporal moment chi(pi, 2 pi / beta) on or off (off after create)."""

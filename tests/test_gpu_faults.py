@@ -7,6 +7,11 @@
 * The opt-in forest check (LCQMC_CHECK_FOREST=1) verifies after every
   compression that each node's word is its root; on a correct update it
   stays silent and changes nothing.
+* A bounded device wait that runs out: the union-find walks of a correct
+  chain get a bound of one step (lcqmc_set_wait_limit), so the update stops
+  on the device.  The call reports LCQMC_E_DEVICE_TIMEOUT, the chain's state
+  is untouched, and the next update at the default bound is the oracle's.
+  No kernel faults or hangs: every wait returns once its bound is reached.
 """
 import ctypes
 
@@ -102,3 +107,47 @@ def test_forest_check_silent_on_correct_updates(monkeypatch):
     for f in ("n", "n_clusters", "sw2_lo", "sw2_hi", "sf2_lo", "sf2_hi"):
         assert np.array_equal(rg[f].astype(np.int64), ro[f].astype(np.int64)), f
     ch.close()
+
+
+def test_device_timeout_leaves_state_and_recovers(monkeypatch):
+    from oracle import orc
+    from paper_1810_07485_gb300 import lcqmc as lc
+    # every tile keeps at most 64 vertices in shared memory, so that its edges
+    # are united in the global forest, whose walks the bound applies to
+    monkeypatch.setenv("LCQMC_LOCAL_CAP", "64")
+    L, beta, seed = 1024, 40.0, 9
+    p = orc.params(L, beta, seed=seed)
+    st = orc.neel(p)
+    ch = lc.Chain(L, beta, seed=seed)
+    try:
+        for t in range(3):
+            st, ro, _ = orc.keyed_update(p, t, st)
+            ch.update(1)
+            assert int(ch.records()[0]["n"]) == int(ro["n"])
+        s0, ptr, tau = ch.export_config()
+        assert ch.geometry().sweep == 3
+        ch.set_wait_limit(1)
+        ch.update(1)
+        with pytest.raises(lc.LcqmcError) as e:
+            ch.sync()
+        assert e.value.code == -5  # LCQMC_E_DEVICE_TIMEOUT
+        s0b, ptrb, taub = ch.export_config()
+        assert np.array_equal(s0, s0b) and np.array_equal(ptr, ptrb) and np.array_equal(tau, taub)
+        assert ch.geometry().sweep == 3
+        assert len(ch.records()) == 0
+        with pytest.raises(lc.LcqmcError):
+            ch.set_wait_limit(1 << 23)  # above the maximum bound
+        ch.set_wait_limit(0)
+        new, ro, go = orc.keyed_update(p, 3, st, graph=True)
+        ch.update(1)
+        rg = ch.records()
+        assert len(rg) == 1
+        for f in ("n", "n_off_old", "n_off_new", "n_clusters", "sw2_lo", "sw2_hi", "sf2_lo", "sf2_hi"):
+            assert int(rg[0][f]) == int(ro[f]), f
+        g = ch.export_graph()
+        assert np.array_equal(g["root"].astype(np.int64), go["root"])
+        s0c, ptrc, tauc = ch.export_config()
+        assert np.array_equal(s0c, new.s0) and np.array_equal(ptrc.astype(np.int64), new.op_ptr)
+        assert np.array_equal(tauc, new.op_tau)
+    finally:
+        ch.close()

@@ -214,8 +214,10 @@ def test_records_and_measure_consistent():
     assert o.gap == pytest.approx(1 / xt, rel=1e-10)
 
 
-@pytest.mark.parametrize("L,beta,Q", [(8, 4.0, 1), (12, 1.0, 1), (4, 1.0, 2), (4, 0.7, 3), (2, 0.8, 4),
-                                      (4, 0.5, 4)])
+# beta = 16 at L = 8 and 12 is the low-temperature point of the L = 64,
+# beta = 16 accuracy configuration, at sizes exact diagonalization reaches.
+@pytest.mark.parametrize("L,beta,Q", [(8, 4.0, 1), (12, 1.0, 1), (8, 16.0, 1), (12, 16.0, 1), (12, 4.0, 1),
+                                      (4, 1.0, 2), (4, 0.7, 3), (2, 0.8, 4), (4, 0.5, 4)])
 def test_gpu_vs_ed(L, beta, Q):
     # Estimators within 3 standard errors of exact diagonalization.
     lc = gpu()
@@ -343,3 +345,48 @@ def test_batch_autotune_identical():
         assert np.array_equal(b1.records(i), b2.records(i))
     b1.close()
     b2.close()
+
+
+def _tile_sizes(ch):
+    vp = ch.export_cells().astype(np.int64)
+    ends = np.minimum(np.arange(0, len(vp) - 1 + 128, 128), len(vp) - 1)
+    return np.diff(vp[np.unique(ends)])
+
+
+@pytest.mark.parametrize("cap,slots", [(64, 0), (900, 0), (0, 4), (64, 1)])
+@pytest.mark.parametrize("L,beta,Q", [(250, 70.0, 1), (1024, 40.0, 1), (40, 40.0, 2), (34, 10.0, 3)])
+def test_update_parity_global_fallbacks(monkeypatch, cap, slots, L, beta, Q):
+    # Tiles with more vertices than a tile keeps in shared memory (cap) take
+    # the global-memory paths: every edge united in the global forest,
+    # compression walks in global memory, ticks computed on the fly, every
+    # root treated as leaving the tile.  A per-tile loop table of `slots`
+    # entries spills the loops that do not fit to their global records.  The
+    # results must not change.
+    if cap:
+        monkeypatch.setenv("LCQMC_LOCAL_CAP", str(cap))
+    if slots:
+        monkeypatch.setenv("LCQMC_LOOP_SLOTS", str(slots))
+    lc = gpu()
+    p = orc.params(L, beta, Q=Q, seed=300 + L + cap + slots)
+    st = orc.neel(p)
+    ch = lc.Chain(L, beta, S=Q / 2, seed=300 + L + cap + slots)
+    ch.set_temporal(True)
+    try:
+        for t in range(6):
+            new, ro, go = orc.keyed_update(p, t, st, graph=True)
+            ch.update(1)
+            ctx = f"L={L} beta={beta} Q={Q} cap={cap} slots={slots} sweep={t}"
+            assert_records_equal(ch.records()[0], ro, ctx)
+            assert_graph_equal(ch.export_graph(), go, ctx)
+            assert_state_equal(gpu_state(ch), new, ctx)
+            sizes = _tile_sizes(ch)
+            if cap:
+                # the fallback is reached: some tile holds more vertices than the cap
+                assert sizes.max() > cap, (ctx, sizes.max())
+            if slots:
+                # more distinct multi-node loops in a tile than the table holds
+                r, pl, pr = go["root"], go["pl"], go["pr"]
+                assert len(np.unique(r[pl[:sizes[0]] != pr[:sizes[0]]])) > slots, ctx
+            st = new
+    finally:
+        ch.close()

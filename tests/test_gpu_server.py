@@ -3,11 +3,14 @@
 A mix of requests (S=1/2 and S=1, different sizes, temperatures and update
 counts) submitted together, with fewer slots than requests so that chains
 join and leave between ticks, must give every request exactly the result of
-the same chain run alone."""
+the same chain run alone, and the result of the CPU oracle's chain with the
+same parameters and seed."""
 import time
 
 import numpy as np
 import pytest
+
+from oracle import orc
 
 pytestmark = pytest.mark.gpu
 
@@ -49,6 +52,21 @@ def test_mix_equals_alone():
         assert list(r.obs.sumsq) == list(o.sumsq), m
         assert r.vertices_edges == int(o.sum[7])
         ch.close()
+        # the oracle's chain: the same records, summed in update order
+        p = orc.params(m["L"], m["beta"], Q=int(2 * m["S"]), seed=m["seed"])
+        recs = orc.keyed_run(p, 0, m["n"], orc.neel(p))
+        fields = ("energy", "chi_s", "chi_q", "n", "n_off_new", "n_seg", "n_clusters", None)
+        for k, f in enumerate(fields):
+            v = [float(x) for x in (recs["n_seg"] + 2 * recs["n"] if f is None else recs[f])]
+            s1 = s2 = 0.0
+            for x in v:
+                s1 += x
+                s2 += x * x
+            if f in ("energy", "chi_s", "chi_q"):  # fp64 from exact sums; 1e-15 per record
+                assert r.obs.sum[k] == pytest.approx(s1, rel=1e-13, abs=1e-300), (m, f)
+                assert r.obs.sumsq[k] == pytest.approx(s2, rel=1e-13, abs=1e-300), (m, f)
+            else:  # integers, exact in fp64
+                assert r.obs.sum[k] == s1 and r.obs.sumsq[k] == s2, (m, f)
 
 
 def test_admission_rejects_oversized_and_cancels():

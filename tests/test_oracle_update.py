@@ -218,7 +218,8 @@ def test_curie_limit_empty(orc):
 
 @pytest.mark.parametrize("form", ["keyed", "serial"])
 @pytest.mark.parametrize("L,beta,Q,seed", [(2, 1.0, 1, 21), (4, 2.0, 1, 22), (8, 4.0, 1, 23),
-                                           (12, 1.0, 1, 24), (4, 1.0, 2, 25), (2, 2.0, 2, 26),
+                                           (12, 1.0, 1, 24), (8, 16.0, 1, 31), (12, 16.0, 1, 32),
+                                           (4, 1.0, 2, 25), (2, 2.0, 2, 26),
                                            (2, 1.0, 3, 27), (4, 0.7, 3, 28), (2, 0.8, 4, 29),
                                            (4, 0.5, 4, 30)])
 def test_vs_ed(orc, form, L, beta, Q, seed):
