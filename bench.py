@@ -204,8 +204,8 @@ def oracle_sample(beta, steps, warmup, L=ORACLE_SAMPLE_L, state=None):
     p = orc.params(L, beta, seed=1)
     if state is None:
         st, sweep0 = orc.neel(p), 0
-    else:
-        st, sweep0 = orc.State(state[0], state[1], state[2]), int(state[3])
+    else:  # a copy: the oracle updates its state in place
+        st, sweep0 = orc.State(state[0], state[1], state[2]).copy(), int(state[3])
     orc.keyed_run(p, sweep0, warmup, st)
     t0 = time.perf_counter()
     recs = orc.keyed_run(p, sweep0 + warmup, steps, st)

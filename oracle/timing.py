@@ -22,7 +22,7 @@ def chain_sample(job):
     if state is None:
         st, sweep0 = orc.neel(p), 0
     else:
-        st, sweep0 = orc.State(state[0], state[1], state[2]), int(state[3])
+        st, sweep0 = orc.State(state[0], state[1], state[2]).copy(), int(state[3])
     orc.keyed_run(p, sweep0, warmup, st)
     t0 = time.perf_counter()
     recs = orc.keyed_run(p, sweep0 + warmup, steps, st)

@@ -200,6 +200,48 @@ __device__ __forceinline__ int inc_bond(int u, int k, int L) {
   return im * Q * Q + (k - Q) * Q + a;
 }
 
+// ---- bulk copies global -> shared (TMA, no tensor map) ---------------------------
+// One thread arms a shared-memory mbarrier with the byte count and starts the
+// copy; every thread then waits on the barrier's phase.  Both addresses must
+// be 16-byte aligned and the size a multiple of 16.  The wait is bounded: a
+// copy that has not landed after STAGE_MAX_POLLS polls sets ST_TIMEOUT.
+constexpr int STAGE_MAX_POLLS = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Arms the barrier for `bytes` and starts one copy of `bytes` (thread-local call).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Waits for phase `parity` of the barrier to complete; false if it did not
+// within the bound.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (int i = 0; i < STAGE_MAX_POLLS; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 // ---- bits ------------------------------------------------------------------
 __device__ __forceinline__ int get_bit(const uint32_t *bits, int64_t word0, int32_t i) {
   return (int)((__ldcg(bits + word0 + (i >> 5)) >> (i & 31)) & 1u);

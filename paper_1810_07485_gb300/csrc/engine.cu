@@ -321,7 +321,7 @@ int Engine::create_state(const ChainSpec &spec, ChainState *out) {
   for (int k = 0; k < 2; ++k) {
     DALLOC(b.s0[k], uint8_t, d.nsub);
     DALLOC(b.op_ptr[k], int32_t, (int64_t)d.ncell + 1);
-    DALLOC(b.op_tau[k], double, d.op_cap);
+    DALLOC(b.op_tau[k], double, d.op_cap + 2);  // +2: bulk copies end on a 16-byte bound
     d.s0[k] = b.s0[k];
     d.op_ptr[k] = b.op_ptr[k];
     d.op_tau[k] = b.op_tau[k];
@@ -668,7 +668,7 @@ int Engine::grow_ops(int64_t c, int64_t need) {
   (void)nold;
   for (int k = 0; k < 2; ++k) {
     double *p;
-    DALLOC(p, double, cap);
+    DALLOC(p, double, cap + 2);  // +2: bulk copies end on a 16-byte bound
     if (k == d.cur) {
       int32_t n_off = 0;
       CK(cudaMemcpyAsync(&n_off, b.op_ptr[k] + d.ncell, 4, cudaMemcpyDeviceToHost, st_));

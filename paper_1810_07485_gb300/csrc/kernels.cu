@@ -274,8 +274,28 @@ constexpr int INS_MAXG = (TILE * (KMAX - 1)) / INS_MIN_SPAN + 2;
 constexpr int INS_OPCAP = 2048;  // old operators of a group mapped to their cell
 constexpr unsigned long long KEY_DROP = 1ull << 63;
 
+// Old operator times a tile stages in shared memory: its own cells' and those
+// of the cells up to 8 Q^2 cells away (the neighbour bonds of the same
+// windows), when they fit.
+template <int Q>
+struct InsStage {
+  static constexpr int N = Q == 1 ? 1024 : (Q == 2 ? 512 : 2048);
+};
+
+// Where an old operator's time is read: from the staged copy if its index is
+// in [lo, hi), else from global memory.
+struct OpView {
+  const long long *g;   // op_tau of the chain
+  const long long *sv;  // staged copy, indexed like g (valid in [lo, hi))
+  int lo, hi;
+  __device__ __forceinline__ const long long *range(int a, int b) const {
+    return (a >= lo && b <= hi) ? sv : g;
+  }
+};
+
 template <int Q>
 struct InsSmem {
+  long long sop[InsStage<Q>::N];    // staged old operator times (16-byte aligned: first member)
   unsigned long long key[INS_CAP];  // u53, with bit 63 set if the candidate is not kept
   long long tau[INS_CAP];           // time bits; LLONG_MAX if not kept
   short klist[INS_CAP];             // kept candidates' slots (any order)
@@ -290,6 +310,8 @@ struct InsSmem {
   int gfirst[INS_MAXG + 1];
   int G, nkept;
   int sm[33];
+  int slo, shi;
+  uint64_t bar;
   int64_t excl;
   int64_t gt;
 };
@@ -314,20 +336,21 @@ __device__ __forceinline__ int ops_before(const long long *__restrict__ tq, int 
 // multiply-add), and whether it is kept: the bond's spins antiparallel at tau
 // (parity at the window start flipped by the neighbour operators before tau).
 template <int Q>
-__device__ __forceinline__ bool ins_decide(const long long *otau, const NbOps<Q> &X, int b, int par0,
+__device__ __forceinline__ bool ins_decide(const OpView &V, const NbOps<Q> &X, int b, int par0,
                                            uint64_t u53, double t0, double d, long long teb,
                                            long long &tau) {
   tau = __double_as_longlong(__fma_rn(d, __longlong_as_double((long long)unit_bits(u53)), t0));
   if (!(tau < teb)) return false;
   int p = par0;
 #pragma unroll
-  for (int k = 0; k < NbOps<Q>::N; ++k) p ^= ops_before(otau, X.o0[k], X.o1[k], tau, X.bond[k], b);
+  for (int k = 0; k < NbOps<Q>::N; ++k)
+    p ^= ops_before(V.range(X.o0[k], X.o1[k]), X.o0[k], X.o1[k], tau, X.bond[k], b);
   return p & 1;
 }
 
 // Draw and decide the candidates of the cells of group g.
 template <int Q>
-__device__ void ins_draw(const DevChain &C, InsSmem<Q> &S, const long long *otau, int g, bool count) {
+__device__ void ins_draw(const DevChain &C, InsSmem<Q> &S, const OpView &V, int g, bool count) {
   const int c0 = S.gfirst[g], c1 = S.gfirst[g + 1];
   const int kb = S.kpre[c0], ub = S.upre[c0], nu = S.upre[c1] - ub;
   {
@@ -360,7 +383,7 @@ __device__ void ins_draw(const DevChain &C, InsSmem<Q> &S, const long long *otau
         const uint64_t u53 = (h ? ((uint64_t)o.z | ((uint64_t)o.w << 32))
                                 : ((uint64_t)o.x | ((uint64_t)o.y << 32))) >> 11;
         long long tau;
-        const bool keep = ins_decide<Q>(otau, X, b, par0, u53, t0, d, teb, tau);
+        const bool keep = ins_decide<Q>(V, X, b, par0, u53, t0, d, teb, tau);
         const int slot = ks + k;
         S.key[slot] = keep ? u53 : (u53 | KEY_DROP);
         S.tau[slot] = keep ? tau : LLONG_MAX;
@@ -392,7 +415,7 @@ __device__ void ins_draw(const DevChain &C, InsSmem<Q> &S, const long long *otau
 // Place and write the vertices of the cells of group g (kept candidates, then
 // old operators); vertex ids are chain-local, base = the tile's first id.
 template <int Q>
-__device__ void ins_write(const DevChain &C, InsSmem<Q> &S, const long long *otau, int g,
+__device__ void ins_write(const DevChain &C, InsSmem<Q> &S, const OpView &V, int g,
                           int64_t base, const Scratch &s) {
   const int c0 = S.gfirst[g], c1 = S.gfirst[g + 1];
   const int kb = S.kpre[c0];
@@ -419,6 +442,7 @@ __device__ void ins_write(const DevChain &C, InsSmem<Q> &S, const long long *ota
     // old operators at or before tau (ascending times)
     int lo = S.q[c], hi = S.q[c + 1];
     const int q0 = lo;
+    const long long *otau = V.range(lo, hi);
     while (lo < hi) {
       const int mid = lo + ((hi - lo) >> 1);  // no overflow near 2^31
       if (otau[mid] <= tau)
@@ -455,7 +479,7 @@ __device__ void ins_write(const DevChain &C, InsSmem<Q> &S, const long long *ota
       }
       c = lo;
     }
-    const long long ot = otau[q];
+    const long long ot = (q >= V.lo && q < V.hi) ? V.sv[q] : V.g[q];
     const int ks = S.kpre[c] - kb, K = S.K[c];
     int r = q - S.q[c];
     for (int x = 0; x < K; ++x) r += S.tau[ks + x] < ot;
@@ -480,7 +504,7 @@ __global__ void __launch_bounds__(TILE) k_insert(DevChain *__restrict__ ch,
                                                  const int2 *__restrict__ tab, int64_t blk0,
                                                  int group, Scratch s) {
   if constexpr (Q <= 2) {
-    __shared__ InsSmem<Q> S;
+    __shared__ __align__(16) InsSmem<Q> S;
     insert_tile<Q>(S, ch, tab, blk0, group, s);
   } else {
     extern __shared__ __align__(16) unsigned char ins_dyn[];
@@ -506,6 +530,23 @@ __device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict_
   const long long *otau = (const long long *)C.op_tau[cur];
   const uint8_t *s0 = C.s0[cur];
   int32_t *vp = s.vptr + C.cell_off;
+  if (threadIdx.x == 0) {
+    // Stage the old operator times around the tile with one bulk copy
+    // (16-byte bounds: op_tau has room for one time past its capacity),
+    // overlapped with the cells' set-up.
+    const int R = 8 * Q * Q;
+    const int ce = min(C.ncell, t.y * TILE + TILE);
+    int lo = op[max(0, t.y * TILE - R)] & ~1, hi = (op[min(C.ncell, ce + R)] + 1) & ~1;
+    if (hi - lo > InsStage<Q>::N) {
+      lo = op[min(C.ncell, t.y * TILE)] & ~1;
+      hi = (op[ce] + 1) & ~1;
+      if (hi - lo > InsStage<Q>::N) hi = lo;
+    }
+    S.slo = lo;
+    S.shi = hi;
+    mbar_init(&S.bar);
+    if (hi > lo) bulk_g2s(S.sop, otau + lo, (uint32_t)(hi - lo) * 8u, &S.bar);
+  }
   if (threadIdx.x < KMAX) {
     S.T[0][threadIdx.x] = c_T_full[threadIdx.x];
     S.T[1][threadIdx.x] = C.T_last[threadIdx.x];
@@ -587,9 +628,17 @@ __device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict_
   }
   __syncthreads();
   const int G = S.G;
+  if (S.shi > S.slo) {
+    const bool ok = mbar_wait(&S.bar, 0);
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) atomicOr(s.status, ST_TIMEOUT);
+      return;
+    }
+  }
+  const OpView V{otau, S.sop - S.slo, S.slo, S.shi};
 
   // -- draw, decide and count ------------------------------------------------
-  for (int g = 0; g < G; ++g) ins_draw<Q>(C, S, otau, g, true);
+  for (int g = 0; g < G; ++g) ins_draw<Q>(C, S, V, g, true);
   const int cnt = valid ? (q1 - q0) + S.nk[c] : 0;
   int ctot;
   S.cex[c] = block_excl_scan<int>(cnt, S.sm, ctot);
@@ -626,8 +675,8 @@ __device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict_
 
   // -- write -----------------------------------------------------------------
   for (int g = 0; g < G; ++g) {
-    if (G > 1) ins_draw<Q>(C, S, otau, g, false);
-    ins_write<Q>(C, S, otau, g, base, s);
+    if (G > 1) ins_draw<Q>(C, S, V, g, false);
+    ins_write<Q>(C, S, V, g, base, s);
     __syncthreads();
   }
 }
@@ -882,6 +931,26 @@ __device__ __forceinline__ int time_lower_bound(const long long *vt, int lo, int
   return lo;
 }
 
+// Vertex times a linking block stages in shared memory (24 KB for Q <= 2,
+// 8 KB beside the larger cell tables of Q = 3, 4): the tile's own and those
+// of the cells up to 8 Q^2 cells away, which hold the neighbour bonds'
+// vertices of the same windows.
+template <int Q>
+__host__ __device__ constexpr int link_stage() {
+  return Q <= 2 ? 3072 : 1024;
+}
+
+__device__ __forceinline__ int smem_lower_bound(const long long *sv, int lo, int hi, long long thr) {
+  while (lo < hi) {
+    const int mid = lo + ((hi - lo) >> 1);
+    if (sv[mid] < thr)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
 // Linking, then the union of the two fragments below every vertex.  Edges
 // with both nodes in the tile are united in shared memory, and the tile's
 // forest is then stored flat: every node points at its tile component's
@@ -890,17 +959,39 @@ __device__ __forceinline__ int time_lower_bound(const long long *vt, int lo, int
 // after every tile has stored its forest (a tile too large for shared memory
 // leaves all of its edges to k_link_x, with every node its own root).
 template <int Q>
-__global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
+__global__ void __launch_bounds__(TPB, 6) k_link(const DevChain *__restrict__ ch,
                                               const int2 *__restrict__ tab, int64_t blk0,
                                               Scratch s) {
   __shared__ LinkCell<Q> lc[TILE];
   __shared__ int cvp[TILE + 1];
   __shared__ int lp[SMEM_CAP];
+  constexpr int LINK_STAGE = link_stage<Q>();
+  __shared__ __align__(16) long long svt[LINK_STAGE];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int stage[2];
   if (halted(s)) return;
   const int2 t = tab[blk0 + blockIdx.x];
   const DevChain &C = ch[t.x];
   const int c0 = t.y * TILE, c1 = min(C.ncell, c0 + TILE), ncl = c1 - c0;
   const int32_t *vp = s.vptr + C.cell_off;
+  const int64_t vb = C.vtx_base, wb = vb >> 5;
+  const long long *__restrict__ vt = (const long long *)s.vtau + vb;
+  if (threadIdx.x == 0) {
+    // Stage the vertex times of the cells around the tile with one bulk copy
+    // (16-byte bounds: vb is a multiple of 128 vertices and the chain's
+    // region ends on an even vertex), started before the cells' set-up.
+    const int R = 8 * Q * Q;
+    int lo = vp[max(0, c0 - R)] & ~1, hi = (vp[min(C.ncell, c1 + R)] + 1) & ~1;
+    if (hi - lo > LINK_STAGE) {
+      lo = vp[c0] & ~1;
+      hi = (vp[c1] + 1) & ~1;
+      if (hi - lo > LINK_STAGE) hi = lo;
+    }
+    stage[0] = lo;
+    stage[1] = hi;
+    mbar_init(&bar);
+    if (hi > lo) bulk_g2s(svt, vt + lo, (uint32_t)(hi - lo) * 8u, &bar);
+  }
   for (int i = threadIdx.x; i <= ncl; i += blockDim.x) cvp[i] = vp[c0 + i];
   if (threadIdx.x < ncl) {
     LinkCell<Q> &L = lc[threadIdx.x];
@@ -929,9 +1020,18 @@ __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
   const bool local = nv <= local_cap(C);
   if (local)
     for (int i = threadIdx.x; i < nv; i += blockDim.x) lp[i] = i;
-  __syncthreads();
-  const int64_t vb = C.vtx_base, wb = vb >> 5;
-  const long long *__restrict__ vt = (const long long *)s.vtau + vb;
+  const int slo = stage[0], shi = stage[1];
+  if (shi > slo) {
+    const bool ok = mbar_wait(&bar, 0);
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) atomicOr(s.status, ST_TIMEOUT);
+      return;
+    }
+  } else {
+    __syncthreads();
+  }
+  const long long *sv = svt - slo;  // sv[q] = time of vertex q for q in [slo, shi)
+  auto vtime = [&](int q) -> long long { return (q >= slo && q < shi) ? sv[q] : vt[q]; };
   int32_t *par = s.parent + vb;
   // Whole warps walk the tile (trip count rounded up) and reconverge after
   // every vertex, so that the divergent union of one iteration does not split
@@ -945,7 +1045,7 @@ __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
     const int ci = s.vcell[vb + w];
     const LinkCell<Q> &L = lc[ci];
     const int v0 = cvp[ci];
-    const long long tw = vt[w];
+    const long long tw = vtime(w);
     int P[2];
     uint8_t wrapbits = 0;
 #pragma unroll
@@ -954,17 +1054,20 @@ __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
       long long bt = 0;
       if (w > v0) {
         best = w - 1;
-        bt = vt[w - 1];
+        bt = vtime(w - 1);
       } else if (L.own_bj >= 0) {
         best = L.own_bj;
-        bt = vt[best];
+        bt = vtime(best);
       }
 #pragma unroll
       for (int k = 0; k < LinkCell<Q>::NO; ++k) {
-        const int q = time_lower_bound(vt, L.wa[sd][k], L.we[sd][k], tw + (L.wa[sd][k] < w ? 1 : 0));
-        const int cand = (q > L.wa[sd][k]) ? q - 1 : L.bj[sd][k];
+        const int lo = L.wa[sd][k], hi = L.we[sd][k];
+        const long long thr = tw + (lo < w ? 1 : 0);
+        const int q = (lo >= slo && hi <= shi) ? smem_lower_bound(sv, lo, hi, thr)
+                                               : time_lower_bound(vt, lo, hi, thr);
+        const int cand = (q > lo) ? q - 1 : L.bj[sd][k];
         if (cand >= 0) {
-          const long long tc = vt[cand];
+          const long long tc = vtime(cand);
           if (best < 0 || tc > bt || (tc == bt && cand > best)) {
             best = cand;
             bt = tc;

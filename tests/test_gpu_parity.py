@@ -385,8 +385,9 @@ def test_update_parity_global_fallbacks(monkeypatch, cap, slots, L, beta, Q):
                 assert sizes.max() > cap, (ctx, sizes.max())
             if slots:
                 # more distinct multi-node loops in a tile than the table holds
-                r, pl, pr = go["root"], go["pl"], go["pr"]
-                assert len(np.unique(r[pl[:sizes[0]] != pr[:sizes[0]]])) > slots, ctx
+                m = sizes[0]  # the first tile's vertices
+                r, pl, pr = go["root"][:m], go["pl"][:m], go["pr"][:m]
+                assert len(np.unique(r[pl != pr])) > slots, ctx
             st = new
     finally:
         ch.close()
