@@ -931,26 +931,6 @@ __device__ __forceinline__ int time_lower_bound(const long long *vt, int lo, int
   return lo;
 }
 
-// Vertex times a linking block stages in shared memory (24 KB for Q <= 2,
-// 8 KB beside the larger cell tables of Q = 3, 4): the tile's own and those
-// of the cells up to 8 Q^2 cells away, which hold the neighbour bonds'
-// vertices of the same windows.
-template <int Q>
-__host__ __device__ constexpr int link_stage() {
-  return Q <= 2 ? 3072 : 1024;
-}
-
-__device__ __forceinline__ int smem_lower_bound(const long long *sv, int lo, int hi, long long thr) {
-  while (lo < hi) {
-    const int mid = lo + ((hi - lo) >> 1);
-    if (sv[mid] < thr)
-      lo = mid + 1;
-    else
-      hi = mid;
-  }
-  return lo;
-}
-
 // Linking, then the union of the two fragments below every vertex.  Edges
 // with both nodes in the tile are united in shared memory, and the tile's
 // forest is then stored flat: every node points at its tile component's
@@ -959,39 +939,17 @@ __device__ __forceinline__ int smem_lower_bound(const long long *sv, int lo, int
 // after every tile has stored its forest (a tile too large for shared memory
 // leaves all of its edges to k_link_x, with every node its own root).
 template <int Q>
-__global__ void __launch_bounds__(TPB, 6) k_link(const DevChain *__restrict__ ch,
+__global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
                                               const int2 *__restrict__ tab, int64_t blk0,
                                               Scratch s) {
   __shared__ LinkCell<Q> lc[TILE];
   __shared__ int cvp[TILE + 1];
   __shared__ int lp[SMEM_CAP];
-  constexpr int LINK_STAGE = link_stage<Q>();
-  __shared__ __align__(16) long long svt[LINK_STAGE];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ int stage[2];
   if (halted(s)) return;
   const int2 t = tab[blk0 + blockIdx.x];
   const DevChain &C = ch[t.x];
   const int c0 = t.y * TILE, c1 = min(C.ncell, c0 + TILE), ncl = c1 - c0;
   const int32_t *vp = s.vptr + C.cell_off;
-  const int64_t vb = C.vtx_base, wb = vb >> 5;
-  const long long *__restrict__ vt = (const long long *)s.vtau + vb;
-  if (threadIdx.x == 0) {
-    // Stage the vertex times of the cells around the tile with one bulk copy
-    // (16-byte bounds: vb is a multiple of 128 vertices and the chain's
-    // region ends on an even vertex), started before the cells' set-up.
-    const int R = 8 * Q * Q;
-    int lo = vp[max(0, c0 - R)] & ~1, hi = (vp[min(C.ncell, c1 + R)] + 1) & ~1;
-    if (hi - lo > LINK_STAGE) {
-      lo = vp[c0] & ~1;
-      hi = (vp[c1] + 1) & ~1;
-      if (hi - lo > LINK_STAGE) hi = lo;
-    }
-    stage[0] = lo;
-    stage[1] = hi;
-    mbar_init(&bar);
-    if (hi > lo) bulk_g2s(svt, vt + lo, (uint32_t)(hi - lo) * 8u, &bar);
-  }
   for (int i = threadIdx.x; i <= ncl; i += blockDim.x) cvp[i] = vp[c0 + i];
   if (threadIdx.x < ncl) {
     LinkCell<Q> &L = lc[threadIdx.x];
@@ -1020,18 +978,9 @@ __global__ void __launch_bounds__(TPB, 6) k_link(const DevChain *__restrict__ ch
   const bool local = nv <= local_cap(C);
   if (local)
     for (int i = threadIdx.x; i < nv; i += blockDim.x) lp[i] = i;
-  const int slo = stage[0], shi = stage[1];
-  if (shi > slo) {
-    const bool ok = mbar_wait(&bar, 0);
-    if (!__syncthreads_and(ok)) {
-      if (threadIdx.x == 0) atomicOr(s.status, ST_TIMEOUT);
-      return;
-    }
-  } else {
-    __syncthreads();
-  }
-  const long long *sv = svt - slo;  // sv[q] = time of vertex q for q in [slo, shi)
-  auto vtime = [&](int q) -> long long { return (q >= slo && q < shi) ? sv[q] : vt[q]; };
+  __syncthreads();
+  const int64_t vb = C.vtx_base, wb = vb >> 5;
+  const long long *__restrict__ vt = (const long long *)s.vtau + vb;
   int32_t *par = s.parent + vb;
   // Whole warps walk the tile (trip count rounded up) and reconverge after
   // every vertex, so that the divergent union of one iteration does not split
@@ -1045,7 +994,7 @@ __global__ void __launch_bounds__(TPB, 6) k_link(const DevChain *__restrict__ ch
     const int ci = s.vcell[vb + w];
     const LinkCell<Q> &L = lc[ci];
     const int v0 = cvp[ci];
-    const long long tw = vtime(w);
+    const long long tw = vt[w];
     int P[2];
     uint8_t wrapbits = 0;
 #pragma unroll
@@ -1054,20 +1003,17 @@ __global__ void __launch_bounds__(TPB, 6) k_link(const DevChain *__restrict__ ch
       long long bt = 0;
       if (w > v0) {
         best = w - 1;
-        bt = vtime(w - 1);
+        bt = vt[w - 1];
       } else if (L.own_bj >= 0) {
         best = L.own_bj;
-        bt = vtime(best);
+        bt = vt[best];
       }
 #pragma unroll
       for (int k = 0; k < LinkCell<Q>::NO; ++k) {
-        const int lo = L.wa[sd][k], hi = L.we[sd][k];
-        const long long thr = tw + (lo < w ? 1 : 0);
-        const int q = (lo >= slo && hi <= shi) ? smem_lower_bound(sv, lo, hi, thr)
-                                               : time_lower_bound(vt, lo, hi, thr);
-        const int cand = (q > lo) ? q - 1 : L.bj[sd][k];
+        const int q = time_lower_bound(vt, L.wa[sd][k], L.we[sd][k], tw + (L.wa[sd][k] < w ? 1 : 0));
+        const int cand = (q > L.wa[sd][k]) ? q - 1 : L.bj[sd][k];
         if (cand >= 0) {
-          const long long tc = vtime(cand);
+          const long long tc = vt[cand];
           if (best < 0 || tc > bt || (tc == bt && cand > best)) {
             best = cand;
             bt = tc;
