@@ -254,41 +254,32 @@ __device__ int64_t lb_lookback(unsigned long long *st, int64_t g, int64_t first,
   }
 }
 
-// Insertion of one tile (128 cells).
-//  1. Set-up, one thread per cell: the cell's count K of Poisson candidates
-//     (Philox call 0), its bond's spin parity at the window start, the
-//     neighbour bonds' operator ranges in the window, its old operators.
-//  2. Draws, spread over all threads: call 0 of a cell gives K and candidate
-//     0, call m >= 1 candidates 2m-1 and 2m; each candidate's key
-//     (u53, draw index) goes to the cell's slots.
-//  3. Decisions, one thread per cell: the cell's keys sorted, the candidate
-//     times formed in that (ascending) order and walked beside the neighbour
-//     bonds' operators, whose parity below each time tells whether the
-//     bond's spins are antiparallel there (kept) or not.
-//  4. Offsets: the tile's vertex count by a block scan, its first vertex by
-//     decoupled look-back over the tiles before it.
-//  5. Vertices, one thread per cell: kept candidates and old operators
-//     merged by time (an old operator first on a tie) into the tile's output
-//     in shared memory, which the block then writes out in id order.
-// Candidates are staged INS_CAP at a time: a tile whose candidates exceed
-// that (the mean is 8 * TILE) runs its cells in groups, deciding in a
-// counting pass and drawing again in the writing pass.  A tile with more
-// vertices than its output buffer holds writes them from the cells' threads.
-constexpr int INS_CAP = 1152;
+// Candidate-parallel insertion.  A tile's cells first set up in shared memory
+// (count K of Poisson candidates, parity at the window start, neighbour
+// operator ranges); then the tile's Philox calls are spread over all threads
+// (call 0 of a cell gives K and candidate 0, call m >= 1 candidates 2m-1 and
+// 2m), each candidate's time is formed and the antiparallel test taken; the
+// kept candidates' places inside their cell follow from ranks: among the
+// cell's kept candidates by (u53, draw index), and against its old operators
+// by time (an old operator goes first on a tie).  Every vertex is then written
+// by its own thread (time, flag, cell; the parent forest is set by the linking
+// kernels).  Candidates are staged INS_CAP at a time: a tile whose candidates
+// exceed that (the mean is 8 * TILE) runs its cells in groups, counting in a
+// first pass and drawing again in the writing pass.
+constexpr int INS_CAP = 1280;
 constexpr int INS_SPAN = INS_CAP - KMAX;  // a group's cells start within INS_SPAN slots
 constexpr int INS_UCAP = INS_CAP / 2 + TILE;
 constexpr int INS_MIN_SPAN = 256;  // smallest group span a chain may ask for (tests)
 constexpr int INS_MAXG = (TILE * (KMAX - 1)) / INS_MIN_SPAN + 2;
-constexpr int INS_OUT = 1536;      // vertices of a tile staged for the coalesced write
-constexpr uint8_t OUT_OLD = 0x80;  // output cell byte: the vertex is an old operator
+constexpr int INS_OPCAP = 2048;  // old operators of a group mapped to their cell
+constexpr unsigned long long KEY_DROP = 1ull << 63;
 
 // Old operator times a tile stages in shared memory: its own cells' and those
-// of the cells that hold the neighbour bonds of the same windows (bonds at
-// most 2 Q^2 apart, 1 for Q = 1: up to 8 Q^2 cells away, 4 for Q = 1), when
-// they fit.
+// of the cells up to 8 Q^2 cells away (the neighbour bonds of the same
+// windows), when they fit.
 template <int Q>
 struct InsStage {
-  static constexpr int N = Q == 1 ? 704 : (Q == 2 ? 512 : 2048);
+  static constexpr int N = Q == 1 ? 1024 : (Q == 2 ? 512 : 2048);
 };
 
 // Where an old operator's time is read: from the staged copy if its index is
@@ -300,23 +291,24 @@ struct OpView {
   __device__ __forceinline__ const long long *range(int a, int b) const {
     return (a >= lo && b <= hi) ? sv : g;
   }
-  __device__ __forceinline__ long long at(int q) const { return (q >= lo && q < hi) ? sv[q] : g[q]; }
 };
 
 template <int Q>
 struct InsSmem {
   long long sop[InsStage<Q>::N];    // staged old operator times (16-byte aligned: first member)
-  long long out_t[INS_OUT];         // the tile's vertices in id order: time bits
-  unsigned long long key[INS_CAP];  // per cell: (u53 << 6 | draw), then the kept times
-  uint8_t out_c[INS_OUT];           // cell in tile | OUT_OLD
+  unsigned long long key[INS_CAP];  // u53, with bit 63 set if the candidate is not kept
+  long long tau[INS_CAP];           // time bits; LLONG_MAX if not kept
+  short klist[INS_CAP];             // kept candidates' slots (any order)
+  uint8_t scell[INS_CAP];           // slot -> cell in tile
   uint8_t ucell[INS_UCAP];          // Philox call -> cell in tile
+  uint8_t qcell[INS_OPCAP];         // old operator -> cell in tile
   NbOps<Q> X[TILE];
   unsigned long long T[2][KMAX];    // Poisson thresholds: full windows, last window
   int kpre[TILE + 1], upre[TILE + 1], q[TILE + 1];
   int K[TILE], nk[TILE], cex[TILE], b[TILE], j[TILE];
   uint8_t par0[TILE];
   int gfirst[INS_MAXG + 1];
-  int G;
+  int G, nkept;
   int sm[33];
   int slo, shi;
   uint64_t bar;
@@ -324,116 +316,178 @@ struct InsSmem {
   int64_t gt;
 };
 
-// Draw the candidates' keys of the cells of group g: (u53 << 6) | draw index,
-// which orders a cell's candidates by (u53, draw) and hence by time.
+// Number of operators of one neighbour bond (times tq[lo..hi), ascending)
+// that act before a candidate at time tau on bond b: order (time, bond).
+__device__ __forceinline__ int ops_before(const long long *__restrict__ tq, int lo, int hi,
+                                          long long tau, int bb, int b) {
+  const long long thr = tau + (bb < b ? 1 : 0);  // t < thr  <=>  (t, bb) < (tau, b)
+  const int base = lo;
+  while (lo < hi) {
+    const int mid = lo + ((hi - lo) >> 1);  // no overflow near 2^31
+    if (tq[mid] < thr)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo - base;
+}
+
+// Time of a candidate, tau = fma(d, u53 2^-53, t0) (one IEEE fused
+// multiply-add), and whether it is kept: the bond's spins antiparallel at tau
+// (parity at the window start flipped by the neighbour operators before tau).
 template <int Q>
-__device__ void ins_draw(const DevChain &C, InsSmem<Q> &S, int g) {
+__device__ __forceinline__ bool ins_decide(const OpView &V, const NbOps<Q> &X, int b, int par0,
+                                           uint64_t u53, double t0, double d, long long teb,
+                                           long long &tau) {
+  tau = __double_as_longlong(__fma_rn(d, __longlong_as_double((long long)unit_bits(u53)), t0));
+  if (!(tau < teb)) return false;
+  int p = par0;
+#pragma unroll
+  for (int k = 0; k < NbOps<Q>::N; ++k)
+    p ^= ops_before(V.range(X.o0[k], X.o1[k]), X.o0[k], X.o1[k], tau, X.bond[k], b);
+  return p & 1;
+}
+
+// Draw and decide the candidates of the cells of group g.
+template <int Q>
+__device__ void ins_draw(const DevChain &C, InsSmem<Q> &S, const OpView &V, int g, bool count) {
   const int c0 = S.gfirst[g], c1 = S.gfirst[g + 1];
   const int kb = S.kpre[c0], ub = S.upre[c0], nu = S.upre[c1] - ub;
   {
     const int c = threadIdx.x;
     if (c >= c0 && c < c1)
       for (int u = S.upre[c], e = S.upre[c + 1]; u < e; ++u) S.ucell[u - ub] = (uint8_t)c;
+    if (threadIdx.x == 0) S.nkept = 0;
   }
   __syncthreads();
   const uint32_t k0 = (uint32_t)C.seed, k1 = (uint32_t)(C.seed >> 32);
-  for (int u = threadIdx.x; u < nu; u += TILE) {
-    const int c = S.ucell[u];
-    const int m = u + ub - S.upre[c];
-    const int K = S.K[c], ks = S.kpre[c] - kb;
-    const U4 o = philox((TAG_INSERT << 24) | (uint32_t)m, (uint32_t)S.b[c], (uint32_t)S.j[c], C.sweep, k0, k1);
-    // words (x, y): candidate 2m-1 (for m = 0 the count); words (z, w): candidate 2m
-    const int k = 2 * m - 1;
-    if (k >= 0 && k < K)
-      S.key[ks + k] = ((((uint64_t)o.x | ((uint64_t)o.y << 32)) >> 11) << 6) | (uint64_t)k;
-    if (k + 1 < K) S.key[ks + k + 1] = ((((uint64_t)o.z | ((uint64_t)o.w << 32)) >> 11) << 6) | (uint64_t)(k + 1);
+  const int lane = threadIdx.x & 31;
+  for (int u0 = 0; u0 < nu; u0 += TILE) {  // whole warps, reconverged per step
+    const int u = u0 + threadIdx.x;
+    bool kp[2] = {false, false};
+    int sl[2] = {0, 0}, c = 0;
+    if (u < nu) {
+      c = S.ucell[u];
+      const int m = u + ub - S.upre[c];
+      const int j = S.j[c], K = S.K[c], ks = S.kpre[c] - kb, b = S.b[c], par0 = S.par0[c];
+      const NbOps<Q> X = S.X[c];
+      const double t0 = __longlong_as_double((long long)C.win[3 * j]);
+      const long long teb = (long long)C.win[3 * j + 1];
+      const double d = __longlong_as_double((long long)C.win[3 * j + 2]);
+      const U4 o = philox((TAG_INSERT << 24) | (uint32_t)m, (uint32_t)b, (uint32_t)j, C.sweep, k0, k1);
+      // words (x, y): candidate 2m-1 (for m = 0 the count); words (z, w): candidate 2m
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 2 * m - 1 + h;
+        if (k < 0 || k >= K) continue;
+        const uint64_t u53 = (h ? ((uint64_t)o.z | ((uint64_t)o.w << 32))
+                                : ((uint64_t)o.x | ((uint64_t)o.y << 32))) >> 11;
+        long long tau;
+        const bool keep = ins_decide<Q>(V, X, b, par0, u53, t0, d, teb, tau);
+        const int slot = ks + k;
+        S.key[slot] = keep ? u53 : (u53 | KEY_DROP);
+        S.tau[slot] = keep ? tau : LLONG_MAX;
+        S.scell[slot] = (uint8_t)c;
+        kp[h] = keep;
+        sl[h] = slot;
+      }
+    }
+    // kept list: one shared atomic per warp and half
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const unsigned km = __ballot_sync(0xffffffffu, kp[h]);
+      if (km) {
+        const int leader = __ffs(km) - 1;
+        int at = 0;
+        if (lane == leader) at = atomicAdd(&S.nkept, __popc(km));
+        at = __shfl_sync(0xffffffffu, at, leader);
+        if (kp[h]) {
+          S.klist[at + __popc(km & ((1u << lane) - 1u))] = (short)sl[h];
+          if (count) atomicAdd(&S.nk[c], 1);
+        }
+      }
+    }
+    __syncwarp();
   }
   __syncthreads();
 }
 
-// Cell c of group g (its own thread): sort the keys, form the times in that
-// order, keep those where the bond's spins are antiparallel (the parity at
-// the window start flipped by every neighbour operator ordered before
-// (tau, b): earlier, or at the same time on a lower bond).  The kept times
-// replace the keys at the front of the cell's slots; returns their number.
+// Place and write the vertices of the cells of group g (kept candidates, then
+// old operators); vertex ids are chain-local, base = the tile's first id.
 template <int Q>
-__device__ int ins_decide_cell(const DevChain &C, InsSmem<Q> &S, const OpView &V, int g, int c) {
-  const int kb = S.kpre[S.gfirst[g]];
-  const int K = S.K[c], ks = S.kpre[c] - kb;
-  unsigned long long *key = S.key + ks;
-  for (int i = 1; i < K; ++i) {  // insertion sort (K is about 8)
-    const unsigned long long x = key[i];
-    int y = i - 1;
-    while (y >= 0 && key[y] > x) {
-      key[y + 1] = key[y];
-      --y;
-    }
-    key[y + 1] = x;
-  }
-  const int j = S.j[c], b = S.b[c];
-  const double t0 = __longlong_as_double((long long)C.win[3 * j]);
-  const long long teb = (long long)C.win[3 * j + 1];
-  const double d = __longlong_as_double((long long)C.win[3 * j + 2]);
-  const NbOps<Q> &X = S.X[c];
-  int par = S.par0[c];
-  int p[NbOps<Q>::N];
-#pragma unroll
-  for (int k = 0; k < NbOps<Q>::N; ++k) p[k] = X.o0[k];
-  int nk = 0;
-  for (int i = 0; i < K; ++i) {
-    const uint64_t u53 = key[i] >> 6;
-    const long long tau =
-        __double_as_longlong(__fma_rn(d, __longlong_as_double((long long)unit_bits(u53)), t0));
-    if (!(tau < teb)) break;  // later keys give later times
-#pragma unroll
-    for (int k = 0; k < NbOps<Q>::N; ++k) {
-      const long long *tq = V.range(X.o0[k], X.o1[k]);
-      const long long thr = tau + (X.bond[k] < b ? 1 : 0);  // t < thr  <=>  (t, bond) < (tau, b)
-      int pk = p[k];
-      while (pk < X.o1[k] && tq[pk] < thr) {
-        ++pk;
-        par ^= 1;
-      }
-      p[k] = pk;
-    }
-    if (par & 1) key[nk++] = (unsigned long long)tau;
-  }
-  return nk;
-}
-
-// Cell c (its own thread): its kept times and old operators merged by time,
-// an old operator first on a tie, written at the cell's offset: to the
-// tile's output buffer, or straight to the vertex arrays at base.
-template <int Q>
-__device__ void ins_write_cell(const DevChain &C, InsSmem<Q> &S, const OpView &V, int g, int c,
-                               bool staged, int64_t base, const Scratch &s) {
-  const int kb = S.kpre[S.gfirst[g]];
-  const long long *kt = (const long long *)(S.key + (S.kpre[c] - kb));
-  const int nk = S.nk[c];
-  int q = S.q[c];
-  const int q1 = S.q[c + 1];
-  int i = 0, r = S.cex[c];
+__device__ void ins_write(const DevChain &C, InsSmem<Q> &S, const OpView &V, int g,
+                          int64_t base, const Scratch &s) {
+  const int c0 = S.gfirst[g], c1 = S.gfirst[g + 1];
+  const int kb = S.kpre[c0];
   const int64_t vb = C.vtx_base;
-  while (i < nk || q < q1) {
-    long long t;
-    bool old;
-    if (q < q1 && (i >= nk || V.at(q) <= kt[i])) {
-      t = V.at(q++);
-      old = true;
-    } else {
-      t = kt[i++];
-      old = false;
+  long long *vt = (long long *)s.vtau + vb;
+  uint8_t *vf = s.vflag + vb, *vc = s.vcell + vb;
+  const int nkept = S.nkept;
+  for (int i0 = 0; i0 < nkept; i0 += TILE) {
+    const int i = i0 + threadIdx.x;
+    if (i >= nkept) {
+      __syncwarp();
+      continue;
     }
-    if (staged) {
-      S.out_t[r] = t;
-      S.out_c[r] = (uint8_t)(c | (old ? OUT_OLD : 0));
-    } else {
-      const int64_t pos = vb + base + r;
-      ((long long *)s.vtau)[pos] = t;
-      s.vflag[pos] = old ? VF_OLD : 0;
-      s.vcell[pos] = (uint8_t)c;
+    const int slot = S.klist[i];
+    const long long tau = S.tau[slot];
+    const int c = S.scell[slot];
+    const int ks = S.kpre[c] - kb, K = S.K[c], k = slot - ks;
+    const unsigned long long key = S.key[slot];
+    int r = 0;
+    for (int x = 0; x < K; ++x) {
+      const unsigned long long k2 = S.key[ks + x];
+      r += (k2 < key) | ((k2 == key) & (x < k));
     }
-    ++r;
+    // old operators at or before tau (ascending times)
+    int lo = S.q[c], hi = S.q[c + 1];
+    const int q0 = lo;
+    const long long *otau = V.range(lo, hi);
+    while (lo < hi) {
+      const int mid = lo + ((hi - lo) >> 1);  // no overflow near 2^31
+      if (otau[mid] <= tau)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    r += lo - q0;
+    const int64_t pos = base + S.cex[c] + r;
+    vt[pos] = tau;
+    vf[pos] = 0;
+    vc[pos] = (uint8_t)c;
+    __syncwarp();
+  }
+  const int qa = S.q[c0], qb = S.q[c1], qt = S.q[0];
+  const bool mapped = qb - qt <= INS_OPCAP;
+  for (int q0 = qa; q0 < qb; q0 += TILE) {
+    const int q = q0 + threadIdx.x;
+    if (q >= qb) {
+      __syncwarp();
+      continue;
+    }
+    int c;
+    if (mapped) {
+      c = S.qcell[q - qt];
+    } else {
+      int lo = c0, hi = c1 - 1;  // largest c in [c0, c1) with S.q[c] <= q
+      while (lo < hi) {
+        const int mid = lo + ((hi - lo + 1) >> 1);
+        if (S.q[mid] <= q)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      c = lo;
+    }
+    const long long ot = (q >= V.lo && q < V.hi) ? V.sv[q] : V.g[q];
+    const int ks = S.kpre[c] - kb, K = S.K[c];
+    int r = q - S.q[c];
+    for (int x = 0; x < K; ++x) r += S.tau[ks + x] < ot;
+    const int64_t pos = base + S.cex[c] + r;
+    vt[pos] = ot;
+    vf[pos] = VF_OLD;
+    vc[pos] = (uint8_t)c;
+    __syncwarp();
   }
 }
 
@@ -480,7 +534,7 @@ __device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict_
     // Stage the old operator times around the tile with one bulk copy
     // (16-byte bounds: op_tau has room for one time past its capacity),
     // overlapped with the cells' set-up.
-    const int R = Q == 1 ? 4 : 8 * Q * Q;
+    const int R = 8 * Q * Q;
     const int ce = min(C.ncell, t.y * TILE + TILE);
     int lo = op[max(0, t.y * TILE - R)] & ~1, hi = (op[min(C.ncell, ce + R)] + 1) & ~1;
     if (hi - lo > InsStage<Q>::N) {
@@ -550,6 +604,11 @@ __device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict_
   if (c == TILE - 1) S.q[TILE] = q1;
   int tot;
   const int ex = block_excl_scan<int>(K | (P << 16), S.sm, tot);
+  {
+    // old operator -> cell map (all of the tile's operators, if they fit)
+    const int qa = S.q[0];
+    for (int q = q0; q < q1 && q - qa < INS_OPCAP; ++q) S.qcell[q - qa] = (uint8_t)c;
+  }
   S.kpre[c] = ex & 0xffff;
   S.upre[c] = ex >> 16;
   if (c == TILE - 1) {
@@ -569,8 +628,6 @@ __device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict_
   }
   __syncthreads();
   const int G = S.G;
-  int my_g = 0;  // the group of this thread's cell
-  while (my_g + 1 < G && S.gfirst[my_g + 1] <= c) ++my_g;
   if (S.shi > S.slo) {
     const bool ok = mbar_wait(&S.bar, 0);
     if (!__syncthreads_and(ok)) {
@@ -581,14 +638,8 @@ __device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict_
   const OpView V{otau, S.sop - S.slo, S.slo, S.shi};
 
   // -- draw, decide and count ------------------------------------------------
-  int nk = 0;
-  for (int g = 0; g < G; ++g) {
-    ins_draw<Q>(C, S, g);
-    if (valid && g == my_g) nk = ins_decide_cell<Q>(C, S, V, g, c);
-    if (G > 1) __syncthreads();  // the next group's draws reuse the slots
-  }
-  S.nk[c] = nk;
-  const int cnt = valid ? (q1 - q0) + nk : 0;
+  for (int g = 0; g < G; ++g) ins_draw<Q>(C, S, V, g, true);
+  const int cnt = valid ? (q1 - q0) + S.nk[c] : 0;
   int ctot;
   S.cex[c] = block_excl_scan<int>(cnt, S.sm, ctot);
 
@@ -623,26 +674,10 @@ __device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict_
   }
 
   // -- write -----------------------------------------------------------------
-  const bool staged = ctot <= min(INS_OUT, local_cap(C));
   for (int g = 0; g < G; ++g) {
-    if (G > 1) {
-      ins_draw<Q>(C, S, g);
-      if (valid && g == my_g) ins_decide_cell<Q>(C, S, V, g, c);
-    }
-    if (valid && g == my_g) ins_write_cell<Q>(C, S, V, g, c, staged, base, s);
-    if (G > 1) __syncthreads();
-  }
-  if (staged) {
+    if (G > 1) ins_draw<Q>(C, S, V, g, false);
+    ins_write<Q>(C, S, V, g, base, s);
     __syncthreads();
-    const int64_t vb = C.vtx_base;
-    long long *vt = (long long *)s.vtau + vb + base;
-    uint8_t *vf = s.vflag + vb + base, *vc = s.vcell + vb + base;
-    for (int i = threadIdx.x; i < ctot; i += TILE) {
-      const uint8_t oc = S.out_c[i];
-      vt[i] = S.out_t[i];
-      vf[i] = (oc & OUT_OLD) ? VF_OLD : 0;
-      vc[i] = oc & (uint8_t)~OUT_OLD;
-    }
   }
 }
 
@@ -896,28 +931,13 @@ __device__ __forceinline__ int time_lower_bound(const long long *vt, int lo, int
   return lo;
 }
 
-// Linking, then the union of the two fragments below every vertex.
-//
-// Predecessors: one thread per (cell, side) walks the cell's vertices in
-// order (ascending (tau, id)) and, beside them, the vertices of every other
-// bond's cell of the same window on that side's subsite, each with a pointer
-// that only moves forward (a merge of sorted lists): the predecessor of a
-// vertex is the latest leg before it on the subsite among the cell's previous
-// vertex, those bonds' last vertices before it, and the last vertices of
-// earlier windows; with none, it comes through the tau = 0 cut.  The result
-// (bit 31: the fragment crosses the cut) waits in shared memory, or in the
-// global link arrays for a tile too large for shared memory.
-//
-// Unions: whole warps then walk the tile's vertices in id order.  Edges with
-// both nodes in the tile are united in shared memory, and the tile's forest is
-// then stored flat: every node points at its tile component's root, its
-// smallest node.  Edges that leave the tile are marked and united in the
-// global forest by k_link_x, after every tile has stored its forest (a tile
-// too large for shared memory leaves all of its edges to k_link_x, with every
-// node its own root).  Both nodes of an edge that leaves the tile get the
-// open mark.
-constexpr uint32_t LINK_WRAP = 0x80000000u;
-
+// Linking, then the union of the two fragments below every vertex.  Edges
+// with both nodes in the tile are united in shared memory, and the tile's
+// forest is then stored flat: every node points at its tile component's
+// root, its smallest node.  Edges
+// that leave the tile are marked and united in the global forest by k_link_x,
+// after every tile has stored its forest (a tile too large for shared memory
+// leaves all of its edges to k_link_x, with every node its own root).
 template <int Q>
 __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
                                               const int2 *__restrict__ tab, int64_t blk0,
@@ -925,7 +945,6 @@ __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
   __shared__ LinkCell<Q> lc[TILE];
   __shared__ int cvp[TILE + 1];
   __shared__ int lp[SMEM_CAP];
-  __shared__ uint32_t sp[2][SMEM_CAP];
   if (halted(s)) return;
   const int2 t = tab[blk0 + blockIdx.x];
   const DevChain &C = ch[t.x];
@@ -959,34 +978,40 @@ __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
   const bool local = nv <= local_cap(C);
   if (local)
     for (int i = threadIdx.x; i < nv; i += blockDim.x) lp[i] = i;
+  __syncthreads();
   const int64_t vb = C.vtx_base, wb = vb >> 5;
   const long long *__restrict__ vt = (const long long *)s.vtau + vb;
   int32_t *par = s.parent + vb;
-
-  // -- predecessors: a merge walk per (cell, side) ----------------------------
-  for (int item = threadIdx.x; item < 2 * ncl; item += blockDim.x) {
-    const int ci = item >> 1, sd = item & 1;
+  // Whole warps walk the tile (trip count rounded up) and reconverge after
+  // every vertex, so that the divergent union of one iteration does not split
+  // the next one's predecessor search.
+  for (int w0 = a; w0 < e; w0 += blockDim.x) {
+    const int w = w0 + threadIdx.x;
+    if (w >= e) {
+      __syncwarp();
+      continue;
+    }
+    const int ci = s.vcell[vb + w];
     const LinkCell<Q> &L = lc[ci];
-    const int v0 = cvp[ci], v1 = cvp[ci + 1];
-    int q[LinkCell<Q>::NO];
+    const int v0 = cvp[ci];
+    const long long tw = vt[w];
+    int P[2];
+    uint8_t wrapbits = 0;
 #pragma unroll
-    for (int k = 0; k < LinkCell<Q>::NO; ++k) q[k] = L.wa[sd][k];
-    int prev = L.own_bj;
-    long long pt = prev >= 0 ? vt[prev] : 0;
-    for (int w = v0; w < v1; ++w) {
-      const long long tw = vt[w];
-      int best = prev;
-      long long bt = pt;
+    for (int sd = 0; sd < 2; ++sd) {
+      int best = -1;
+      long long bt = 0;
+      if (w > v0) {
+        best = w - 1;
+        bt = vt[w - 1];
+      } else if (L.own_bj >= 0) {
+        best = L.own_bj;
+        bt = vt[best];
+      }
 #pragma unroll
       for (int k = 0; k < LinkCell<Q>::NO; ++k) {
-        const int wa = L.wa[sd][k], we = L.we[sd][k];
-        // key (tau, id) below (tw, w): the neighbour cell's ids are all below
-        // w or all above it
-        const long long thr = tw + (wa < w ? 1 : 0);
-        int qq = q[k];
-        while (qq < we && vt[qq] < thr) ++qq;
-        q[k] = qq;
-        const int cand = (qq > wa) ? qq - 1 : L.bj[sd][k];
+        const int q = time_lower_bound(vt, L.wa[sd][k], L.we[sd][k], tw + (L.wa[sd][k] < w ? 1 : 0));
+        const int cand = (q > L.wa[sd][k]) ? q - 1 : L.bj[sd][k];
         if (cand >= 0) {
           const long long tc = vt[cand];
           if (best < 0 || tc > bt || (tc == bt && cand > best)) {
@@ -995,45 +1020,22 @@ __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
           }
         }
       }
-      uint32_t P;
-      if (best >= 0) {
-        P = (uint32_t)best;
-      } else {
-        const int cut = L.cut[sd];
-        if (cut < 0) fail_check(s, 2, c0 + ci, w, sd, 0, 0);
-        P = (uint32_t)(cut < 0 ? w : cut) | LINK_WRAP;
+      if (best < 0) {
+        best = L.cut[sd];
+        wrapbits |= sd ? VF_WRAP_R : VF_WRAP_L;
+        if (best < 0) {
+          fail_check(s, 2, c0 + ci, w, sd, 0, 0);
+          best = w;
+        }
       }
-      if (local)
-        sp[sd][w - a] = P;
-      else
-        (sd ? s.pr : s.pl)[vb + w] = (int32_t)P;
-      prev = w;
-      pt = tw;
+      P[sd] = best;
     }
-  }
-  __syncthreads();
-
-  // -- links stored, unions ----------------------------------------------------
-  // Whole warps walk the tile (trip count rounded up) and reconverge after
-  // every vertex, so that the divergent union of one iteration does not split
-  // the next one's work.
-  for (int w0 = a; w0 < e; w0 += blockDim.x) {
-    const int w = w0 + threadIdx.x;
-    if (w >= e) {
-      __syncwarp();
-      continue;
-    }
-    const uint32_t x0 = local ? sp[0][w - a] : (uint32_t)s.pl[vb + w];
-    const uint32_t x1 = local ? sp[1][w - a] : (uint32_t)s.pr[vb + w];
-    int P[2] = {(int)(x0 & ~LINK_WRAP), (int)(x1 & ~LINK_WRAP)};
-    const uint8_t wrapbits = ((x0 & LINK_WRAP) ? VF_WRAP_L : 0) | ((x1 & LINK_WRAP) ? VF_WRAP_R : 0);
     s.pl[vb + w] = P[0];
     s.pr[vb + w] = P[1];
     if (wrapbits) s.vflag[vb + w] |= wrapbits;
     const bool inside = P[0] >= a && P[0] < e && P[1] >= a && P[1] < e;
     if (!inside) {
       set_bit(s.openmark, wb, P[0]);
-      if (P[1] != P[0]) set_bit(s.openmark, wb, P[1]);
       if (local && P[0] != P[1]) set_bit(s.xmark, wb, w);
     } else if (local && P[0] != P[1]) {
       suf_union(lp, P[0] - a, P[1] - a, nv, s.status);
@@ -1235,7 +1237,7 @@ __device__ __forceinline__ void loop_add(int *keys, unsigned *vals, int key, con
     }
     if (k == key) {
 #pragma unroll
-      for (int i = 0; i < NS; ++i) sadd64(vals + 2 * (LOOP_SUMS * h + i), x.v[i]);
+      for (int i = 0; i < NS; ++i) sadd64(vals + 2 * (NS * h + i), x.v[i]);
       return;
     }
     h = (h + 1) & mask;
@@ -1252,21 +1254,25 @@ __device__ __forceinline__ void loop_squares(const long long *v, u128 &w2, u128 
   if (T) z2 += sq_abs(v[3]) + sq_abs(v[4]);
 }
 
-constexpr int TPB_EST = 512;
+constexpr int TPB_EST = 256;
+// Vertices of a tile whose ticks (and phase factors) the loop-properties
+// kernel stages in shared memory; ticks beyond it are computed where needed.
+constexpr int EST_STAGE = 1536;
 
 // T: also the temporal moment (phase factors, Zr and Zi); off by default.
 template <int Q, bool T>
-__global__ void __launch_bounds__(TPB_EST, T ? 3 : 4) k_est(const DevChain *__restrict__ ch,
+__global__ void __launch_bounds__(TPB_EST, T ? 6 : 8) k_est(const DevChain *__restrict__ ch,
                                              const int2 *__restrict__ tab, int64_t blk0,
                                              Scratch s) {
   __shared__ int lkeys[LOOP_SLOTS];
-  __shared__ unsigned lvals[2 * LOOP_SUMS * LOOP_SLOTS];
+  constexpr int NS = T ? LOOP_SUMS : 3;  // sums carried per loop
+  __shared__ unsigned lvals[2 * NS * LOOP_SLOTS];
   __shared__ int cvp[TILE + 1];
   __shared__ int cnew[TILE];
   __shared__ long long ccl[TILE], csl[TILE], ccr[TILE], csr[TILE], cxl[TILE], cxr[TILE];
   extern __shared__ long long est_dyn[];
   long long *qv = est_dyn;                   // ticks q(tau) of the tile's vertices
-  int2 *ev = (int2 *)(est_dyn + SMEM_CAP);   // their phase factors exp(i w1 tau)
+  int2 *ev = (int2 *)(est_dyn + EST_STAGE);  // their phase factors exp(i w1 tau)
   if (halted(s)) return;
   const int64_t gt = blk0 + blockIdx.x;
   const int2 t = tab[gt];
@@ -1291,7 +1297,7 @@ __global__ void __launch_bounds__(TPB_EST, T ? 3 : 4) k_est(const DevChain *__re
   for (int i = threadIdx.x; i < LOOP_SLOTS; i += blockDim.x) {
     lkeys[i] = -1;
 #pragma unroll
-    for (int k = 0; k < 2 * LOOP_SUMS; ++k) lvals[2 * LOOP_SUMS * i + k] = 0u;
+    for (int k = 0; k < 2 * NS; ++k) lvals[2 * NS * i + k] = 0u;
   }
   __syncthreads();
   const int a = cvp[0], e = cvp[ncl];
@@ -1304,7 +1310,7 @@ __global__ void __launch_bounds__(TPB_EST, T ? 3 : 4) k_est(const DevChain *__re
   // Their phase factors too (temporal moment, w1 = 2 pi / beta).
   const uint64_t phR = C.phR;
   const int phS = C.phS;
-  const int nq = min(e - a, local_cap(C));
+  const int nq = min(min(e - a, local_cap(C)), EST_STAGE);
   const unsigned slot_mask =
       (C.loop_slots > 0 && C.loop_slots <= LOOP_SLOTS && !(C.loop_slots & (C.loop_slots - 1)))
           ? (unsigned)C.loop_slots - 1u
@@ -1359,7 +1365,7 @@ __global__ void __launch_bounds__(TPB_EST, T ? 3 : 4) k_est(const DevChain *__re
         // two fragments are the two below w: the loop's sums are complete here.
         loop_squares<T>(x.v, w2, f2, z2);
       } else {
-        loop_add<T ? LOOP_SUMS : 3>(lkeys, lvals, rb, x, s, vb, slot_mask);
+        loop_add<NS>(lkeys, lvals, rb, x, s, vb, slot_mask);
       }
     }
     __syncwarp();
@@ -1378,9 +1384,9 @@ __global__ void __launch_bounds__(TPB_EST, T ? 3 : 4) k_est(const DevChain *__re
     if (kk < 0) continue;
     long long v[LOOP_SUMS] = {};
 #pragma unroll
-    for (int i = 0; i < (T ? LOOP_SUMS : 3); ++i) v[i] = (long long)sget64(lvals + 2 * (LOOP_SUMS * h + i));
+    for (int i = 0; i < NS; ++i) v[i] = (long long)sget64(lvals + 2 * (NS * h + i));
     if (get_bit(s.openroot, wb, kk)) {
-      acc_add<T ? LOOP_SUMS : 3>(s, vb + kk, v);
+      acc_add<NS>(s, vb + kk, v);
     } else {
       loop_squares<T>(v, w2, f2, z2);
     }
@@ -1730,7 +1736,7 @@ void launch_check_forest(const Launch &L, cudaStream_t st) {
 }
 
 // Per-vertex staging of the loop-properties kernel: ticks and phase factors.
-constexpr size_t EST_DYN_SMEM = SMEM_CAP * (sizeof(long long) + sizeof(int2));
+constexpr size_t EST_DYN_SMEM = EST_STAGE * (sizeof(long long) + sizeof(int2));
 
 // Device tables and kernel attributes, set once per process and device: the
 // phase factor table (cos and sin of 2 pi k / 2^16 rounded to 30 fractional
@@ -1766,7 +1772,7 @@ int init_kernel_attributes() {
 
 void launch_est(const Launch &L, cudaStream_t st) {
   // without the temporal moment only the ticks are staged
-  const size_t dyn = L.temporal ? EST_DYN_SMEM : SMEM_CAP * sizeof(long long);
+  const size_t dyn = L.temporal ? EST_DYN_SMEM : EST_STAGE * sizeof(long long);
 #define EST_Q(Q)                                                                                       \
   if (L.ntile[Q - 1]) {                                                                                \
     if (L.temporal)                                                                                    \
