@@ -48,7 +48,7 @@ ORACLE_SAMPLE_L = 8192
 # The batched form beside the single chain (the benchmark list's batched
 # configuration): chains, updates per chain, device budget of one wave.
 BATCH_CHAINS, BATCH_UPDATES, BATCH_BUDGET_GB = 4096, 100, 150.0
-KERNELS_PER_UPDATE = 9
+KERNELS_PER_UPDATE = 11
 # DRAM bytes per vertex of each phase's kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture at L=16384, beta=4096, divided by
 # that update's vertex count; profiles/topkernels_L16384_beta4096.md), valid
@@ -115,12 +115,14 @@ def phase_bytes(rec, ncell, L):
         # vertex time and cell in, predecessor links and parent forest out,
         # flag read-modify-write, cell offsets
         "link_union": 23 * n + 4 * ncell,
-        # parent read and root written; cell, links, flag read + write, time;
-        # open-mark, open-root and flip bitmaps; the new operators' times
-        # written and the next operator offsets
-        "loops": 27.375 * n + 8 * nn + 8 * ncell,
-        # the open-root bitmap (the open loops' records are not counted)
-        "open_loops": n / 8.0,
+        # parent read, root written, open-mark / open-root / flip bitmaps
+        "loop_ids": 8.375 * n,
+        # cell, links, flag read+write, parent, time, flip bits; new-operator
+        # counts per cell
+        "loop_props": 23.125 * n + 4 * ncell,
+        "op_offsets": 16 * (ncell / 128.0),
+        # flags, new operator times read + written, cell offsets
+        "op_rewrite": n + 16 * nn + 8 * ncell,
         "spin_rewrite": 2.0 * L + 64.0,
     }
 
@@ -297,7 +299,7 @@ def run_ours(args, world, rank, local):
         ch.set_temporal(True)
     geo = ch.geometry()
     # thermalization from the Neel state, the block sizes of the union-find
-    # phases tuned (9 trials of 2 updates), then W warm-up updates (untimed)
+    # phases tuned (8 trials of 2 updates), then W warm-up updates (untimed)
     ch.update(therm)
     tuning = ch.autotune(2)
     ch.update(args.warmup)
@@ -408,7 +410,7 @@ def run_ours(args, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": workload_name(L, beta) + f", one chain per GPU (seed 1+rank), Neel start, "
-                               f"{therm}+18+{args.warmup} untimed updates (18: autotuning trials)",
+                               f"{therm}+16+{args.warmup} untimed updates (16: autotuning trials)",
                    "L": L, "beta": beta, "vertices_per_update": mean_n,
                    "temporal_moment": bool(args.temporal), "tuning": tuning, "retimed_windows": retimed,
                    "l2": "inputs larger than L2 (state and per-update graph are tens of GB)"},

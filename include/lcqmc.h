@@ -186,10 +186,9 @@ int lcqmc_restore(lcqmc_handle h, const void *buf, size_t len);
 /* Per-phase device time (ms) accumulated over updates while enabled, in the
  * spirit of the cost table of Sec. 4.3: 0 random numbers and labeling
  * (insertion with vertex offsets), 1 tau=0 cut, 2 linking and union-find,
- * 3 loops (ids and coins, loop properties, new flags, operator offsets and
- * rewrite, in one kernel), 4 loops that left their tile (their squared
- * sums), 5 spin rewrite and record. */
-#define LCQMC_NPHASE 6
+ * 3 loop ids (compression, coins), 4 loop properties and new flags,
+ * 5 operator offsets, 6 operator rewrite, 7 spin rewrite and record. */
+#define LCQMC_NPHASE 8
 int lcqmc_set_phase_timing(lcqmc_handle h, int enable);
 
 /* Turns the temporal moment on or off (off after create): chi(pi, w1) at the
@@ -212,11 +211,10 @@ int lcqmc_set_wait_limit(lcqmc_handle h, int64_t limit);
 /* Block sizes of the union-find phases (Sec. 3.2 on the GPU): threads per
  * block of the tile linking and local union-find (128 or 256), warps per block
  * of the union of tile-crossing edges (1..8, one tile each) and threads per
- * block of the pass over the loops that left their tile (32..256 in steps of
- * 32, one warp per tile).  Defaults 256, 8, 128.  Any choice gives
- * bit-identical results; only the time changes. */
+ * block of the compression (32..128 in steps of 32).  Defaults 256, 8, 128.
+ * Any choice gives bit-identical results; only the time changes. */
 typedef struct {
-  int32_t link_threads, link_x_warps, open_threads, pad;
+  int32_t link_threads, link_x_warps, compress_threads, pad;
 } lcqmc_tuning;
 /* Current block sizes (host struct, caller-owned). */
 int lcqmc_get_tuning(lcqmc_handle h, lcqmc_tuning *out);
@@ -225,7 +223,7 @@ int lcqmc_get_tuning(lcqmc_handle h, lcqmc_tuning *out);
 int lcqmc_set_tuning(lcqmc_handle h, const lcqmc_tuning *cfg);
 /* Autotuner: times each candidate with the phase events over
  * updates_per_trial updates (a coordinate search: 128/256 x 2/4/8 for the
- * linking phase, then 64/128/256 for the open-loop pass; 9 trials) and keeps the
+ * linking phase, then 64/128 for the compression; 8 trials) and keeps the
  * fastest.  The trial updates are ordinary updates of the chain (records and
  * running sums included).  out (may be NULL) receives the choice. */
 int lcqmc_autotune(lcqmc_handle h, int64_t updates_per_trial, lcqmc_tuning *out);

@@ -102,8 +102,7 @@ struct Scratch {
   uint32_t *openmark, *openroot, *flipbits, *xmark;
   int64_t vcap;
   unsigned long long *tile_state;  // per tile: insertion look-back word (flag << 62 | count)
-  unsigned long long *tile_state2; // per tile: new-operator look-back word of the loops kernel
-  unsigned int *tickets;           // per Q group: next tile of the insertion launch, then of the loops launch
+  unsigned int *tickets;           // per Q group: next tile of the insertion launch
   int *status;
   int uf_limit;   // bound of the global union-find walks and retries (UF_MAX_ITERS)
   int64_t *need;  // [0] vertex capacity needed by the last update

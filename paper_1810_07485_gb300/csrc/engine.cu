@@ -256,7 +256,6 @@ Engine::~Engine() {
   dfree(s_.status);
   dfree(s_.tickets);
   dfree(s_.tile_state);
-  dfree(s_.tile_state2);
   dfree(s_.need);
   dfree(s_.dbg);
   if (own_stream_ && st_) cudaStreamDestroy(st_);
@@ -268,7 +267,7 @@ int Engine::open(void *stream, const lcqmc_allocator *alloc, int ring_cap) {
     set_error("device table initialization failed");
     return LCQMC_E_CUDA;
   }
-  // Debug: verify the loop forest after the loops kernel.
+  // Debug: verify the loop forest after every compression.
   if (const char *e = std::getenv("LCQMC_CHECK_FOREST")) L_.check_forest = std::atoi(e) != 0;
   if (alloc && alloc->alloc && alloc->free) {
     alloc_ = *alloc;
@@ -286,7 +285,7 @@ int Engine::open(void *stream, const lcqmc_allocator *alloc, int ring_cap) {
   set_full_table(T.data(), st_);
   DALLOC(s_.status, int, 1);
   s_.uf_limit = UF_MAX_ITERS;
-  DALLOC(s_.tickets, unsigned int, 2 * QMAX);
+  DALLOC(s_.tickets, unsigned int, QMAX);
   DALLOC(s_.need, int64_t, 4);
   DALLOC(s_.dbg, long long, 8);
   CK(cudaMemsetAsync(s_.status, 0, sizeof(int), st_));
@@ -446,7 +445,7 @@ int Engine::layout() {
       d.ins_span = 0;
       if (const char *e = std::getenv("LCQMC_INSERT_GROUP_SLOTS")) d.ins_span = std::atoi(e);
       // Test hooks: fewer vertices per tile in shared memory (tiles above it
-      // take the global-memory paths of linking, union-find, root walks and
+      // take the global-memory paths of linking, union-find, compression and
       // loop sums), and a smaller per-tile loop table (loops that do not fit
       // spill to their global records).
       d.local_cap = 0;
@@ -492,8 +491,6 @@ int Engine::layout() {
     GROW(s_.tile_sz2, c9, 2 * nt, unsigned long long);
     int64_t c8 = cap_tiles_;
     GROW(s_.tile_state, c8, nt, unsigned long long);
-    int64_t c10 = cap_tiles_;
-    GROW(s_.tile_state2, c10, nt, unsigned long long);
     cap_tiles_ = nt;
   }
   if (ns > cap_sites_) {
@@ -566,8 +563,10 @@ int Engine::init(const std::vector<ChainSpec> &specs, void *stream, const lcqmc_
 int Engine::enqueue_one(bool timed, int slot) {
   const int64_t nw = vcap_ / 32 + 1;
   // phases as in the paper's Table 3 rows: event pairs and NVTX ranges
-  static const char *const kPhase[LCQMC_NPHASE] = {"lcqmc.insert", "lcqmc.cut", "lcqmc.link_union",
-                                                   "lcqmc.loops",  "lcqmc.open_loops", "lcqmc.spin_rewrite"};
+  static const char *const kPhase[LCQMC_NPHASE] = {"lcqmc.insert",    "lcqmc.cut",
+                                                   "lcqmc.link_union", "lcqmc.loop_ids",
+                                                   "lcqmc.loop_props", "lcqmc.op_offsets",
+                                                   "lcqmc.op_rewrite", "lcqmc.spin_rewrite"};
   auto mark = [&](int k) {
     if (!timed) return;
     cudaEventRecord(ev_[slot * (LCQMC_NPHASE + 1) + k], st_);
@@ -577,8 +576,7 @@ int Engine::enqueue_one(bool timed, int slot) {
   mark(0);  // [0] labeling: random numbers, insertion, vertex offsets (one pass)
   launch_bond_parity(L_, st_);
   CK(cudaMemsetAsync(s_.tile_state, 0, 8 * (size_t)cap_tiles_, st_));
-  CK(cudaMemsetAsync(s_.tile_state2, 0, 8 * (size_t)cap_tiles_, st_));
-  CK(cudaMemsetAsync(s_.tickets, 0, 2 * QMAX * sizeof(unsigned int), st_));
+  CK(cudaMemsetAsync(s_.tickets, 0, QMAX * sizeof(unsigned int), st_));
   CK(cudaMemsetAsync(s_.openmark, 0, 4 * nw, st_));
   CK(cudaMemsetAsync(s_.openroot, 0, 4 * nw, st_));
   CK(cudaMemsetAsync(s_.flipbits, 0, 4 * nw, st_));
@@ -588,15 +586,19 @@ int Engine::enqueue_one(bool timed, int slot) {
   launch_cut(L_, st_);
   mark(2);  // [2] linking + union-find
   launch_link(L_, st_);
-  mark(3);  // [3] loops: ids and coins, properties, new flags, operator rewrite
-  launch_loops(L_, st_);
+  mark(3);  // [3] loop ids (compression, coins)
+  launch_compress(L_, st_);
   if (L_.check_forest) launch_check_forest(L_, st_);
-  mark(4);  // [4] loops that left their tile
-  launch_open(L_, st_);
-  mark(5);  // [5] spin rewrite + record
+  mark(4);  // [4] loop properties, new flags
+  launch_est(L_, st_);
+  mark(5);  // [5] operator offsets
+  launch_scan_ops(L_, st_);
+  mark(6);  // [6] operator rewrite
+  launch_compact(L_, st_);
+  mark(7);  // [7] spin rewrite + record
   launch_sites(L_, st_);
   launch_final(L_, st_);
-  mark(6);
+  mark(8);
   CK(cudaGetLastError());
   return LCQMC_OK;
 }
@@ -1013,22 +1015,22 @@ int Engine::set_temporal(int enable) {
 void Engine::get_tuning(lcqmc_tuning *out) const {
   out->link_threads = L_.link_threads;
   out->link_x_warps = L_.link_x_warps;
-  out->open_threads = L_.open_threads;
+  out->compress_threads = L_.compress_threads;
   out->pad = 0;
 }
 
 int Engine::set_tuning(const lcqmc_tuning &t) {
   if (!(t.link_threads == 128 || t.link_threads == 256) || t.link_x_warps < 1 || t.link_x_warps > 8 ||
-      t.open_threads < 32 || t.open_threads > 256 || t.open_threads % 32 != 0) {
+      t.compress_threads < 32 || t.compress_threads > 128 || t.compress_threads % 32 != 0) {
     set_error("tuning out of range: link_threads 128 or 256, link_x_warps 1..8, "
-              "open_threads 32..256 in steps of 32");
+              "compress_threads 32..128 in steps of 32");
     return LCQMC_E_INVAL;
   }
   int rc = sync();
   if (rc) return rc;
   L_.link_threads = t.link_threads;
   L_.link_x_warps = t.link_x_warps;
-  L_.open_threads = t.open_threads;
+  L_.compress_threads = t.compress_threads;
   if (gexec_) {  // the captured launches carry the block sizes
     cudaGraphExecDestroy(gexec_);
     gexec_ = nullptr;
@@ -1038,9 +1040,9 @@ int Engine::set_tuning(const lcqmc_tuning &t) {
 
 // Coordinate search over the block sizes of the union-find phases, each
 // candidate timed by the phase events over n updates: linking + global unions
-// (phase 2) over link_threads x link_x_warps, then the pass over the loops
-// that left their tile (phase 4) over open_threads.  The trial updates are
-// ordinary updates of every chain; the block sizes do not change any result.
+// (phase 2) over link_threads x link_x_warps, then compression (phase 3) over
+// compress_threads.  The trial updates are ordinary updates of every chain;
+// the block sizes do not change any result.
 int Engine::autotune(int64_t n, lcqmc_tuning *out) {
   if (n < 1) {
     set_error("autotune needs at least one update per trial");
@@ -1058,7 +1060,7 @@ int Engine::autotune(int64_t n, lcqmc_tuning *out) {
     return rc;
   };
   double best_ms = 1e300;
-  static const int link_threads[] = {128, 256}, link_x_warps[] = {2, 4, 8}, open_threads[] = {64, 128, 256};
+  static const int link_threads[] = {128, 256}, link_x_warps[] = {2, 4, 8}, compress_threads[] = {64, 128};
   lcqmc_tuning cur = best;
   for (int lt : link_threads)
     for (int xw : link_x_warps) {
@@ -1074,14 +1076,14 @@ int Engine::autotune(int64_t n, lcqmc_tuning *out) {
     }
   best_ms = 1e300;
   cur = best;
-  for (int ct : open_threads) {
-    cur.open_threads = ct;
+  for (int ct : compress_threads) {
+    cur.compress_threads = ct;
     double ms = 0.0;
-    int rc = trial(cur, 4, &ms);
+    int rc = trial(cur, 3, &ms);
     if (rc) return rc;
     if (ms < best_ms) {
       best_ms = ms;
-      best.open_threads = ct;
+      best.compress_threads = ct;
     }
   }
   int rc = set_tuning(best);

@@ -10,11 +10,11 @@
 //   k_cut            last leg per subsite, tau=0 subspin permutation
 //   k_link           predecessor of each leg on both subsites; union of the two
 //                    fragments below each vertex (lock-free, min root)    [2]
-//   k_loops          root of every node, one coin per loop, new operator
-//                    flags, loop lengths (tile-local loops in shared
-//                    memory, others in global accumulators), next
-//                    operator list (offsets by decoupled look-back) [3, 4, 8]
-//   k_open           squared lengths of the loops that left their tile
+//   k_compress       root of every node, one coin per loop              [3]
+//   k_est            new operator flags, loop lengths (tile-local loops in
+//                    shared memory, others in global accumulators)      [4]
+//   k_scan_ops       operator offsets per tile
+//   k_compact        next operator list, squared lengths of open loops  [8]
 //   k_sites          spins at tau = 0, vertex-free loops                [8]
 //   k_final          per-chain record, running sums, buffer swap
 #include <cmath>
@@ -681,6 +681,52 @@ __device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict_
   }
 }
 
+// ---- per-chain scan of the tiles' new-operator counts ------------------------------
+__global__ void __launch_bounds__(1024) k_scan_ops(DevChain *__restrict__ ch, Scratch s) {
+  // Chunks of 4 x 1024 tiles: each thread loads four consecutive counts
+  // (coalesced across the warp), one block scan per chunk; the next chunk's
+  // loads are issued before the current chunk's scan.
+  __shared__ int64_t sm[33];
+  if (halted(s)) return;
+  DevChain &C = ch[blockIdx.x];
+  const int nt = C.ntile;
+  const int64_t *cnt = s.tile_sum2 + C.tile0;
+  int64_t *pref = s.tile_pref2 + C.tile0;
+  constexpr int V = 4;
+  const int chunk = V * (int)blockDim.x;
+  int64_t v[V], nx[V];
+  auto load = [&](int base, int64_t *x) {
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const int i = base + V * (int)threadIdx.x + k;
+      x[k] = (i < nt) ? cnt[i] : 0;
+    }
+  };
+  load(0, v);
+  int64_t run = 0;
+  for (int base = 0; base < nt; base += chunk) {
+    if (base + chunk < nt) load(base + chunk, nx);
+    int64_t mine = 0;
+#pragma unroll
+    for (int k = 0; k < V; ++k) mine += v[k];
+    int64_t total;
+    int64_t ex = run + block_excl_scan<int64_t>(mine, sm, total);
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const int i = base + V * (int)threadIdx.x + k;
+      if (i < nt) pref[i] = ex;
+      ex += v[k];
+    }
+    run += total;
+#pragma unroll
+    for (int k = 0; k < V; ++k) v[k] = nx[k];
+  }
+  if (threadIdx.x == 0) {
+    C.n_off_new = run;
+    if (run > C.op_cap) atomicOr(s.status, ST_OP_OVERFLOW);
+  }
+}
+
 // ---- tau = 0: last leg per subsite, subspin permutation, cut predecessors -----
 template <int Q>
 __device__ void last_leg(const DevChain &C, const int32_t *vp, const long long *vtau, int64_t vb,
@@ -891,8 +937,7 @@ __device__ __forceinline__ int time_lower_bound(const long long *vt, int lo, int
 // root, its smallest node.  Edges
 // that leave the tile are marked and united in the global forest by k_link_x,
 // after every tile has stored its forest (a tile too large for shared memory
-// leaves all of its edges to k_link_x, with every node its own root); both
-// nodes of such an edge get the open mark.
+// leaves all of its edges to k_link_x, with every node its own root).
 template <int Q>
 __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
                                               const int2 *__restrict__ tab, int64_t blk0,
@@ -990,9 +1035,7 @@ __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
     if (wrapbits) s.vflag[vb + w] |= wrapbits;
     const bool inside = P[0] >= a && P[0] < e && P[1] >= a && P[1] < e;
     if (!inside) {
-      // both nodes: the tile of each one's root learns that the loop is open
       set_bit(s.openmark, wb, P[0]);
-      if (P[1] != P[0]) set_bit(s.openmark, wb, P[1]);
       if (local && P[0] != P[1]) set_bit(s.xmark, wb, w);
     } else if (local && P[0] != P[1]) {
       suf_union(lp, P[0] - a, P[1] - a, nv, s.status);
@@ -1059,6 +1102,69 @@ __global__ void __launch_bounds__(TPB_X) k_link_x(const DevChain *__restrict__ c
       uf_union(par, s.pl[vb + w], s.pr[vb + w], s.status, s.uf_limit);
     }
   }
+}
+
+// ---- compression + coins --------------------------------------------------------
+__global__ void __launch_bounds__(TILE) k_compress(const DevChain *__restrict__ ch,
+                                                   const int2 *__restrict__ tab, int64_t blk0,
+                                                   Scratch s) {
+  __shared__ U4 coins[MAX_COIN_GROUPS];
+  __shared__ int64_t sm[33];
+  __shared__ int spar[SMEM_CAP];  // the tile's parent words: walks stay here until they leave it
+  if (halted(s)) return;
+  const int64_t gt = blk0 + blockIdx.x;
+  const int2 t = tab[gt];
+  const DevChain &C = ch[t.x];
+  const int c0 = t.y * TILE, c1 = min(C.ncell, c0 + TILE);
+  const int32_t *vp = s.vptr + C.cell_off;
+  const int a = vp[c0], e = vp[c1];
+  const int64_t vb = C.vtx_base, wb = vb >> 5;
+  int32_t *par = s.parent + vb;
+  const bool oversized = (e - a) > local_cap(C);
+  const int g0 = a >> 7;
+  const int ng = (e > a) ? ((e - 1) >> 7) - g0 + 1 : 0;
+  const uint32_t k0 = (uint32_t)C.seed, k1 = (uint32_t)(C.seed >> 32);
+  for (int g = threadIdx.x; g < ng && g < MAX_COIN_GROUPS; g += blockDim.x)
+    coins[g] = philox(TAG_FLIP << 24, (uint32_t)(g0 + g), 0u, C.sweep, k0, k1);
+  // Only this block writes parent words of [a, e) in this kernel, and every
+  // word it writes is an ancestor of the old one: the copy stays a valid forest.
+  if (!oversized)
+    for (int i = threadIdx.x; i < e - a; i += blockDim.x) spar[i] = __ldcg(par + a + i);
+  __syncthreads();
+  int64_t roots = 0;
+  for (int v0 = a; v0 < e; v0 += blockDim.x) {  // whole warps, reconverged per step
+    const int v = v0 + threadIdx.x;
+    if (v >= e) {
+      __syncwarp();
+      continue;
+    }
+    int r;
+    if (oversized) {
+      r = uf_root(par, v, s.status, s.uf_limit);
+    } else {
+      // parents are never larger than their children: the walk leaves the
+      // tile only downwards (below a), and then finishes in global memory
+      r = v;
+      int p = spar[v - a];
+      for (int it = 0; p != r && p >= a && it < SMEM_CAP; ++it) {
+        r = p;
+        p = spar[p - a];
+      }
+      if (p != r) r = uf_root(par, p, s.status, s.uf_limit);
+    }
+    if (r != v) par[v] = r;
+    if (r == v) {
+      ++roots;
+      const int g = (v >> 7) - g0;
+      const int cf = (g < MAX_COIN_GROUPS) ? coin_from(coins[g], (uint32_t)v) : coin(C, TAG_FLIP, v);
+      if (cf) set_bit(s.flipbits, wb, v);
+      if (oversized) set_bit(s.openroot, wb, v);
+    }
+    if (get_bit(s.openmark, wb, v)) set_bit(s.openroot, wb, r);
+    __syncwarp();
+  }
+  const int64_t tot = block_sum<int64_t>(roots, sm);
+  if (threadIdx.x == 0) s.tile_roots[gt] = tot;
 }
 
 // ---- opt-in check of the loop forest after compression ----------------------------
@@ -1148,63 +1254,29 @@ __device__ __forceinline__ void loop_squares(const long long *v, u128 &w2, u128 
   if (T) z2 += sq_abs(v[3]) + sq_abs(v[4]);
 }
 
+constexpr int TPB_EST = 256;
+// Vertices of a tile whose ticks (and phase factors) the loop-properties
+// kernel stages in shared memory; ticks beyond it are computed where needed.
+constexpr int EST_STAGE = 1536;
 
-// ---- loops: compression, coins, loop sums, new operators (one kernel) -----------
-// One block per tile, in four steps.
-//  A. Roots: the tile's parent words are copied to shared memory; every
-//     node's walk stays there until it leaves the tile downwards (parents are
-//     never larger than their children) and then finishes in the global
-//     forest.  The root is stored back (shared and global).  Each root of the
-//     tile draws its coin (one Philox block per 128 ids).  A root whose loop
-//     holds a node with the open mark (an edge of the loop leaves its tile)
-//     is marked open: its loop's sums are added up in global memory.
-//  B. Per vertex: the new operator flag (old flag xor the coins of the loops
-//     below and above the vertex) and the two fragments below it, whose
-//     lengths (in ticks of 2^-F) and Fourier parts go to the loop of the node
-//     they start at: squared at once for a loop of one node, else summed in a
-//     per-tile table keyed by root (split 32-bit shared atomics).  A root in
-//     another tile comes from a read-only walk of the global forest and its
-//     coin from its own Philox block (its tile may not have run yet).
-//  C. The table: loops closed in the tile are squared, the others added to
-//     their root's global record (squared by k_open once every tile has added).
-//  D. New operators: the tile's count gets its chain-local offset by
-//     decoupled look-back over the tiles before it (tile order = ticket
-//     order), then the next operator list's offsets and times are written.
-// A loop that leaves its root's tile always has a node in that tile with the
-// open mark (linking marks both nodes of every edge that leaves a tile, and
-// every node of a vertex's edge when the vertex sits in another tile), so
-// each tile decides open or closed for its own roots alone.
-constexpr int TPB_LOOPS = 256;
-// Vertices of a tile whose ticks (and phase factors) are staged in shared
-// memory; ticks beyond it are computed where needed.
-constexpr int EST_STAGE = 1504;
-
+// T: also the temporal moment (phase factors, Zr and Zi); off by default.
 template <int Q, bool T>
-__global__ void __launch_bounds__(TPB_LOOPS, T ? 5 : 6) k_loops(DevChain *__restrict__ ch,
-                                                               const int2 *__restrict__ tab,
-                                                               int64_t blk0, int group, Scratch s) {
-  constexpr int NS = T ? LOOP_SUMS : 3;  // sums carried per loop
+__global__ void __launch_bounds__(TPB_EST, T ? 6 : 8) k_est(const DevChain *__restrict__ ch,
+                                             const int2 *__restrict__ tab, int64_t blk0,
+                                             Scratch s) {
   __shared__ int lkeys[LOOP_SLOTS];
+  constexpr int NS = T ? LOOP_SUMS : 3;  // sums carried per loop
   __shared__ unsigned lvals[2 * NS * LOOP_SLOTS];
   __shared__ int cvp[TILE + 1];
   __shared__ int cnew[TILE];
   __shared__ long long ccl[TILE], csl[TILE], ccr[TILE], csr[TILE], cxl[TILE], cxr[TILE];
-  __shared__ int spar[SMEM_CAP];                 // A: parent words, then roots
-  __shared__ uint32_t sflip[SMEM_CAP / 32];      // coins of the tile's roots
-  __shared__ uint32_t snew[SMEM_CAP / 32 + 1];   // new operator flags of the tile's vertices
-  __shared__ U4 coins[MAX_COIN_GROUPS];
-  __shared__ int wtot[TPB_LOOPS / 32];
-  __shared__ int64_t sm[33];
-  __shared__ int64_t sgt, sbase;
-  extern __shared__ long long loops_dyn[];
-  long long *qv = loops_dyn;                   // ticks q(tau) of the tile's vertices
-  int2 *ev = (int2 *)(loops_dyn + EST_STAGE);  // their phase factors exp(i w1 tau)
+  extern __shared__ long long est_dyn[];
+  long long *qv = est_dyn;                   // ticks q(tau) of the tile's vertices
+  int2 *ev = (int2 *)(est_dyn + EST_STAGE);  // their phase factors exp(i w1 tau)
   if (halted(s)) return;
-  if (threadIdx.x == 0) sgt = blk0 + (int64_t)atomicAdd(s.tickets + QMAX + group, 1u);
-  __syncthreads();
-  const int64_t gt = sgt;
+  const int64_t gt = blk0 + blockIdx.x;
   const int2 t = tab[gt];
-  DevChain &C = ch[t.x];
+  const DevChain &C = ch[t.x];
   const int c0 = t.y * TILE, c1 = min(C.ncell, c0 + TILE), ncl = c1 - c0;
   const int32_t *vp = s.vptr + C.cell_off;
   for (int i = threadIdx.x; i <= ncl; i += blockDim.x) cvp[i] = vp[c0 + i];
@@ -1227,89 +1299,35 @@ __global__ void __launch_bounds__(TPB_LOOPS, T ? 5 : 6) k_loops(DevChain *__rest
 #pragma unroll
     for (int k = 0; k < 2 * NS; ++k) lvals[2 * NS * i + k] = 0u;
   }
-  for (int i = threadIdx.x; i <= SMEM_CAP / 32; i += blockDim.x) {
-    snew[i] = 0u;
-    if (i < SMEM_CAP / 32) sflip[i] = 0u;
-  }
   __syncthreads();
-  const int a = cvp[0], e = cvp[ncl], nv = e - a;
+  const int a = cvp[0], e = cvp[ncl];
   const int64_t vb = C.vtx_base, wb = vb >> 5;
-  int32_t *par = s.parent + vb;
-  const bool local = nv <= local_cap(C);
-  const uint32_t k0 = (uint32_t)C.seed, k1 = (uint32_t)(C.seed >> 32);
-  const int g0 = a >> 7;
-  const int ng = (e > a) ? ((e - 1) >> 7) - g0 + 1 : 0;
-  for (int g = threadIdx.x; g < ng && g < MAX_COIN_GROUPS; g += blockDim.x)
-    coins[g] = philox(TAG_FLIP << 24, (uint32_t)(g0 + g), 0u, C.sweep, k0, k1);
-  if (local)
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) spar[i] = __ldcg(par + a + i);
+  const int32_t *par = s.parent + vb;
   const uint64_t *vt = (const uint64_t *)s.vtau + vb;
   const int F = C.F;
+  // Ticks of every vertex of the tile, once: the fragments below a vertex
+  // mostly start at vertices of the same tile.
+  // Their phase factors too (temporal moment, w1 = 2 pi / beta).
   const uint64_t phR = C.phR;
   const int phS = C.phS;
-  const int nq = min(min(nv, local_cap(C)), EST_STAGE);
+  const int nq = min(min(e - a, local_cap(C)), EST_STAGE);
+  const unsigned slot_mask =
+      (C.loop_slots > 0 && C.loop_slots <= LOOP_SLOTS && !(C.loop_slots & (C.loop_slots - 1)))
+          ? (unsigned)C.loop_slots - 1u
+          : (unsigned)LOOP_SLOTS - 1u;
   for (int i = threadIdx.x; i < nq; i += blockDim.x) {
     const long long q = q_time(vt[a + i], F);
     qv[i] = q;
     if (T) ev[i] = phase_of((uint64_t)q, phR, phS, g_phase_tab);
   }
   __syncthreads();
-
-  // -- A: roots, coins, open marks ---------------------------------------------
-  volatile int *vsp = spar;
-  int64_t roots = 0;
-  for (int v0 = a; v0 < e; v0 += blockDim.x) {  // whole warps, reconverged per step
-    const int v = v0 + threadIdx.x;
-    if (v >= e) {
-      __syncwarp();
-      continue;
-    }
-    int r;
-    if (!local) {
-      r = uf_root(par, v, s.status, s.uf_limit);
-    } else {
-      r = v;
-      int p = vsp[v - a];
-      for (int it = 0; p != r && p >= a && it < SMEM_CAP; ++it) {
-        r = p;
-        p = vsp[p - a];
-      }
-      if (p != r) r = uf_root(par, p, s.status, s.uf_limit);
-      vsp[v - a] = r;  // an ancestor: walks of other nodes stay valid
-    }
-    if (r != v) par[v] = r;
-    if (r == v) {
-      ++roots;
-      const int g = (v >> 7) - g0;
-      const int cf = (g < MAX_COIN_GROUPS) ? coin_from(coins[g], (uint32_t)v) : coin(C, TAG_FLIP, v);
-      if (cf) {
-        set_bit(s.flipbits, wb, v);
-        if (local) atomicOr(sflip + ((v - a) >> 5), 1u << ((v - a) & 31));
-      }
-      if (!local) set_bit(s.openroot, wb, v);
-    }
-    if (r >= a && get_bit(s.openmark, wb, v)) set_bit(s.openroot, wb, r);
-    __syncwarp();
-  }
-  __syncthreads();
-
-  // -- B: new flags, fragment sums ---------------------------------------------
   auto inq = [&](int v) { return v >= a && v < a + nq; };
   auto ticks = [&](int v) { return inq(v) ? qv[v - a] : q_time(vt[v], F); };
   auto phase = [&](int v) {
     return inq(v) ? ev[v - a] : phase_of((uint64_t)q_time(vt[v], F), phR, phS, g_phase_tab);
   };
-  auto root_of = [&](int v) {
-    return (local && v >= a && v < e) ? vsp[v - a] : uf_root(par, v, s.status, s.uf_limit);
-  };
-  auto flip_of = [&](int r) {
-    return (local && r >= a && r < e) ? (int)((sflip[(r - a) >> 5] >> ((r - a) & 31)) & 1u)
-                                      : coin(C, TAG_FLIP, (uint32_t)r);
-  };
-  const unsigned slot_mask =
-      (C.loop_slots > 0 && C.loop_slots <= LOOP_SLOTS && !(C.loop_slots & (C.loop_slots - 1)))
-          ? (unsigned)C.loop_slots - 1u
-          : (unsigned)LOOP_SLOTS - 1u;
+  // Whole warps walk the tile (trip count rounded up), reconverging after
+  // every vertex.
   u128 w2 = 0, f2 = 0, z2 = 0;  // this thread's share of the loops' squared sums
   for (int w0 = a; w0 < e; w0 += blockDim.x) {
     const int w = w0 + threadIdx.x;
@@ -1319,13 +1337,10 @@ __global__ void __launch_bounds__(TPB_LOOPS, T ? 5 : 6) k_loops(DevChain *__rest
       const uint8_t f = s.vflag[vb + w];
       // a node whose two upper legs both end at w is a loop by itself: its
       // own root
-      const int rb = (P == R) ? P : root_of(P), ra = root_of(w);
-      const int nf = (f & VF_OLD) ^ flip_of(rb) ^ flip_of(ra);
+      const int rb = (P == R) ? P : __ldcg(par + P), ra = __ldcg(par + w);
+      const int nf = (f & VF_OLD) ^ get_bit(s.flipbits, wb, rb) ^ get_bit(s.flipbits, wb, ra);
       s.vflag[vb + w] = (uint8_t)(f | (nf ? VF_NEW : 0));
-      if (nf) {
-        atomicAdd(cnew + ci, 1);
-        if (local) atomicOr(snew + ((w - a) >> 5), 1u << ((w - a) & 31));  // nv <= SMEM_CAP
-      }
+      if (nf) atomicAdd(cnew + ci, 1);
       // fragment lengths in ticks of 2^-F: q(tau_top) - q(tau_bottom) (+ crossings)
       const long long qw = ticks(w);
       const long long qP = ticks(P);
@@ -1356,101 +1371,29 @@ __global__ void __launch_bounds__(TPB_LOOPS, T ? 5 : 6) k_loops(DevChain *__rest
     __syncwarp();
   }
   __syncthreads();
-
-  // -- C: the loop table ---------------------------------------------------------
+  long long newcnt = 0;
+  if (threadIdx.x < ncl) {
+    newcnt = cnew[threadIdx.x];
+    C.op_ptr[C.cur ^ 1][c0 + threadIdx.x] = (int32_t)newcnt;
+  }
+  // A loop closed in the tile is complete in its slot: square it here.  A loop
+  // that leaves the tile adds its slot to the root's global record, squared
+  // once every tile has added (next operator list kernel).
   for (int h = threadIdx.x; h < LOOP_SLOTS; h += blockDim.x) {
     const int kk = lkeys[h];
     if (kk < 0) continue;
     long long v[LOOP_SUMS] = {};
 #pragma unroll
     for (int i = 0; i < NS; ++i) v[i] = (long long)sget64(lvals + 2 * (NS * h + i));
-    if (kk < a || kk >= e || get_bit(s.openroot, wb, kk)) {
+    if (get_bit(s.openroot, wb, kk)) {
       acc_add<NS>(s, vb + kk, v);
     } else {
       loop_squares<T>(v, w2, f2, z2);
     }
   }
-
-  // -- D: new operators ------------------------------------------------------------
-  const int cc = (threadIdx.x < ncl) ? cnew[threadIdx.x] : 0;
-  int64_t ntot;
-  const int64_t cex = block_excl_scan<int64_t>((int64_t)cc, sm, ntot);
-  if (threadIdx.x < 32) {
-    int64_t excl = 0;
-    if (t.y == 0) {
-      if (threadIdx.x == 0) lb_publish(s.tile_state2, gt, LB_INC, ntot);
-    } else {
-      if (threadIdx.x == 0) lb_publish(s.tile_state2, gt, LB_AGG, ntot);
-      __syncwarp();
-      excl = lb_lookback(s.tile_state2, gt, gt - t.y, s);
-      if (threadIdx.x == 0) lb_publish(s.tile_state2, gt, LB_INC, excl + ntot);
-    }
-    if (threadIdx.x == 0) {
-      sbase = excl;
-      if (t.y == C.ntile - 1) {
-        C.n_off_new = excl + ntot;
-        if (excl + ntot > C.op_cap) atomicOr(s.status, ST_OP_OVERFLOW);
-      }
-    }
-  }
-  __syncthreads();
-  const int64_t base = sbase;
-  int32_t *nptr = C.op_ptr[C.cur ^ 1];
-  double *ntau = C.op_tau[C.cur ^ 1];
-  if (threadIdx.x < ncl) {
-    nptr[c0 + threadIdx.x] = (int32_t)(base + cex);
-    if (c0 + (int)threadIdx.x == C.ncell - 1) nptr[C.ncell] = (int32_t)(base + ntot);
-  }
-  if (base + ntot <= C.op_cap) {
-    // times of the new operators in id order: each warp takes a contiguous
-    // range of flag words, counts, then places with a warp scan
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = TPB_LOOPS / 32;
-    const int nwords = local ? (nv + 31) >> 5 : 0;
-    const int per = (nwords + nw - 1) / nw;
-    const int ww0 = min(nwords, wid * per), ww1 = min(nwords, ww0 + per);
-    int cnt = 0;
-    for (int wd = ww0 + lane; wd < ww1; wd += 32) cnt += __popc(snew[wd]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    if (lane == 0) wtot[wid] = cnt;
-    __syncthreads();
-    if (local) {
-      int64_t pos = base;
-      for (int k = 0; k < wid; ++k) pos += wtot[k];
-      for (int s0 = ww0; s0 < ww1; s0 += 32) {
-        const int wd = s0 + lane;
-        uint32_t m = (wd < ww1) ? snew[wd] : 0u;
-        const int c = __popc(m);
-        int inc = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, inc, o);
-          if (lane >= o) inc += y;
-        }
-        int64_t p = pos + inc - c;
-        while (m) {
-          const int i = __ffs(m) - 1;
-          m &= m - 1;
-          ntau[p++] = s.vtau[vb + a + 32 * wd + i];
-        }
-        pos += __shfl_sync(0xffffffffu, inc, 31);
-      }
-    } else if (threadIdx.x < 32) {
-      // a tile above the cap keeps no flag words: one warp reads the flags
-      int64_t pos = base;
-      for (int w0 = a; w0 < e; w0 += 32) {
-        const int w = w0 + lane;
-        const bool isnew = w < e && (s.vflag[vb + w] & VF_NEW);
-        const unsigned m = __ballot_sync(0xffffffffu, isnew);
-        if (isnew) ntau[pos + __popc(m & ((1u << lane) - 1u))] = s.vtau[vb + w];
-        pos += __popc(m);
-      }
-    }
-  }
-  long long nroot = roots;
-  block_sums<T>(nroot, w2, f2, z2);
+  block_sums<T>(newcnt, w2, f2, z2);
   if (threadIdx.x == 0) {
-    s.tile_roots[gt] = nroot;
+    s.tile_sum2[gt] = newcnt;
     s.tile_sw2[2 * gt] = (unsigned long long)w2;
     s.tile_sw2[2 * gt + 1] = (unsigned long long)(w2 >> 64);
     s.tile_sf2[2 * gt] = (unsigned long long)f2;
@@ -1460,29 +1403,86 @@ __global__ void __launch_bounds__(TPB_LOOPS, T ? 5 : 6) k_loops(DevChain *__rest
   }
 }
 
-// ---- open loops ------------------------------------------------------------------
-// Loops that left their tile: one 32-byte accumulator record per root (and
-// its Zi word), read, squared and cleared; a warp takes one tile, a lane one
-// 32-vertex word of the open-root bitmap at a time.  With the Zi words, the
-// next root's reads are issued before the current root is cleared (two roots
-// in flight per thread); without them, the plain loop needs fewer registers.
-// The squares are added to the tile's sums.
+// ---- next operator list + open loops -------------------------------------------------
+// The tile's flags are read as aligned 32-bit words (four vertices each).
+// Each warp takes a contiguous range of words: a first pass counts its new
+// operators, one barrier exchanges the warp totals, and a second pass places
+// them with warp shuffles (id order = order of the next operator list).  The
+// cell offsets come from a block scan of the per-cell counts.
 template <bool T>
-__global__ void __launch_bounds__(256) k_open(const DevChain *__restrict__ ch,
-                                              const int2 *__restrict__ tab, int64_t ntiles, Scratch s) {
+__global__ void __launch_bounds__(TPB, T ? 4 : 8) k_compact(const DevChain *__restrict__ ch,
+                                                 const int2 *__restrict__ tab, int64_t blk0,
+                                                 Scratch s) {
+  __shared__ int64_t sm[33];
+  __shared__ int wtot[TPB / 32];
   if (halted(s)) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t gt = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (gt >= ntiles) return;
+  const int64_t gt = blk0 + blockIdx.x;
   const int2 t = tab[gt];
   const DevChain &C = ch[t.x];
-  const int c0 = t.y * TILE, c1 = min(C.ncell, c0 + TILE);
+  const int c0 = t.y * TILE, c1 = min(C.ncell, c0 + TILE), ncl = c1 - c0;
+  int32_t *nptr = C.op_ptr[C.cur ^ 1];
+  double *ntau = C.op_tau[C.cur ^ 1];
   const int32_t *vp = s.vptr + C.cell_off;
-  const int a = vp[c0], e = vp[c1];
   const int64_t vb = C.vtx_base;
+  const int64_t base = s.tile_pref2[gt];
+  const int a = vp[c0], e = vp[c1];
+  const uint8_t *vf = s.vflag + vb;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = TPB / 32;
+  // words [wa, we) of four flags; warp wid takes [wa + wid*per, ...)
+  const int wa = a >> 2, we = (e + 3) >> 2;
+  const int per = (we - wa + nw - 1) / nw;
+  const int ww0 = min(we, wa + wid * per), ww1 = min(we, ww0 + per);
+  auto newmask = [&](int wd) {  // bit i: vertex 4*wd + i is a new operator of this tile
+    const uint32_t fl = *(const uint32_t *)(vf + 4 * wd);  // vb and 4*wd are multiples of 4
+    int m = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int w = 4 * wd + i;
+      if (w >= a && w < e && ((fl >> (8 * i)) & VF_NEW)) m |= 1 << i;
+    }
+    return m;
+  };
+  int cnt = 0;
+  for (int wd = ww0 + lane; wd < ww1; wd += 32) cnt += __popc(newmask(wd));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0) wtot[wid] = cnt;
+  {
+    const int cc = (threadIdx.x < ncl) ? nptr[c0 + threadIdx.x] : 0;
+    int64_t tot;
+    const int64_t ex = block_excl_scan<int64_t>((int64_t)cc, sm, tot);  // also publishes wtot
+    if (threadIdx.x < ncl) {
+      nptr[c0 + threadIdx.x] = (int32_t)(base + ex);
+      if (c0 + (int)threadIdx.x == C.ncell - 1) nptr[C.ncell] = (int32_t)C.n_off_new;
+    }
+  }
+  int64_t pos = base;
+  for (int k = 0; k < wid; ++k) pos += wtot[k];
+  for (int s0 = ww0; s0 < ww1; s0 += 32) {
+    const int wd = s0 + lane;
+    const int m = (wd < ww1) ? newmask(wd) : 0;
+    const int c = __popc(m);
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    int64_t p = pos + inc - c;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (m & (1 << i)) ntau[p++] = s.vtau[vb + 4 * wd + i];
+    pos += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  // Loops that left their tile: one 32-byte accumulator record per root (and
+  // its Zi word), read and cleared; a thread takes one 32-vertex word of the
+  // open-root bitmap.  With the Zi words, the next root's reads are issued
+  // before the current root is cleared (two roots in flight per thread);
+  // without them, the plain loop needs fewer registers and more resident
+  // warps hide the latency better.
   u128 w2 = 0, f2 = 0, z2 = 0;
   const int64_t wfirst = (vb + a) >> 5, wlast = (vb + e - 1) >> 5;
-  for (int64_t wd = wfirst + lane; e > a && wd <= wlast; wd += 32) {
+  for (int64_t wd = wfirst + threadIdx.x; e > a && wd <= wlast; wd += blockDim.x) {
     uint32_t bits = __ldcg(s.openroot + wd);
     const int64_t v0 = (wd << 5) - vb;
     if (v0 < a) bits &= ~0u << (a - v0);
@@ -1529,18 +1529,14 @@ __global__ void __launch_bounds__(256) k_open(const DevChain *__restrict__ ch,
       zi = zn;
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    w2 += shfl_down_u128(w2, o);
-    f2 += shfl_down_u128(f2, o);
-    if (T) z2 += shfl_down_u128(z2, o);
-  }
-  if (lane == 0) {
-    auto add = [&](unsigned long long *tt, u128 v) {
-      u128 x = ((u128)tt[2 * gt + 1] << 64) | tt[2 * gt];
+  long long none = 0;
+  block_sums<T>(none, w2, f2, z2);
+  if (threadIdx.x == 0) {
+    auto add = [&](unsigned long long *t, u128 v) {
+      u128 x = ((u128)t[2 * gt + 1] << 64) | t[2 * gt];
       x += v;
-      tt[2 * gt] = (unsigned long long)x;
-      tt[2 * gt + 1] = (unsigned long long)(x >> 64);
+      t[2 * gt] = (unsigned long long)x;
+      t[2 * gt + 1] = (unsigned long long)(x >> 64);
     };
     add(s.tile_sw2, w2);
     add(s.tile_sf2, f2);
@@ -1707,6 +1703,9 @@ void launch_insert(const Launch &L, cudaStream_t st) {
 #undef INSERT_Q
 }
 
+void launch_scan_ops(const Launch &L, cudaStream_t st) {
+  k_scan_ops<<<L.nchains, 1024, 0, st>>>(L.ch, L.s);
+}
 
 void launch_cut(const Launch &L, cudaStream_t st) {
 #define CUT_Q(Q) \
@@ -1726,18 +1725,22 @@ void launch_link(const Launch &L, cudaStream_t st) {
   if (n) k_link_x<<<g1((n + wpb - 1) / wpb), 32 * wpb, 0, st>>>(L.ch, L.tile_tab, n, L.s);
 }
 
+void launch_compress(const Launch &L, cudaStream_t st) {
+  const int64_t n = all_tiles(L);
+  if (n) k_compress<<<g1(n), L.compress_threads, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
+}
 
 void launch_check_forest(const Launch &L, cudaStream_t st) {
   const int64_t n = all_tiles(L);
   if (n) k_check_forest<<<g1(n), TILE, 0, st>>>(L.ch, L.tile_tab, L.s);
 }
 
-// Per-vertex staging of the loops kernel: ticks and phase factors.
-constexpr size_t LOOPS_DYN_SMEM = EST_STAGE * (sizeof(long long) + sizeof(int2));
+// Per-vertex staging of the loop-properties kernel: ticks and phase factors.
+constexpr size_t EST_DYN_SMEM = EST_STAGE * (sizeof(long long) + sizeof(int2));
 
 // Device tables and kernel attributes, set once per process and device: the
 // phase factor table (cos and sin of 2 pi k / 2^16 rounded to 30 fractional
-// bits) and the loops kernel's shared memory size.
+// bits) and the loop-properties kernel's shared memory size.
 int init_kernel_attributes() {
   static std::mutex mu;
   static bool done[256];
@@ -1752,14 +1755,12 @@ int init_kernel_attributes() {
                        (int)std::llrint(std::ldexp(std::sin(ang), 30)));
   }
   if (cudaMemcpyToSymbol(g_phase_tab, tab, sizeof(tab)) != cudaSuccess) return -1;
-#define LOOPS_ATTR_Q(Q)                                                                  \
-  if (cudaFuncSetAttribute(k_loops<Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                           (int)LOOPS_DYN_SMEM) != cudaSuccess ||                          \
-      cudaFuncSetAttribute(k_loops<Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                           (int)LOOPS_DYN_SMEM) != cudaSuccess)                            \
+#define EST_ATTR_Q(Q)                                                                 \
+  if (cudaFuncSetAttribute(k_est<Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                           (int)EST_DYN_SMEM) != cudaSuccess)                           \
     return -1;
-  FOR_EACH_Q(LOOPS_ATTR_Q)
-#undef LOOPS_ATTR_Q
+  FOR_EACH_Q(EST_ATTR_Q)
+#undef EST_ATTR_Q
   if (cudaFuncSetAttribute(k_insert<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sizeof(InsSmem<3>)) != cudaSuccess ||
       cudaFuncSetAttribute(k_insert<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1769,30 +1770,27 @@ int init_kernel_attributes() {
   return 0;
 }
 
-void launch_loops(const Launch &L, cudaStream_t st) {
+void launch_est(const Launch &L, cudaStream_t st) {
   // without the temporal moment only the ticks are staged
-  const size_t dyn = L.temporal ? LOOPS_DYN_SMEM : EST_STAGE * sizeof(long long);
-#define LOOPS_Q(Q)                                                                             \
-  if (L.ntile[Q - 1]) {                                                                        \
-    if (L.temporal)                                                                            \
-      k_loops<Q, true><<<g1(L.ntile[Q - 1]), TPB_LOOPS, dyn, st>>>(L.ch, L.tile_tab, L.tile0[Q - 1], \
-                                                                   Q - 1, L.s);                \
-    else                                                                                       \
-      k_loops<Q, false><<<g1(L.ntile[Q - 1]), TPB_LOOPS, dyn, st>>>(L.ch, L.tile_tab,          \
-                                                                    L.tile0[Q - 1], Q - 1, L.s); \
+  const size_t dyn = L.temporal ? EST_DYN_SMEM : EST_STAGE * sizeof(long long);
+#define EST_Q(Q)                                                                                       \
+  if (L.ntile[Q - 1]) {                                                                                \
+    if (L.temporal)                                                                                    \
+      k_est<Q, true><<<g1(L.ntile[Q - 1]), TPB_EST, dyn, st>>>(L.ch, L.tile_tab, L.tile0[Q - 1], L.s);  \
+    else                                                                                               \
+      k_est<Q, false><<<g1(L.ntile[Q - 1]), TPB_EST, dyn, st>>>(L.ch, L.tile_tab, L.tile0[Q - 1], L.s); \
   }
-  FOR_EACH_Q(LOOPS_Q)
-#undef LOOPS_Q
+  FOR_EACH_Q(EST_Q)
+#undef EST_Q
 }
 
-void launch_open(const Launch &L, cudaStream_t st) {
+void launch_compact(const Launch &L, cudaStream_t st) {
   const int64_t n = all_tiles(L);
-  const int wpb = L.open_threads / 32;
   if (n) {
     if (L.temporal)
-      k_open<true><<<g1((n + wpb - 1) / wpb), 32 * wpb, 0, st>>>(L.ch, L.tile_tab, n, L.s);
+      k_compact<true><<<g1(n), TPB, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
     else
-      k_open<false><<<g1((n + wpb - 1) / wpb), 32 * wpb, 0, st>>>(L.ch, L.tile_tab, n, L.s);
+      k_compact<false><<<g1(n), TPB, 0, st>>>(L.ch, L.tile_tab, 0, L.s);
   }
 }
 

@@ -19,7 +19,7 @@ struct Launch {
   // block sizes of the union-find phases (any choice gives the same results)
   int link_threads = 256;     // k_link: 128 or 256
   int link_x_warps = 8;       // k_link_x: 1 .. 8 warps (one tile each) per block
-  int open_threads = 128;     // k_open: 32 .. 256 in steps of 32 (a warp per tile)
+  int compress_threads = 128; // k_compress: 32, 64, 96 or 128
   int check_forest = 0;       // verify the loop forest after compression (debug)
 };
 
@@ -27,11 +27,13 @@ void set_full_table(const uint64_t *T, cudaStream_t st);
 int init_kernel_attributes();
 void launch_bond_parity(const Launch &L, cudaStream_t st);
 void launch_insert(const Launch &L, cudaStream_t st);
+void launch_scan_ops(const Launch &L, cudaStream_t st);
 void launch_cut(const Launch &L, cudaStream_t st);
 void launch_link(const Launch &L, cudaStream_t st);
+void launch_compress(const Launch &L, cudaStream_t st);
 void launch_check_forest(const Launch &L, cudaStream_t st);
-void launch_loops(const Launch &L, cudaStream_t st);
-void launch_open(const Launch &L, cudaStream_t st);
+void launch_est(const Launch &L, cudaStream_t st);
+void launch_compact(const Launch &L, cudaStream_t st);
 void launch_sites(const Launch &L, cudaStream_t st);
 void launch_final(const Launch &L, cudaStream_t st);
 

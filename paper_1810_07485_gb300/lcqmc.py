@@ -17,8 +17,8 @@ PENDING = 1
 ERRORS = {-1: "E_INVAL", -2: "E_NOMEM", -3: "E_TOO_LARGE", -4: "E_ID_OVERFLOW",
           -5: "E_DEVICE_TIMEOUT", -6: "E_CUDA", -7: "E_STATE", -8: "E_NOT_FOUND",
           -9: "E_CANCELLED", -10: "E_CAPACITY"}
-NPHASE = 6
-PHASES = ["insert", "cut", "link_union", "loops", "open_loops", "spin_rewrite"]
+NPHASE = 8
+PHASES = ["insert", "cut", "link_union", "loop_ids", "loop_props", "op_offsets", "op_rewrite", "spin_rewrite"]
 
 
 class LcqmcError(RuntimeError):
@@ -38,11 +38,11 @@ class Obs(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("link_threads", ctypes.c_int32), ("link_x_warps", ctypes.c_int32),
-                ("open_threads", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("compress_threads", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
     def as_dict(self):
         return {"link_threads": self.link_threads, "link_x_warps": self.link_x_warps,
-                "open_threads": self.open_threads}
+                "compress_threads": self.compress_threads}
 
 
 SW_NOBS = 4  # energy per site, sum_c |c|^2 / N, M^2 / N, |M| / N
@@ -325,9 +325,9 @@ class Chain:
         _check(lib().lcqmc_get_tuning(self.h, ctypes.byref(t)))
         return t.as_dict()
 
-    def set_tuning(self, link_threads=256, link_x_warps=8, open_threads=128):
+    def set_tuning(self, link_threads=256, link_x_warps=8, compress_threads=128):
         _check(lib().lcqmc_set_tuning(self.h, ctypes.byref(Tuning(link_threads, link_x_warps,
-                                                                  open_threads, 0))))
+                                                                  compress_threads, 0))))
 
     def autotune(self, updates_per_trial=2):
         t = Tuning()
@@ -379,9 +379,9 @@ class Batch:
         _check(lib().lcqmc_batch_get_tuning(self.h, ctypes.byref(t)))
         return t.as_dict()
 
-    def set_tuning(self, link_threads=256, link_x_warps=8, open_threads=128):
+    def set_tuning(self, link_threads=256, link_x_warps=8, compress_threads=128):
         _check(lib().lcqmc_batch_set_tuning(self.h, ctypes.byref(Tuning(link_threads, link_x_warps,
-                                                                        open_threads, 0))))
+                                                                        compress_threads, 0))))
 
     def autotune(self, updates_per_trial=1):
         t = Tuning()

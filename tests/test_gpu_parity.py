@@ -306,9 +306,9 @@ def test_tuning_gives_identical_results():
     L, beta = 1024, 40.0
     a = lc.Chain(L, beta, seed=3)
     b = lc.Chain(L, beta, seed=3)
-    assert a.tuning() == {"link_threads": 256, "link_x_warps": 8, "open_threads": 128}
-    b.set_tuning(link_threads=128, link_x_warps=2, open_threads=64)
-    assert b.tuning() == {"link_threads": 128, "link_x_warps": 2, "open_threads": 64}
+    assert a.tuning() == {"link_threads": 256, "link_x_warps": 8, "compress_threads": 128}
+    b.set_tuning(link_threads=128, link_x_warps=2, compress_threads=64)
+    assert b.tuning() == {"link_threads": 128, "link_x_warps": 2, "compress_threads": 64}
     a.update(10)
     b.update(10)
     assert np.array_equal(a.records(), b.records())
@@ -316,18 +316,18 @@ def test_tuning_gives_identical_results():
     with pytest.raises(lc.LcqmcError):
         b.set_tuning(link_threads=192)
     with pytest.raises(lc.LcqmcError):
-        b.set_tuning(open_threads=288)
-    # autotune: 9 trials of 2 ordinary updates; the chain goes on as an
-    # untuned chain advanced by the same 18 updates
+        b.set_tuning(compress_threads=160)
+    # autotune: 8 trials of 2 ordinary updates; the chain goes on as an
+    # untuned chain advanced by the same 16 updates
     c = lc.Chain(L, beta, seed=3)
     t = c.autotune(2)
-    assert t["link_threads"] in (128, 256) and t["link_x_warps"] in (2, 4, 8) and t["open_threads"] in (64, 128, 256)
+    assert t["link_threads"] in (128, 256) and t["link_x_warps"] in (2, 4, 8) and t["compress_threads"] in (64, 128)
     d = lc.Chain(L, beta, seed=3)
-    d.update(18)
+    d.update(16)
     c.update(5)
     d.update(5)
     rc, rd = c.records(), d.records()
-    assert len(rc) == len(rd) == 23 and np.array_equal(rc, rd)
+    assert len(rc) == len(rd) == 21 and np.array_equal(rc, rd)
     assert_state_equal(gpu_state(c), gpu_state(d))
     for h in (a, b, c, d):
         h.close()
