@@ -1128,8 +1128,16 @@ __global__ void __launch_bounds__(TILE) k_compress(const DevChain *__restrict__ 
     coins[g] = philox(TAG_FLIP << 24, (uint32_t)(g0 + g), 0u, C.sweep, k0, k1);
   // Only this block writes parent words of [a, e) in this kernel, and every
   // word it writes is an ancestor of the old one: the copy stays a valid forest.
-  if (!oversized)
-    for (int i = threadIdx.x; i < e - a; i += blockDim.x) spar[i] = __ldcg(par + a + i);
+  // Words that point out of the tile (parents are never larger than their
+  // children, so outside means below a) are resolved first, each with one
+  // global walk to its root, so that the nodes walking through them share
+  // that walk; every other walk then stays in shared memory.
+  if (!oversized) {
+    for (int i = threadIdx.x; i < e - a; i += blockDim.x) {
+      const int p = __ldcg(par + a + i);
+      spar[i] = (p < a) ? uf_root(par, p, s.status, s.uf_limit) : p;
+    }
+  }
   __syncthreads();
   int64_t roots = 0;
   for (int v0 = a; v0 < e; v0 += blockDim.x) {  // whole warps, reconverged per step
@@ -1142,15 +1150,14 @@ __global__ void __launch_bounds__(TILE) k_compress(const DevChain *__restrict__ 
     if (oversized) {
       r = uf_root(par, v, s.status, s.uf_limit);
     } else {
-      // parents are never larger than their children: the walk leaves the
-      // tile only downwards (below a), and then finishes in global memory
+      // the walk ends at a root of the tile, or at a resolved outside root
       r = v;
       int p = spar[v - a];
       for (int it = 0; p != r && p >= a && it < SMEM_CAP; ++it) {
         r = p;
         p = spar[p - a];
       }
-      if (p != r) r = uf_root(par, p, s.status, s.uf_limit);
+      if (p != r) r = (p < a) ? p : uf_root(par, p, s.status, s.uf_limit);
     }
     if (r != v) par[v] = r;
     if (r == v) {
