@@ -137,27 +137,6 @@ __device__ void block_sums(long long &c, u128 &x, u128 &y, u128 &z) {
 
 __device__ __forceinline__ bool halted(const Scratch &s) { return __ldcg(s.status) != 0; }
 
-// First index q in [lo, hi) with a[q] >= thr (a ascending).  Ranges shorter
-// than 16, the usual case, take four fixed halving steps (the same count for
-// every lane of a warp); longer ones a plain binary search.
-__device__ __forceinline__ int lower_bound16(const long long *a, int lo, int hi, long long thr) {
-  if (hi - lo < 16) {
-    int pos = lo;  // a[q] < thr for every q < pos
-#pragma unroll
-    for (int h = 8; h > 0; h >>= 1)
-      if (pos + h <= hi && a[pos + h - 1] < thr) pos += h;
-    return pos;
-  }
-  while (lo < hi) {
-    const int mid = lo + ((hi - lo) >> 1);  // no overflow near 2^31
-    if (a[mid] < thr)
-      lo = mid + 1;
-    else
-      hi = mid;
-  }
-  return lo;
-}
-
 // Tile blocks of the vertex-parallel kernels: TPB threads walk the tile's
 // vertices in id order (coalesced); a vertex's cell comes from a binary search
 // in the tile's cell offsets staged in shared memory.
@@ -342,7 +321,15 @@ struct InsSmem {
 __device__ __forceinline__ int ops_before(const long long *__restrict__ tq, int lo, int hi,
                                           long long tau, int bb, int b) {
   const long long thr = tau + (bb < b ? 1 : 0);  // t < thr  <=>  (t, bb) < (tau, b)
-  return lower_bound16(tq, lo, hi, thr) - lo;
+  const int base = lo;
+  while (lo < hi) {
+    const int mid = lo + ((hi - lo) >> 1);  // no overflow near 2^31
+    if (tq[mid] < thr)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo - base;
 }
 
 // Time of a candidate, tau = fma(d, u53 2^-53, t0) (one IEEE fused
@@ -456,7 +443,13 @@ __device__ void ins_write(const DevChain &C, InsSmem<Q> &S, const OpView &V, int
     int lo = S.q[c], hi = S.q[c + 1];
     const int q0 = lo;
     const long long *otau = V.range(lo, hi);
-    lo = lower_bound16(otau, lo, hi, tau + 1);  // times are bit patterns: t <= tau <=> t < tau + 1
+    while (lo < hi) {
+      const int mid = lo + ((hi - lo) >> 1);  // no overflow near 2^31
+      if (otau[mid] <= tau)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
     r += lo - q0;
     const int64_t pos = base + S.cex[c] + r;
     vt[pos] = tau;
@@ -928,7 +921,14 @@ __device__ __forceinline__ void suf_union(int *lp, int a, int b, int bound, int 
 // ids are all below w or all above it, "key (tau, id) below (tw, w)" is
 // vt[q] < tw + 1 or vt[q] < tw respectively.
 __device__ __forceinline__ int time_lower_bound(const long long *vt, int lo, int hi, long long thr) {
-  return lower_bound16(vt, lo, hi, thr);
+  while (lo < hi) {
+    const int mid = lo + ((hi - lo) >> 1);  // no overflow near 2^31
+    if (vt[mid] < thr)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
 }
 
 // Linking, then the union of the two fragments below every vertex.  Edges
@@ -1416,15 +1416,12 @@ __global__ void __launch_bounds__(TPB_EST, T ? 6 : 8) k_est(const DevChain *__re
 // operators, one barrier exchanges the warp totals, and a second pass places
 // them with warp shuffles (id order = order of the next operator list).  The
 // cell offsets come from a block scan of the per-cell counts.
-constexpr int OPEN_LIST = 1024;  // open roots of a tile listed in shared memory
-
 template <bool T>
 __global__ void __launch_bounds__(TPB, T ? 4 : 8) k_compact(const DevChain *__restrict__ ch,
                                                  const int2 *__restrict__ tab, int64_t blk0,
                                                  Scratch s) {
   __shared__ int64_t sm[33];
   __shared__ int wtot[TPB / 32];
-  __shared__ int olist[OPEN_LIST];  // the tile's open roots (chain-local ids)
   if (halted(s)) return;
   const int64_t gt = blk0 + blockIdx.x;
   const int2 t = tab[gt];
@@ -1485,72 +1482,58 @@ __global__ void __launch_bounds__(TPB, T ? 4 : 8) k_compact(const DevChain *__re
     pos += __shfl_sync(0xffffffffu, inc, 31);
   }
   // Loops that left their tile: one 32-byte accumulator record per root (and
-  // its Zi word), read, squared and cleared.  The open roots of the tile
-  // cluster at its first vertices (the loops that leave it mostly cross its
-  // first bond), so they are first listed in shared memory from the bitmap
-  // (a block scan of the words' counts) and then taken one per thread.
+  // its Zi word), read and cleared; a thread takes one 32-vertex word of the
+  // open-root bitmap.  With the Zi words, the next root's reads are issued
+  // before the current root is cleared (two roots in flight per thread);
+  // without them, the plain loop needs fewer registers and more resident
+  // warps hide the latency better.
   u128 w2 = 0, f2 = 0, z2 = 0;
-  const int64_t wfirst = (vb + a) >> 5;
-  const int nwords = (e > a) ? (int)(((vb + e - 1) >> 5) - wfirst + 1) : 0;
-  int nopen = 0;
-  for (int w0 = 0; w0 < nwords; w0 += blockDim.x) {  // uniform trip count: one scan per round
-    const int wi = w0 + threadIdx.x;
-    uint32_t bits = 0u;
-    if (wi < nwords) {
-      const int64_t wd = wfirst + wi;
-      bits = __ldcg(s.openroot + wd);
-      const int64_t v0 = (wd << 5) - vb;
-      if (v0 < a) bits &= ~0u << (a - v0);
-      if (v0 + 32 > e) bits &= (e - v0 >= 32) ? ~0u : ((1u << (e - v0)) - 1u);
-    }
-    int64_t tot;
-    int at = nopen + (int)block_excl_scan<int64_t>((int64_t)__popc(bits), sm, tot);
-    while (bits) {
-      if (at < OPEN_LIST) olist[at] = (int)(((wfirst + wi) << 5) - vb) + __ffs(bits) - 1;
-      ++at;
-      bits &= bits - 1;
-    }
-    nopen += (int)tot;
-  }
-  __syncthreads();
-  const int nlist = min(nopen, OPEN_LIST);
-  for (int i = threadIdx.x; i < nlist; i += blockDim.x) {
-    const int64_t v = vb + olist[i];
-    const ulonglong2 x = s.acc2[2 * v], y = s.acc2[2 * v + 1];
-    unsigned long long zi = 0ull;
-    if (T) zi = s.accz[v];
-    s.acc2[2 * v] = make_ulonglong2(0ull, 0ull);
-    s.acc2[2 * v + 1] = make_ulonglong2(0ull, 0ull);
-    if (T) s.accz[v] = 0ull;
-    w2 += sq_abs((long long)x.x);
-    f2 += sq_abs((long long)x.y) + sq_abs((long long)y.x);
-    if (T) z2 += sq_abs((long long)y.y) + sq_abs((long long)zi);
-  }
-  if (nopen > OPEN_LIST) {
-    // more open roots than the list holds (not seen in practice): the rest,
-    // in bitmap order past the listed ones, a thread per word
-    int seen = 0;
-    for (int wi = 0; wi < nwords; ++wi) {
-      const int64_t wd = wfirst + wi;
-      uint32_t bits = __ldcg(s.openroot + wd);
-      const int64_t v0 = (wd << 5) - vb;
-      if (v0 < a) bits &= ~0u << (a - v0);
-      if (v0 + 32 > e) bits &= (e - v0 >= 32) ? ~0u : ((1u << (e - v0)) - 1u);
+  const int64_t wfirst = (vb + a) >> 5, wlast = (vb + e - 1) >> 5;
+  for (int64_t wd = wfirst + threadIdx.x; e > a && wd <= wlast; wd += blockDim.x) {
+    uint32_t bits = __ldcg(s.openroot + wd);
+    const int64_t v0 = (wd << 5) - vb;
+    if (v0 < a) bits &= ~0u << (a - v0);
+    if (v0 + 32 > e) bits &= (e - v0 >= 32) ? ~0u : ((1u << (e - v0)) - 1u);
+    if (!T) {
       while (bits) {
-        const int bit = __ffs(bits) - 1;
+        const int64_t v = vb + v0 + __ffs(bits) - 1;
         bits &= bits - 1;
-        if (seen++ < OPEN_LIST || ((seen - 1 - OPEN_LIST) % (int)blockDim.x) != (int)threadIdx.x) continue;
-        const int64_t v = vb + v0 + bit;
         const ulonglong2 x = s.acc2[2 * v], y = s.acc2[2 * v + 1];
-        unsigned long long zi = 0ull;
-        if (T) zi = s.accz[v];
         s.acc2[2 * v] = make_ulonglong2(0ull, 0ull);
         s.acc2[2 * v + 1] = make_ulonglong2(0ull, 0ull);
-        if (T) s.accz[v] = 0ull;
         w2 += sq_abs((long long)x.x);
         f2 += sq_abs((long long)x.y) + sq_abs((long long)y.x);
-        if (T) z2 += sq_abs((long long)y.y) + sq_abs((long long)zi);
       }
+      continue;
+    }
+    if (!bits) continue;
+    int64_t v = vb + v0 + __ffs(bits) - 1;
+    bits &= bits - 1;
+    ulonglong2 x = s.acc2[2 * v], y = s.acc2[2 * v + 1];
+    unsigned long long zi = s.accz[v];
+    for (;;) {
+      const bool more = bits != 0;
+      int64_t vn = 0;
+      ulonglong2 xn, yn;
+      unsigned long long zn = 0ull;
+      if (more) {
+        vn = vb + v0 + __ffs(bits) - 1;
+        bits &= bits - 1;
+        xn = s.acc2[2 * vn];
+        yn = s.acc2[2 * vn + 1];
+        zn = s.accz[vn];
+      }
+      s.acc2[2 * v] = make_ulonglong2(0ull, 0ull);
+      s.acc2[2 * v + 1] = make_ulonglong2(0ull, 0ull);
+      s.accz[v] = 0ull;
+      w2 += sq_abs((long long)x.x);
+      f2 += sq_abs((long long)x.y) + sq_abs((long long)y.x);
+      z2 += sq_abs((long long)y.y) + sq_abs((long long)zi);
+      if (!more) break;
+      v = vn;
+      x = xn;
+      y = yn;
+      zi = zn;
     }
   }
   long long none = 0;
