@@ -514,16 +514,14 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
-def run_served(args):
+def served_record(n_requests, rate, req_lmax, req_updates, budget_gb, slots, time_limit):
     """Poisson stream of requests (S in {1/2, 1}, L log-uniform in [64, L_max],
-    beta = L U, U log-uniform in [1/4, 4], 50 updates + readout each) into the
-    continuous-batching server; polling bounded by --time-limit."""
-    import torch
+    beta = L U, U log-uniform in [1/4, 4], req_updates updates + readout
+    each) into the continuous-batching server; polling bounded by
+    time_limit.  Latency = submit to result, per request (one update block)."""
     from paper_1810_07485_gb300 import lcqmc, workloads
-    torch.cuda.set_device(0)
-    stream = workloads.request_stream(args.requests, args.rate, L_max=args.req_lmax,
-                                      n_updates=args.req_updates, seed=0)
-    srv = lcqmc.Server(int(args.budget_gb * 1e9), args.slots)
+    stream = workloads.request_stream(n_requests, rate, L_max=req_lmax, n_updates=req_updates, seed=0)
+    srv = lcqmc.Server(int(budget_gb * 1e9), slots)
     rejected = {}
     tickets = {}
     t0 = time.perf_counter()
@@ -535,10 +533,10 @@ def run_served(args):
             tickets[k] = srv.submit(s["L"], s["beta"], s["n_updates"], S=s["S"], seed=s["seed"])
         except lcqmc.LcqmcError as e:
             rejected[k] = e.code
-    log(f"served: {len(tickets)} submitted, {len(rejected)} rejected at submission")
+    log(f"served {rate}/s: {len(tickets)} submitted, {len(rejected)} rejected at submission")
     res = {}
     t_log = time.perf_counter()
-    while time.perf_counter() - t0 < args.time_limit and len(res) < len(tickets):
+    while time.perf_counter() - t0 < time_limit and len(res) < len(tickets):
         for k, t in tickets.items():
             if k not in res:
                 r = srv.poll(t)
@@ -546,12 +544,10 @@ def run_served(args):
                     res[k] = (r.status, r.t_done - r.t_submit, r.t_admit - r.t_submit, r.vertices_edges, r.t_done)
         if time.perf_counter() - t_log > 5.0:
             t_log = time.perf_counter()
-            log(f"served: t={t_log - t0:.1f}s finished {len(res)}/{len(tickets)}")
+            log(f"served {rate}/s: t={t_log - t0:.1f}s finished {len(res)}/{len(tickets)}")
         time.sleep(0.01)
     wall = time.perf_counter() - t0
-    log(f"served: polling ended at t={wall:.1f}s, finished {len(res)}/{len(tickets)}; stopping the server")
     srv.close()
-    log(f"served: server stopped at t={time.perf_counter() - t0:.1f}s")
     done = {k: v for k, v in res.items() if v[0] == 0}
     lat = [v[1] for v in done.values()]
     ve = float(sum(v[3] for v in done.values()))
@@ -559,18 +555,35 @@ def run_served(args):
     rej_s = {0.5: 0, 1.0: 0}
     for k in rejected:
         rej_s[stream[k][1]["S"]] += 1
-    line = {
-        "metric": "served requests: latency p50/p99 and V+E/s", "mode": "served", "value": ve / last,
-        "unit": "V+E/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
-        "config": {"workload": f"{args.requests} requests, Poisson {args.rate}/s, S in {{1/2,1}}, L log-uniform "
-                               f"[64,{args.req_lmax}], beta=L*U, U log-uniform [1/4,4], {args.req_updates} updates each",
-                   "hbm_budget_gb": args.budget_gb, "slots": args.slots, "time_limit_s": args.time_limit},
-        "submitted": len(stream), "rejected_at_admission": len(rejected),
+    return {
+        "rate_per_s": rate, "submitted": len(stream), "rejected_at_admission": len(rejected),
         "rejected_fraction": {"S=1/2": rej_s[0.5] / max(1, sum(1 for _, s in stream if s["S"] == 0.5)),
                               "S=1": rej_s[1.0] / max(1, sum(1 for _, s in stream if s["S"] == 1.0))},
-        "completed": len(done), "unfinished_at_limit": len(tickets) - len(res),
+        "completed": len(done), "failed": len(res) - len(done), "unfinished_at_limit": len(tickets) - len(res),
         "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
-        "queue_wait_p50_s": _pct([v[2] for v in done.values()], 50), "wall_s": wall,
+        "queue_wait_p50_s": _pct([v[2] for v in done.values()], 50), "ve_per_s": ve / last if last > 0 else None,
+        "wall_s": wall,
+    }
+
+
+def run_served(args):
+    """The served form at one rate, or at each rate of --sweep (one JSON line)."""
+    import torch
+    torch.cuda.set_device(0)
+    rates = [float(x) for x in args.sweep.split(",")] if args.sweep else [args.rate]
+    out = []
+    for rate in rates:
+        n_req = args.requests if not args.sweep else int(round(rate * args.sweep_seconds))
+        out.append(served_record(n_req, rate, args.req_lmax, args.req_updates, args.budget_gb, args.slots,
+                                 args.time_limit))
+    line = {
+        "metric": "served requests: latency p50/p99 per update block and V+E/s", "mode": "served",
+        "value": out[-1]["ve_per_s"], "unit": "V+E/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": f"Poisson arrivals, S in {{1/2,1}}, L log-uniform [64,{args.req_lmax}], beta=L*U, "
+                               f"U log-uniform [1/4,4], {args.req_updates} updates + readout each",
+                   "hbm_budget_gb": args.budget_gb, "slots": args.slots, "time_limit_s": args.time_limit,
+                   "arrival_seconds_per_rate": args.sweep_seconds if args.sweep else None},
+        "rates": out,
     }
     print(json.dumps(line), flush=True)
 
@@ -705,6 +718,9 @@ def main():
     ap.add_argument("--req-updates", type=int, default=50)
     ap.add_argument("--slots", type=int, default=512)
     ap.add_argument("--time-limit", type=float, default=60.0)
+    ap.add_argument("--sweep", default="", help="served mode: comma-separated arrival rates (req/s)")
+    ap.add_argument("--sweep-seconds", type=float, default=10.0,
+                    help="served sweep: seconds of arrivals at each rate")
     ap.add_argument("--temporal", action="store_true",
                     help="also measure the temporal moment chi(pi, 2 pi/beta) (single mode)")
     args = ap.parse_args()

@@ -133,6 +133,11 @@ void *Engine::dalloc(size_t bytes) {
   void *p = nullptr;
   if (has_alloc_) {
     p = alloc_.alloc(bytes, alloc_.ctx);
+  } else if (pool_) {
+    if (cudaMallocFromPoolAsync(&p, bytes, pool_, st_) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
   } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
     cudaGetLastError();
     p = nullptr;
@@ -143,9 +148,12 @@ void Engine::dfree(void *p) {
   if (!p) return;
   if (has_alloc_)
     alloc_.free(p, alloc_.ctx);
+  else if (pool_)
+    cudaFreeAsync(p, st_);
   else
     cudaFree(p);
 }
+
 
 #define DALLOC(ptr, type, count)                                                    \
   do {                                                                              \
@@ -258,10 +266,12 @@ Engine::~Engine() {
   dfree(s_.tile_state);
   dfree(s_.need);
   dfree(s_.dbg);
+  if (st_) cudaStreamSynchronize(st_);  // stream-ordered frees done
+  if (pool_) cudaMemPoolDestroy(pool_);
   if (own_stream_ && st_) cudaStreamDestroy(st_);
 }
 
-int Engine::open(void *stream, const lcqmc_allocator *alloc, int ring_cap) {
+int Engine::open(void *stream, const lcqmc_allocator *alloc, int ring_cap, bool serving) {
   CK(cudaGetDevice(&device_));
   if (init_kernel_attributes() != 0) {
     set_error("device table initialization failed");
@@ -278,6 +288,19 @@ int Engine::open(void *stream, const lcqmc_allocator *alloc, int ring_cap) {
   } else {
     CK(cudaStreamCreateWithFlags(&st_, cudaStreamNonBlocking));
     own_stream_ = true;
+  }
+  if (serving) {
+    serving_ = true;
+    if (!has_alloc_) {
+      cudaMemPoolProps props{};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = device_;
+      CK(cudaMemPoolCreate(&pool_, &props));
+      // keep freed memory in the pool for the next request's state
+      uint64_t keep = UINT64_MAX;
+      CK(cudaMemPoolSetAttribute(pool_, cudaMemPoolAttrReleaseThreshold, &keep));
+    }
   }
   ring_cap_ = ring_cap;
   std::vector<uint64_t> T(KMAX);
@@ -633,6 +656,11 @@ int Engine::update(int64_t n) {
     }
     for (int64_t i = 0; i < n; ++i) {
       int rc = enqueue_one(true, ev_used_++);
+      if (rc) return rc;
+    }
+  } else if (serving_) {
+    for (int64_t i = 0; i < n; ++i) {
+      int rc = enqueue_one(false, 0);
       if (rc) return rc;
     }
   } else {

@@ -50,7 +50,11 @@ class Engine {
            int ring_cap);
   // Served form: open an engine with no chains, create / destroy chain states
   // it does not own, and change the resident set between ticks.
-  int open(void *stream, const lcqmc_allocator *alloc, int ring_cap);
+  // serving: device memory from a stream-ordered pool of the engine's own (no
+  // device-wide synchronization when request states come and go), and
+  // updates launched directly instead of from a captured graph (the resident
+  // set changes too often for a capture to pay off).
+  int open(void *stream, const lcqmc_allocator *alloc, int ring_cap, bool serving = false);
   int create_state(const ChainSpec &spec, ChainState *out);
   void destroy_state(ChainState *c);
   int set_chains(const std::vector<ChainState *> &chains);
@@ -117,6 +121,8 @@ class Engine {
   int ring_cap_ = 0;
   size_t fixed_bytes_ = 0, vertex_bytes_ = 0, op_bytes_ = 0;
   cudaGraphExec_t gexec_ = nullptr;
+  bool serving_ = false;
+  cudaMemPool_t pool_ = nullptr;
   bool timing_ = false;
   std::vector<cudaEvent_t> ev_;
   int ev_used_ = 0;

@@ -10,7 +10,11 @@
 // kTickMax), so chains finish on their exact update count; finished chains are
 // read out and freed, and newly admitted ones join at the next tick.  Each
 // chain's random numbers are keyed by its own seed and sweep, so its result is
-// the same alone and in any mix.
+// the same alone and in any mix.  Device memory comes from a stream-ordered
+// pool (request states come and go without a device-wide synchronization)
+// and the updates are launched directly: the resident set changes too often
+// for a captured graph to pay off.  A chain whose update fails (a bounded
+// wait that ran out) fails its own request only.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -143,13 +147,36 @@ struct lcqmc_server {
       if (active.empty()) continue;
       int64_t k = kTickMax;
       for (Req *q : active) k = std::min<int64_t>(k, q->r.n_updates - q->done);
+      std::vector<uint32_t> sweep0(active.size());
+      for (size_t i = 0; i < active.size(); ++i) sweep0[i] = eng.hch[i].sweep;
       int rc = eng.update(k);
       if (rc == 0) rc = eng.sync();
+      std::vector<int> qrc(active.size(), rc);
+      if (rc && active.size() > 1) {
+        // A failed update (a bounded wait that ran out, too many vertices)
+        // stops every resident chain at the same sweep, with its state as it
+        // was before that update.  The rest of the tick is run chain by
+        // chain, so that only the chain that fails loses its request.
+        std::vector<lcq::ChainState *> all;
+        for (Req *q : active) all.push_back(q->st.get());
+        for (size_t i = 0; i < active.size(); ++i) {
+          int r2 = eng.set_chains({active[i]->st.get()});
+          if (!r2) {
+            const int64_t left = k - (int64_t)(uint32_t)(eng.hch[0].sweep - sweep0[i]);
+            if (left > 0) r2 = eng.update(left);
+            if (!r2) r2 = eng.sync();
+          }
+          qrc[i] = r2;
+        }
+        const int r3 = eng.set_chains(all);  // engine index i = active index i again
+        if (r3)
+          for (int &x : qrc) x = x ? x : r3;
+      }
       std::lock_guard<std::mutex> lk(mu);
       for (size_t i = 0; i < active.size(); ++i) {
         Req *q = active[i];
-        if (rc) {
-          finish(q, rc);
+        if (qrc[i]) {
+          finish(q, qrc[i]);
           leaving.push_back(q);
           continue;
         }
@@ -191,7 +218,7 @@ int lcqmc_server_create(size_t hbm_budget, int max_slots, lcqmc_server_t *out) {
     lcq::set_error("no CUDA device");
     return LCQMC_E_CUDA;
   }
-  int rc = s->eng.open(nullptr, nullptr, kServerRing);
+  int rc = s->eng.open(nullptr, nullptr, kServerRing, /*serving=*/true);
   if (rc) {
     delete s;
     return rc;
