@@ -49,17 +49,18 @@ ORACLE_SAMPLE_L = 8192
 # configuration): chains, updates per chain, device budget of one wave.
 BATCH_CHAINS, BATCH_UPDATES, BATCH_BUDGET_GB = 4096, 100, 150.0
 KERNELS_PER_UPDATE = 11
-# DRAM bytes per vertex of each phase's kernels (dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture at L=16384, beta=4096, divided by
-# that update's vertex count; profiles/topkernels_L16384_beta4096.md), valid
-# for the kernel source with this sha1 only.  The second table is for the
-# kernels that differ with the temporal moment on.
-TRAFFIC_PER_VERTEX = {"insert": 13.1, "link_union": 26.8, "loop_ids": 7.5, "loop_props": 25.0,
+# DRAM bytes per vertex of each phase's kernels (DRAM bytes of one ncu
+# capture at L=16384, beta=4096 -- dram__bytes.sum.per_second x
+# gpu__time_duration.sum -- divided by that update's vertex count;
+# profiles/topkernels_L16384_beta4096.md), valid for the kernel source with
+# this sha1 only.  The same tile shapes and per-vertex work hold at
+# L=2^20, beta=2^10, so the full launch's traffic is this figure times its
+# vertex count.  With the temporal moment on, the loop-properties and
+# operator-rewrite kernels differ and have no entry.
+TRAFFIC_PER_VERTEX = {"insert": 13.0, "link_union": 26.8, "loop_ids": 7.5, "loop_props": 25.0,
                       "op_rewrite": 14.8}
-TRAFFIC_PER_VERTEX_TEMPORAL = dict(TRAFFIC_PER_VERTEX, loop_props=25.8, op_rewrite=16.6)
-# The profiled source, and the current one, which only adds the opt-in forest
-# check kernel (off by default, not launched by the bench).
-TRAFFIC_KERNELS_SHA1 = ("fa4001f21f027ccb15dd41a712fca6ac8db77c09", "6b1970f4bba55d2a13c23a301ca60db461da7af2")
+TRAFFIC_PER_VERTEX_TEMPORAL = {k: v for k, v in TRAFFIC_PER_VERTEX.items() if k not in ("loop_props", "op_rewrite")}
+TRAFFIC_KERNELS_SHA1 = ("317b94c016f8e2ad2752f09541ff57e821eaa33a",)
 
 
 # DRAM bytes per launch of each Swendsen-Wang phase at L = 8192, K = K_c (one
