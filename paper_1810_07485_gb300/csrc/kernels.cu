@@ -267,6 +267,10 @@ __device__ int64_t lb_lookback(unsigned long long *st, int64_t g, int64_t first,
 // exceed that (the mean is 8 * TILE) runs its cells in groups, counting in a
 // first pass and drawing again in the writing pass.
 constexpr int INS_CAP = 1280;
+// Threads of an insertion block: one per cell for the set-up and the scans
+// (the upper half only joins the scans with zeros), all of them for the
+// candidates' draws and the vertices' writes.
+constexpr int INS_THREADS = 256;
 constexpr int INS_SPAN = INS_CAP - KMAX;  // a group's cells start within INS_SPAN slots
 constexpr int INS_UCAP = INS_CAP / 2 + TILE;
 constexpr int INS_MIN_SPAN = 256;  // smallest group span a chain may ask for (tests)
@@ -362,7 +366,7 @@ __device__ void ins_draw(const DevChain &C, InsSmem<Q> &S, const OpView &V, int 
   __syncthreads();
   const uint32_t k0 = (uint32_t)C.seed, k1 = (uint32_t)(C.seed >> 32);
   const int lane = threadIdx.x & 31;
-  for (int u0 = 0; u0 < nu; u0 += TILE) {  // whole warps, reconverged per step
+  for (int u0 = 0; u0 < nu; u0 += INS_THREADS) {  // whole warps, reconverged per step
     const int u = u0 + threadIdx.x;
     bool kp[2] = {false, false};
     int sl[2] = {0, 0}, c = 0;
@@ -423,7 +427,7 @@ __device__ void ins_write(const DevChain &C, InsSmem<Q> &S, const OpView &V, int
   long long *vt = (long long *)s.vtau + vb;
   uint8_t *vf = s.vflag + vb, *vc = s.vcell + vb;
   const int nkept = S.nkept;
-  for (int i0 = 0; i0 < nkept; i0 += TILE) {
+  for (int i0 = 0; i0 < nkept; i0 += INS_THREADS) {
     const int i = i0 + threadIdx.x;
     if (i >= nkept) {
       __syncwarp();
@@ -459,7 +463,7 @@ __device__ void ins_write(const DevChain &C, InsSmem<Q> &S, const OpView &V, int
   }
   const int qa = S.q[c0], qb = S.q[c1], qt = S.q[0];
   const bool mapped = qb - qt <= INS_OPCAP;
-  for (int q0 = qa; q0 < qb; q0 += TILE) {
+  for (int q0 = qa; q0 < qb; q0 += INS_THREADS) {
     const int q = q0 + threadIdx.x;
     if (q >= qb) {
       __syncwarp();
@@ -500,7 +504,7 @@ __device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict_
 // memory (above the 48 KB static limit) for the larger neighbour tables of
 // Q = 3, 4.
 template <int Q>
-__global__ void __launch_bounds__(TILE) k_insert(DevChain *__restrict__ ch,
+__global__ void __launch_bounds__(INS_THREADS, 4) k_insert(DevChain *__restrict__ ch,
                                                  const int2 *__restrict__ tab, int64_t blk0,
                                                  int group, Scratch s) {
   if constexpr (Q <= 2) {
@@ -523,8 +527,9 @@ __device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict_
   const int2 t = tab[gt];
   DevChain &C = ch[t.x];
   const int c = threadIdx.x;
+  const bool own = c < TILE;  // this thread's cell (the upper half has none)
   const int cell = t.y * TILE + c;
-  const bool valid = cell < C.ncell;
+  const bool valid = own && cell < C.ncell;
   const int cur = C.cur;
   const int32_t *op = C.op_ptr[cur];
   const long long *otau = (const long long *)C.op_tau[cur];
@@ -598,25 +603,27 @@ __device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict_
     P = K ? K / 2 + 1 : 0;
   }
   if (!valid) q0 = q1 = op[C.ncell];  // cells past the chain's end: empty ranges
-  S.K[c] = K;
-  S.nk[c] = 0;
-  S.q[c] = q0;
+  if (own) {
+    S.K[c] = K;
+    S.nk[c] = 0;
+    S.q[c] = q0;
+  }
   if (c == TILE - 1) S.q[TILE] = q1;
   int tot;
   const int ex = block_excl_scan<int>(K | (P << 16), S.sm, tot);
-  {
+  if (own) {
     // old operator -> cell map (all of the tile's operators, if they fit)
     const int qa = S.q[0];
     for (int q = q0; q < q1 && q - qa < INS_OPCAP; ++q) S.qcell[q - qa] = (uint8_t)c;
+    S.kpre[c] = ex & 0xffff;
+    S.upre[c] = ex >> 16;
   }
-  S.kpre[c] = ex & 0xffff;
-  S.upre[c] = ex >> 16;
   if (c == TILE - 1) {
     S.kpre[TILE] = tot & 0xffff;
     S.upre[TILE] = tot >> 16;
   }
   __syncthreads();
-  {
+  if (own) {
     const int span =
         (C.ins_span >= INS_MIN_SPAN && C.ins_span < INS_SPAN) ? C.ins_span : INS_SPAN;
     const int gc = S.kpre[c] / span;
@@ -641,7 +648,8 @@ __device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict_
   for (int g = 0; g < G; ++g) ins_draw<Q>(C, S, V, g, true);
   const int cnt = valid ? (q1 - q0) + S.nk[c] : 0;
   int ctot;
-  S.cex[c] = block_excl_scan<int>(cnt, S.sm, ctot);
+  const int cex = block_excl_scan<int>(cnt, S.sm, ctot);
+  if (own) S.cex[c] = cex;
 
   // -- chain-local offset of the tile: decoupled look-back --------------------
   if (threadIdx.x < 32) {
@@ -1702,10 +1710,12 @@ void launch_bond_parity(const Launch &L, cudaStream_t st) {
 }
 
 void launch_insert(const Launch &L, cudaStream_t st) {
-#define INSERT_Q(Q)                                                                              \
-  if (L.ntile[Q - 1])                                                                            \
-    k_insert<Q><<<g1(L.ntile[Q - 1]), TILE, Q <= 2 ? 0 : sizeof(InsSmem<Q>), st>>>(L.ch, L.tile_tab, \
-                                                                                  L.tile0[Q - 1], Q - 1, L.s);
+#define INSERT_Q(Q)                                                                                   \
+  if (L.ntile[Q - 1])                                                                                 \
+    k_insert<Q><<<g1(L.ntile[Q - 1]), INS_THREADS, Q <= 2 ? 0 : sizeof(InsSmem<Q>), st>>>(L.ch,          \
+                                                                                          L.tile_tab,    \
+                                                                                          L.tile0[Q - 1], \
+                                                                                          Q - 1, L.s);
   FOR_EACH_Q(INSERT_Q)
 #undef INSERT_Q
 }
