@@ -504,7 +504,7 @@ __device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict_
 // memory (above the 48 KB static limit) for the larger neighbour tables of
 // Q = 3, 4.
 template <int Q>
-__global__ void __launch_bounds__(INS_THREADS, 4) k_insert(DevChain *__restrict__ ch,
+__global__ void __launch_bounds__(INS_THREADS, 5) k_insert(DevChain *__restrict__ ch,
                                                  const int2 *__restrict__ tab, int64_t blk0,
                                                  int group, Scratch s) {
   if constexpr (Q <= 2) {
