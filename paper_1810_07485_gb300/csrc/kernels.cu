@@ -300,7 +300,7 @@ struct OpView {
 template <int Q>
 struct InsSmem {
   long long sop[InsStage<Q>::N];    // staged old operator times (16-byte aligned: first member)
-  unsigned long long key[INS_CAP];  // u53, with bit 63 set if the candidate is not kept
+  unsigned long long key[INS_CAP];  // (u53 << 6) | draw, with bit 63 set if the candidate is not kept
   long long tau[INS_CAP];           // time bits; LLONG_MAX if not kept
   short klist[INS_CAP];             // kept candidates' slots (any order)
   uint8_t scell[INS_CAP];           // slot -> cell in tile
@@ -389,7 +389,8 @@ __device__ void ins_draw(const DevChain &C, InsSmem<Q> &S, const OpView &V, int 
         long long tau;
         const bool keep = ins_decide<Q>(V, X, b, par0, u53, t0, d, teb, tau);
         const int slot = ks + k;
-        S.key[slot] = keep ? u53 : (u53 | KEY_DROP);
+        // (u53, draw) packed into one key, unique within the cell
+        S.key[slot] = ((u53 << 6) | (uint64_t)k) | (keep ? 0ull : KEY_DROP);
         S.tau[slot] = keep ? tau : LLONG_MAX;
         S.scell[slot] = (uint8_t)c;
         kp[h] = keep;
@@ -436,13 +437,10 @@ __device__ void ins_write(const DevChain &C, InsSmem<Q> &S, const OpView &V, int
     const int slot = S.klist[i];
     const long long tau = S.tau[slot];
     const int c = S.scell[slot];
-    const int ks = S.kpre[c] - kb, K = S.K[c], k = slot - ks;
+    const int ks = S.kpre[c] - kb, K = S.K[c];
     const unsigned long long key = S.key[slot];
     int r = 0;
-    for (int x = 0; x < K; ++x) {
-      const unsigned long long k2 = S.key[ks + x];
-      r += (k2 < key) | ((k2 == key) & (x < k));
-    }
+    for (int x = 0; x < K; ++x) r += S.key[ks + x] < key;  // kept keys ahead (a dropped one has bit 63)
     // old operators at or before tau (ascending times)
     int lo = S.q[c], hi = S.q[c + 1];
     const int q0 = lo;
