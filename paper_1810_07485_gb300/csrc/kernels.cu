@@ -557,7 +557,10 @@ __device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict_
   __syncthreads();
 
   // -- per-cell setup --------------------------------------------------------
-  int K = 0, P = 0, q0 = 0, q1 = 0;
+  // The lower half of the block takes the cells' neighbour ranges and spin
+  // parities, the upper half their candidate counts (Philox call 0), side by
+  // side.
+  int q0 = 0, q1 = 0;
   if (valid) {
     int b, j;
     cell_bj(C, cell, b, j);
@@ -588,6 +591,10 @@ __device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict_
     S.j[c] = j;
     q0 = op[cell];
     q1 = op[cell + 1];
+  } else if (!own && t.y * TILE + (c - TILE) < C.ncell) {
+    const int cc = c - TILE;  // the cell whose count this thread draws
+    int b, j, K = 0;
+    cell_bj(C, t.y * TILE + cc, b, j);
     const uint64_t db = C.win[3 * j + 2];
     const U4 o0 = philox(TAG_INSERT << 24, (uint32_t)b, (uint32_t)j, C.sweep, (uint32_t)C.seed,
                          (uint32_t)(C.seed >> 32));
@@ -598,15 +605,18 @@ __device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict_
     for (int step = 32; step > 0; step >>= 1)
       if (K + step <= KMAX - 1 && T[K + step - 1] <= U) K += step;
     if ((long long)db <= 0) K = 0;  // empty last window
-    P = K ? K / 2 + 1 : 0;
+    S.K[cc] = K;
+  } else if (!own) {
+    S.K[c - TILE] = 0;  // cells past the chain's end
   }
   if (!valid) q0 = q1 = op[C.ncell];  // cells past the chain's end: empty ranges
   if (own) {
-    S.K[c] = K;
     S.nk[c] = 0;
     S.q[c] = q0;
   }
   if (c == TILE - 1) S.q[TILE] = q1;
+  __syncthreads();
+  const int K = own ? S.K[c] : 0, P = K ? K / 2 + 1 : 0;
   int tot;
   const int ex = block_excl_scan<int>(K | (P << 16), S.sm, tot);
   if (own) {
