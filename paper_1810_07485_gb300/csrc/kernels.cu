@@ -1086,10 +1086,12 @@ __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
 // unions are chains of dependent global loads, so many tiles are kept in
 // flight.
 constexpr int TPB_X = 256;
+constexpr int XLIST = 256;  // crossing edges of a tile listed per warp
 
 __global__ void __launch_bounds__(TPB_X) k_link_x(const DevChain *__restrict__ ch,
                                                 const int2 *__restrict__ tab, int64_t ntiles,
                                                 Scratch s) {
+  __shared__ int xlist[TPB_X / 32][XLIST];
   if (halted(s)) return;
   const int lane = threadIdx.x & 31;
   const int64_t gt = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -1106,17 +1108,44 @@ __global__ void __launch_bounds__(TPB_X) k_link_x(const DevChain *__restrict__ c
     for (int w = a + lane; w < e; w += 32) uf_union(par, s.pl[vb + w], s.pr[vb + w], s.status, s.uf_limit);
     return;
   }
+  // The tile's crossing edges cluster at its first vertices (its first bond's
+  // cells): they are listed first (a warp scan of the mark words' counts) and
+  // then taken round-robin by the lanes, so that no lane walks most of them.
+  int *list = xlist[threadIdx.x >> 5];
   const int64_t wfirst = (vb + a) >> 5, wlast = (vb + e - 1) >> 5;
-  for (int64_t wd = wfirst + lane; e > a && wd <= wlast; wd += 32) {
-    uint32_t bits = __ldcg(s.xmark + wd);
+  int nlist = 0;
+  for (int64_t w0 = wfirst; e > a && w0 <= wlast; w0 += 32) {  // the same trip count on every lane
+    const int64_t wd = w0 + lane;
+    uint32_t bits = 0u;
     const int64_t v0 = (wd << 5) - vb;
-    if (v0 < a) bits &= ~0u << (a - v0);
-    if (v0 + 32 > e) bits &= (e - v0 >= 32) ? ~0u : ((1u << (e - v0)) - 1u);
+    if (wd <= wlast) {
+      bits = __ldcg(s.xmark + wd);
+      if (v0 < a) bits &= ~0u << (a - v0);
+      if (v0 + 32 > e) bits &= (e - v0 >= 32) ? ~0u : ((1u << (e - v0)) - 1u);
+    }
+    const int cnt = __popc(bits);
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    int at = nlist + inc - cnt;
     while (bits) {
       const int w = (int)v0 + __ffs(bits) - 1;
       bits &= bits - 1;
-      uf_union(par, s.pl[vb + w], s.pr[vb + w], s.status, s.uf_limit);
+      if (at < XLIST)
+        list[at] = w;
+      else
+        uf_union(par, s.pl[vb + w], s.pr[vb + w], s.status, s.uf_limit);  // past the list
+      ++at;
     }
+    nlist += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  __syncwarp();
+  for (int i = lane; i < min(nlist, XLIST); i += 32) {
+    const int w = list[i];
+    uf_union(par, s.pl[vb + w], s.pr[vb + w], s.status, s.uf_limit);
   }
 }
 
