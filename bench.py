@@ -57,10 +57,10 @@ KERNELS_PER_UPDATE = 11
 # L=2^20, beta=2^10, so the full launch's traffic is this figure times its
 # vertex count.  With the temporal moment on, the loop-properties and
 # operator-rewrite kernels differ and have no entry.
-TRAFFIC_PER_VERTEX = {"insert": 13.0, "link_union": 26.8, "loop_ids": 7.5, "loop_props": 25.0,
+TRAFFIC_PER_VERTEX = {"insert": 13.5, "link_union": 26.7, "loop_ids": 7.5, "loop_props": 25.0,
                       "op_rewrite": 14.8}
 TRAFFIC_PER_VERTEX_TEMPORAL = {k: v for k, v in TRAFFIC_PER_VERTEX.items() if k not in ("loop_props", "op_rewrite")}
-TRAFFIC_KERNELS_SHA1 = ("317b94c016f8e2ad2752f09541ff57e821eaa33a",)
+TRAFFIC_KERNELS_SHA1 = ("b448d0df19ee37b811fd916694430994ebf60528",)
 
 
 # DRAM bytes per launch of each Swendsen-Wang phase at L = 8192, K = K_c (one
