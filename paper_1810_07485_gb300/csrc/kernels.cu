@@ -189,24 +189,6 @@ struct NbOps {
   int o0[N], o1[N];
 };
 
-// Parity of the operators on the neighbour bonds ahead of (tau, b).
-template <int Q>
-__device__ __forceinline__ int nb_parity(const NbOps<Q> &X, const long long *__restrict__ tau_arr,
-                                         long long tau, int b) {
-  int p = 0;
-#pragma unroll
-  for (int k = 0; k < NbOps<Q>::N; ++k) {
-    for (int q = X.o0[k]; q < X.o1[k]; ++q) {
-      const long long t = tau_arr[q];
-      if (t < tau || (t == tau && X.bond[k] < b))
-        p ^= 1;
-      else
-        break;
-    }
-  }
-  return p;
-}
-
 // Single pass: every tile counts its cells' vertices, publishes the count, and
 // gets the chain-local offset of its first vertex by decoupled look-back over
 // the tiles before it (tile order = order in which blocks took their ticket,
