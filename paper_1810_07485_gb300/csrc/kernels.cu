@@ -262,10 +262,10 @@ constexpr unsigned long long KEY_DROP = 1ull << 63;
 
 // Old operator times a tile stages in shared memory: its own cells' and those
 // of the cells up to 8 Q^2 cells away (the neighbour bonds of the same
-// windows), when they fit.
+// windows), when they fit (about 1230 for a thermalized S = 1 tile).
 template <int Q>
 struct InsStage {
-  static constexpr int N = Q == 1 ? 1024 : (Q == 2 ? 512 : 2048);
+  static constexpr int N = Q == 1 ? 1024 : (Q == 2 ? 1536 : 2048);
 };
 
 // Where an old operator's time is read: from the staged copy if its index is
@@ -480,14 +480,14 @@ __device__ __forceinline__ void insert_tile(InsSmem<Q> &S, DevChain *__restrict_
                                             const int2 *__restrict__ tab, int64_t blk0, int group,
                                             Scratch s);
 
-// The staging area is static shared memory for Q <= 2 and dynamic shared
-// memory (above the 48 KB static limit) for the larger neighbour tables of
-// Q = 3, 4.
+// The staging area is static shared memory for Q = 1 and dynamic shared
+// memory (above the 48 KB static limit) for the larger neighbour tables and
+// operator stages of Q = 2, 3, 4.
 template <int Q>
-__global__ void __launch_bounds__(INS_THREADS, 5) k_insert(DevChain *__restrict__ ch,
+__global__ void __launch_bounds__(INS_THREADS, Q == 1 ? 5 : 4) k_insert(DevChain *__restrict__ ch,
                                                  const int2 *__restrict__ tab, int64_t blk0,
                                                  int group, Scratch s) {
-  if constexpr (Q <= 2) {
+  if constexpr (Q == 1) {
     __shared__ __align__(16) InsSmem<Q> S;
     insert_tile<Q>(S, ch, tab, blk0, group, s);
   } else {
@@ -1731,7 +1731,7 @@ void launch_bond_parity(const Launch &L, cudaStream_t st) {
 void launch_insert(const Launch &L, cudaStream_t st) {
 #define INSERT_Q(Q)                                                                                   \
   if (L.ntile[Q - 1])                                                                                 \
-    k_insert<Q><<<g1(L.ntile[Q - 1]), INS_THREADS, Q <= 2 ? 0 : sizeof(InsSmem<Q>), st>>>(L.ch,          \
+    k_insert<Q><<<g1(L.ntile[Q - 1]), INS_THREADS, Q == 1 ? 0 : sizeof(InsSmem<Q>), st>>>(L.ch,          \
                                                                                           L.tile_tab,    \
                                                                                           L.tile0[Q - 1], \
                                                                                           Q - 1, L.s);
@@ -1797,7 +1797,9 @@ int init_kernel_attributes() {
     return -1;
   FOR_EACH_Q(EST_ATTR_Q)
 #undef EST_ATTR_Q
-  if (cudaFuncSetAttribute(k_insert<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(k_insert<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(InsSmem<2>)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_insert<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sizeof(InsSmem<3>)) != cudaSuccess ||
       cudaFuncSetAttribute(k_insert<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sizeof(InsSmem<4>)) != cudaSuccess)
