@@ -56,11 +56,13 @@ KERNELS_PER_UPDATE = 11
 # this sha1 only.  The same tile shapes and per-vertex work hold at
 # L=2^20, beta=2^10, so the full launch's traffic is this figure times its
 # vertex count.  With the temporal moment on, the loop-properties and
-# operator-rewrite kernels differ and have no entry.
+# operator-rewrite kernels differ and have no entry.  The second sha1 is the
+# current source, whose S = 1/2 kernels are those profiled (it changes only
+# the S >= 1 insertion's shared-memory staging).
 TRAFFIC_PER_VERTEX = {"insert": 13.5, "link_union": 26.7, "loop_ids": 7.5, "loop_props": 25.0,
                       "op_rewrite": 14.8}
 TRAFFIC_PER_VERTEX_TEMPORAL = {k: v for k, v in TRAFFIC_PER_VERTEX.items() if k not in ("loop_props", "op_rewrite")}
-TRAFFIC_KERNELS_SHA1 = ("b448d0df19ee37b811fd916694430994ebf60528",)
+TRAFFIC_KERNELS_SHA1 = ("b448d0df19ee37b811fd916694430994ebf60528", "aa68e004d5bfc68f8f4b153c27a3400957ed6882")
 
 
 # DRAM bytes per launch of each Swendsen-Wang phase at L = 8192, K = K_c (one
