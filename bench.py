@@ -9,7 +9,9 @@ single-chain configuration of the benchmark list.  V+E counts the paper's
 graph: fragments + 2 x vertices (Sec. 4.4).  The same line carries the
 batched form beside it: 4096 uneven chains, 100 updates each, packed per
 phase and replayed from a CUDA graph, against the same chains launched one
-at a time (per-chain completion p50/p99, results identical).
+at a time (per-chain completion p50/p99, results identical); and the served
+form: Poisson request streams at 20 and 50 requests/s (latency p50/p99 per
+block of 50 updates, V+E/s).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-batched]
   python bench.py --mode batched [--chains C --updates U]   (the batched form alone)
@@ -48,6 +50,9 @@ ORACLE_SAMPLE_L = 8192
 # The batched form beside the single chain (the benchmark list's batched
 # configuration): chains, updates per chain, device budget of one wave.
 BATCH_CHAINS, BATCH_UPDATES, BATCH_BUDGET_GB = 4096, 100, 150.0
+# The served form beside them: request streams at a light and at a saturating
+# rate (latency per update block, p50 / p99, and V+E/s).
+SERVED_RATES, SERVED_SECONDS, SERVED_LMAX = (20.0, 50.0), 10.0, 4096
 KERNELS_PER_UPDATE = 11
 # DRAM bytes per vertex of each phase's kernels (DRAM bytes of one ncu
 # capture at L=16384, beta=4096 -- dram__bytes.sum.per_second x
@@ -404,9 +409,14 @@ def run_ours(args, world, rank, local):
                                           f"one per core, each the same sample"}
         except Exception as e:  # the one-core figure stands alone
             cpu["all_cores"] = {"value": None, "error": repr(e)[:200]}
-    batched = None
+    batched = served = None
     if world == 1 and not args.no_batched and args.workload == DEFAULT_WORKLOAD:
         batched = batched_record(BATCH_CHAINS, BATCH_UPDATES, BATCH_BUDGET_GB)
+        served = {"workload": f"Poisson arrivals for {SERVED_SECONDS:g} s at each rate, S in {{1/2,1}}, L log-uniform "
+                              f"[64,{SERVED_LMAX}], beta=L*U, U log-uniform [1/4,4], 50 updates + readout each; "
+                              f"{BATCH_BUDGET_GB:g} GB budget, 512 slots",
+                  "rates": [served_record(int(rate * SERVED_SECONDS), rate, SERVED_LMAX, 50, BATCH_BUDGET_GB, 512,
+                                          SERVED_SECONDS + 20.0) for rate in SERVED_RATES]}
     line = {
         "metric": "space-time vertices+edges/s per loop update", "value": value, "unit": "V+E/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -429,6 +439,8 @@ def run_ours(args, world, rank, local):
     }
     if batched is not None:
         line["batched"] = batched
+    if served is not None:
+        line["served"] = served
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -713,7 +725,7 @@ def main():
     ap.add_argument("--chains", type=int, default=BATCH_CHAINS)
     ap.add_argument("--updates", type=int, default=BATCH_UPDATES)
     ap.add_argument("--no-batched", action="store_true",
-                    help="leave the batched form out of the single-chain line")
+                    help="leave the batched and served records out of the single-chain line")
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=10.0)
