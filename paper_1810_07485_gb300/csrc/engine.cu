@@ -210,10 +210,7 @@ int Engine::alloc_vertex(int64_t vcap) {
   vcap_ = vcap;
   vertex_bytes_ = (size_t)vcap * (8 + 2 + 12 + 8 * ACC_WORDS + 8) + 4 * (size_t)nw * 4;
   L_.s = s_;
-  if (gexec_) {
-    cudaGraphExecDestroy(gexec_);
-    gexec_ = nullptr;
-  }
+  drop_graphs();
   return LCQMC_OK;
 }
 
@@ -235,7 +232,7 @@ void Engine::destroy_state(ChainState *c) {
 
 Engine::~Engine() {
   if (st_) cudaStreamSynchronize(st_);
-  if (gexec_) cudaGraphExecDestroy(gexec_);
+  drop_graphs();
   for (auto e : ev_) cudaEventDestroy(e);
   free_vertex();
   for (auto &c : owned_) destroy_state(c.get());
@@ -549,10 +546,7 @@ int Engine::layout() {
   L_.site_tab = site_tab_;
   L_.bond_tab = bond_tab_;
   L_.s = s_;
-  if (gexec_) {
-    cudaGraphExecDestroy(gexec_);
-    gexec_ = nullptr;
-  }
+  drop_graphs();
   if (vest > vcap_) {
     rc = alloc_vertex(vest);
     if (rc) return rc;
@@ -598,12 +592,7 @@ int Engine::enqueue_one(bool timed, int slot) {
   };
   mark(0);  // [0] labeling: random numbers, insertion, vertex offsets (one pass)
   launch_bond_parity(L_, st_);
-  CK(cudaMemsetAsync(s_.tile_state, 0, 8 * (size_t)cap_tiles_, st_));
-  CK(cudaMemsetAsync(s_.tickets, 0, QMAX * sizeof(unsigned int), st_));
-  CK(cudaMemsetAsync(s_.openmark, 0, 4 * nw, st_));
-  CK(cudaMemsetAsync(s_.openroot, 0, 4 * nw, st_));
-  CK(cudaMemsetAsync(s_.flipbits, 0, 4 * nw, st_));
-  CK(cudaMemsetAsync(s_.xmark, 0, 4 * nw, st_));
+  launch_clear(L_, cap_tiles_, nw, st_);
   launch_insert(L_, st_);
   mark(1);  // [1] tau = 0 cut
   launch_cut(L_, st_);
@@ -626,16 +615,30 @@ int Engine::enqueue_one(bool timed, int slot) {
   return LCQMC_OK;
 }
 
-int Engine::capture() {
-  if (gexec_) return LCQMC_OK;
+void Engine::drop_graphs() {
+  if (gexec_) cudaGraphExecDestroy(gexec_);
+  if (gexec_blk_) cudaGraphExecDestroy(gexec_blk_);
+  gexec_ = gexec_blk_ = nullptr;
+}
+
+// Captures `count` consecutive updates as one graph (the launches carry the
+// current buffers, block sizes and temporal switch: drop_graphs() whenever
+// one of those changes).
+int Engine::capture(int count, cudaGraphExec_t *out) {
+  if (*out) return LCQMC_OK;
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
-  int rc = enqueue_one(false, 0);
+  int rc = LCQMC_OK;
+  for (int i = 0; i < count && !rc; ++i) rc = enqueue_one(false, 0);
   cudaError_t e = cudaStreamEndCapture(st_, &g);
-  if (rc) return rc;
+  if (rc) {
+    if (e == cudaSuccess) cudaGraphDestroy(g);
+    return rc;
+  }
   CK(e);
-  CK(cudaGraphInstantiate(&gexec_, g, 0));
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
+  CK(e);
   return LCQMC_OK;
 }
 
@@ -664,9 +667,12 @@ int Engine::update(int64_t n) {
       if (rc) return rc;
     }
   } else {
-    int rc = capture();
+    const int64_t nblk = n / kGraphBlock, rest = n % kGraphBlock;
+    int rc = nblk ? capture(kGraphBlock, &gexec_blk_) : LCQMC_OK;
+    if (!rc && rest) rc = capture(1, &gexec_);
     if (rc) return rc;
-    for (int64_t i = 0; i < n; ++i) CK(cudaGraphLaunch(gexec_, st_));
+    for (int64_t i = 0; i < nblk; ++i) CK(cudaGraphLaunch(gexec_blk_, st_));
+    for (int64_t i = 0; i < rest; ++i) CK(cudaGraphLaunch(gexec_, st_));
   }
   pending_ += n;
   return LCQMC_OK;
@@ -776,10 +782,7 @@ int Engine::sync() {
         }
       rc = push_chains();
       if (rc) return rc;
-      if (gexec_) {
-        cudaGraphExecDestroy(gexec_);
-        gexec_ = nullptr;
-      }
+      drop_graphs();
     }
     CK(cudaMemsetAsync(s_.status, 0, sizeof(int), st_));
     pending_ = 0;
@@ -954,10 +957,7 @@ int Engine::import_config(int64_t c, const uint8_t *s0, const int32_t *op_ptr, c
   if (n_off > d.op_cap) {
     rc = grow_ops(c, n_off);
     if (rc) return rc;
-    if (gexec_) {
-      cudaGraphExecDestroy(gexec_);
-      gexec_ = nullptr;
-    }
+    drop_graphs();
   }
   const ChainBuf &b = cs_[c]->buf;
   CK(cudaMemcpy(b.s0[d.cur], s0, d.nsub, cudaMemcpyHostToDevice));
@@ -1020,10 +1020,7 @@ int Engine::set_wait_limit(int64_t limit) {
   if (rc) return rc;
   s_.uf_limit = limit ? (int)limit : UF_MAX_ITERS;
   L_.s = s_;
-  if (gexec_) {  // the captured launches carry the scratch descriptor
-    cudaGraphExecDestroy(gexec_);
-    gexec_ = nullptr;
-  }
+  drop_graphs();  // the captured launches carry the scratch descriptor
   return LCQMC_OK;
 }
 
@@ -1032,10 +1029,7 @@ int Engine::set_temporal(int enable) {
   if (rc) return rc;
   if ((L_.temporal != 0) != (enable != 0)) {
     L_.temporal = enable != 0;
-    if (gexec_) {  // the captured launches carry the choice
-      cudaGraphExecDestroy(gexec_);
-      gexec_ = nullptr;
-    }
+    drop_graphs();  // the captured launches carry the choice
   }
   return LCQMC_OK;
 }
@@ -1059,10 +1053,7 @@ int Engine::set_tuning(const lcqmc_tuning &t) {
   L_.link_threads = t.link_threads;
   L_.link_x_warps = t.link_x_warps;
   L_.compress_threads = t.compress_threads;
-  if (gexec_) {  // the captured launches carry the block sizes
-    cudaGraphExecDestroy(gexec_);
-    gexec_ = nullptr;
-  }
+  drop_graphs();  // the captured launches carry the block sizes
   return LCQMC_OK;
 }
 

@@ -100,7 +100,8 @@ class Engine {
   void free_vertex();
   int grow_ops(int64_t chain, int64_t need);
   int enqueue_one(bool timed, int slot);
-  int capture();
+  int capture(int count, cudaGraphExec_t *out);
+  void drop_graphs();
 
   int device_ = 0;
   cudaStream_t st_ = nullptr;
@@ -120,7 +121,10 @@ class Engine {
   int64_t vcap_ = 0;
   int ring_cap_ = 0;
   size_t fixed_bytes_ = 0, vertex_bytes_ = 0, op_bytes_ = 0;
-  cudaGraphExec_t gexec_ = nullptr;
+  // one update, and a block of kGraphBlock updates (fewer graph launches for
+  // small chains, whose updates are a few microseconds of work)
+  static constexpr int kGraphBlock = 8;
+  cudaGraphExec_t gexec_ = nullptr, gexec_blk_ = nullptr;
   bool serving_ = false;
   cudaMemPool_t pool_ = nullptr;
   bool timing_ = false;

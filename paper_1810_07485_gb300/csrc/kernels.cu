@@ -17,6 +17,7 @@
 //   k_compact        next operator list, squared lengths of open loops  [8]
 //   k_sites          spins at tau = 0, vertex-free loops                [8]
 //   k_final          per-chain record, running sums, buffer swap
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -176,6 +177,24 @@ __global__ void k_bond_parity(const DevChain *__restrict__ ch, const int2 *__res
     p ^= (uint8_t)((op[c0 + tw] - op[c0]) & 1);
     row[(int64_t)(blk + 1) * C.nbond + b] = p;
   }
+}
+
+// ---- per-update scratch reset -------------------------------------------------
+// The insertion's look-back words and tile tickets and the four per-vertex
+// bitmaps (open marks, open roots, coin flips, crossing marks) start each
+// update at zero: one grid-stride launch instead of one memset each (a small
+// chain's update is a chain of short launches).
+__global__ void k_clear(Scratch s, int64_t ntile, int64_t nw) {
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = i0; i < nw; i += step) {
+    s.openmark[i] = 0u;
+    s.openroot[i] = 0u;
+    s.flipbits[i] = 0u;
+    s.xmark[i] = 0u;
+  }
+  for (int64_t i = i0; i < ntile; i += step) s.tile_state[i] = 0ull;
+  if (i0 < QMAX) s.tickets[i0] = 0u;
 }
 
 // ---- insertion (labeling, rules i-iii) --------------------------------------
@@ -1726,6 +1745,13 @@ void launch_bond_parity(const Launch &L, cudaStream_t st) {
   for (int q = 0; q < QMAX; ++q)
     if (L.nbondblk[q])
       k_bond_parity<<<g1(L.nbondblk[q]), BOND_BLOCK, 0, st>>>(L.ch, L.bond_tab, L.bond0[q], L.s);
+}
+
+void launch_clear(const Launch &L, int64_t ntile, int64_t nw, cudaStream_t st) {
+  constexpr int T = 256;
+  const int64_t n = std::max<int64_t>(std::max(ntile, nw), QMAX);
+  const int64_t blocks = std::min<int64_t>((n + T - 1) / T, 152 * 8);
+  k_clear<<<g1(blocks), T, 0, st>>>(L.s, ntile, nw);
 }
 
 void launch_insert(const Launch &L, cudaStream_t st) {

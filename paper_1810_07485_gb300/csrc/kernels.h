@@ -26,6 +26,8 @@ struct Launch {
 void set_full_table(const uint64_t *T, cudaStream_t st);
 int init_kernel_attributes();
 void launch_bond_parity(const Launch &L, cudaStream_t st);
+// zeroes the look-back words of ntile tiles, the tickets and nw words of each bitmap
+void launch_clear(const Launch &L, int64_t ntile, int64_t nw, cudaStream_t st);
 void launch_insert(const Launch &L, cudaStream_t st);
 void launch_scan_ops(const Launch &L, cudaStream_t st);
 void launch_cut(const Launch &L, cudaStream_t st);
