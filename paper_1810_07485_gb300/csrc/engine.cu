@@ -305,6 +305,12 @@ int Engine::open(void *stream, const lcqmc_allocator *alloc, int ring_cap, bool 
   set_full_table(T.data(), st_);
   DALLOC(s_.status, int, 1);
   s_.uf_limit = UF_MAX_ITERS;
+  // Tests: the most steps a global union-find walk or retry loop of this
+  // engine may take (1 .. 2^22; lcqmc_set_wait_limit sets it for a chain).
+  if (const char *e = std::getenv("LCQMC_WAIT_LIMIT")) {
+    const long long v = std::atoll(e);
+    if (v >= 1 && v <= UF_MAX_ITERS) s_.uf_limit = (int)v;
+  }
   DALLOC(s_.tickets, unsigned int, QMAX);
   DALLOC(s_.need, int64_t, 4);
   DALLOC(s_.dbg, long long, 8);

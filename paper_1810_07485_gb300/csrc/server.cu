@@ -5,7 +5,7 @@
 // order while free slots and the HBM budget allow (a request that does not fit
 // yet waits; later ones that fit may go ahead), allocates their device state,
 // and advances every resident chain together in ticks: one batched update per
-// phase over all resident chains, replayed from a CUDA graph.  A tick runs as
+// phase over all resident chains (each phase one launch per Q group).  A tick runs as
 // many updates as the nearest-to-completion chain still needs (at most
 // kTickMax), so chains finish on their exact update count; finished chains are
 // read out and freed, and newly admitted ones join at the next tick.  Each

@@ -34,6 +34,24 @@ def _wait(srv, tickets, timeout=120.0):
     return out
 
 
+def _check_against_oracle(r, m):
+    # the oracle's chain: the same records, summed in update order
+    p = orc.params(m["L"], m["beta"], Q=int(2 * m["S"]), seed=m["seed"])
+    recs = orc.keyed_run(p, 0, m["n"], orc.neel(p))
+    fields = ("energy", "chi_s", "chi_q", "n", "n_off_new", "n_seg", "n_clusters", None)
+    for k, f in enumerate(fields):
+        v = [float(x) for x in (recs["n_seg"] + 2 * recs["n"] if f is None else recs[f])]
+        s1 = s2 = 0.0
+        for x in v:
+            s1 += x
+            s2 += x * x
+        if f in ("energy", "chi_s", "chi_q"):  # fp64 from exact sums; 1e-15 per record
+            assert r.obs.sum[k] == pytest.approx(s1, rel=1e-13, abs=1e-300), (m, f)
+            assert r.obs.sumsq[k] == pytest.approx(s2, rel=1e-13, abs=1e-300), (m, f)
+        else:  # integers, exact in fp64
+            assert r.obs.sum[k] == s1 and r.obs.sumsq[k] == s2, (m, f)
+
+
 def test_mix_equals_alone():
     from paper_1810_07485_gb300 import lcqmc
     srv = lcqmc.Server(hbm_budget=8 << 30, max_slots=3)
@@ -52,21 +70,7 @@ def test_mix_equals_alone():
         assert list(r.obs.sumsq) == list(o.sumsq), m
         assert r.vertices_edges == int(o.sum[7])
         ch.close()
-        # the oracle's chain: the same records, summed in update order
-        p = orc.params(m["L"], m["beta"], Q=int(2 * m["S"]), seed=m["seed"])
-        recs = orc.keyed_run(p, 0, m["n"], orc.neel(p))
-        fields = ("energy", "chi_s", "chi_q", "n", "n_off_new", "n_seg", "n_clusters", None)
-        for k, f in enumerate(fields):
-            v = [float(x) for x in (recs["n_seg"] + 2 * recs["n"] if f is None else recs[f])]
-            s1 = s2 = 0.0
-            for x in v:
-                s1 += x
-                s2 += x * x
-            if f in ("energy", "chi_s", "chi_q"):  # fp64 from exact sums; 1e-15 per record
-                assert r.obs.sum[k] == pytest.approx(s1, rel=1e-13, abs=1e-300), (m, f)
-                assert r.obs.sumsq[k] == pytest.approx(s2, rel=1e-13, abs=1e-300), (m, f)
-            else:  # integers, exact in fp64
-                assert r.obs.sum[k] == s1 and r.obs.sumsq[k] == s2, (m, f)
+        _check_against_oracle(r, m)
 
 
 def test_admission_rejects_oversized_and_cancels():
@@ -81,3 +85,29 @@ def test_admission_rejects_oversized_and_cancels():
     res = _wait(srv, [a, b])
     assert res[a].status == 0 and res[b].status == -9  # E_CANCELLED
     srv.close()
+
+
+def test_failing_chain_fails_only_its_request(monkeypatch):
+    # One resident chain's bounded wait runs out: the tick is run again chain
+    # by chain, that chain's request fails with LCQMC_E_DEVICE_TIMEOUT and
+    # the others finish with the oracle's results.  Tiles above 64 vertices
+    # unite their edges in the global forest, whose walks get a bound of one
+    # step; the small chains (one tile of a few vertices) never walk it.
+    monkeypatch.setenv("LCQMC_LOCAL_CAP", "64")
+    monkeypatch.setenv("LCQMC_WAIT_LIMIT", "1")
+    from paper_1810_07485_gb300 import lcqmc
+    # the small chains run 200 updates (at least 20 ticks), so they are still
+    # resident when the large one joins and fails
+    small = [dict(L=8, beta=0.5, S=0.5, seed=11, n=200), dict(L=4, beta=1.0, S=0.5, seed=12, n=210),
+             dict(L=2, beta=0.5, S=1.0, seed=13, n=205)]
+    big = dict(L=1024, beta=40.0, S=0.5, seed=9, n=6)
+    srv = lcqmc.Server(hbm_budget=8 << 30, max_slots=4)
+    tickets = [srv.submit(m["L"], m["beta"], m["n"], S=m["S"], seed=m["seed"]) for m in small + [big]]
+    res = _wait(srv, tickets)
+    srv.close()
+    assert res[tickets[-1]].status == -5  # LCQMC_E_DEVICE_TIMEOUT
+    for m, t in zip(small, tickets):
+        r = res[t]
+        assert r.status == 0, (m, r.status)
+        assert r.obs.n_updates == m["n"]
+        _check_against_oracle(r, m)
