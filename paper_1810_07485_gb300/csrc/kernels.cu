@@ -1061,21 +1061,23 @@ __global__ void __launch_bounds__(TPB) k_link(const DevChain *__restrict__ ch,
   }
   __syncthreads();
   if (local) {
-    // Pointer jumping until every node points at its root (the depth halves
-    // each round; 2^12 > SMEM_CAP bounds the rounds).
+    // Every node walks to its root and stores it (in shared memory too, which
+    // shortens the walks of the nodes below it).  Each store writes an
+    // ancestor of the old word, so concurrent walks still end at the root;
+    // the walks are bounded by the tile's node count.  One pass without
+    // barriers (pointer jumping, one barrier per round: 0.83 -> 0.81 ms at
+    // L=16384, beta=4096).
     volatile int *vlp = lp;
-    for (int round = 0; round < 12; ++round) {
-      int changed = 0;
-      for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-        const int p = vlp[i], g = vlp[p];
-        if (g != p) {
-          vlp[i] = g;
-          changed = 1;
-        }
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+      int r = vlp[i];
+      for (int it = 0; it < SMEM_CAP; ++it) {
+        const int q = vlp[r];
+        if (q == r) break;
+        r = q;
       }
-      if (!__syncthreads_or(changed)) break;
+      vlp[i] = r;
+      par[a + i] = a + r;
     }
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) par[a + i] = a + lp[i];
   } else {
     for (int v = a + threadIdx.x; v < e; v += blockDim.x) par[v] = v;
   }
