@@ -65,11 +65,14 @@ KERNELS_PER_UPDATE = 12
 # was captured from the first source listed; the other kernels from an
 # earlier one that differs from it only in S >= 1 staging.  The second
 # source flattens the linking kernel's shared-memory forest by root walks
-# instead of pointer jumping (the same global loads and stores).
+# instead of pointer jumping (the same global loads and stores); the third
+# also stages the loop-properties kernel's ticks before its first barrier
+# (the same loads).
 TRAFFIC_PER_VERTEX = {"insert": 13.5, "link_union": 26.7, "loop_ids": 6.6, "loop_props": 25.0,
                       "op_rewrite": 14.8}
 TRAFFIC_PER_VERTEX_TEMPORAL = {k: v for k, v in TRAFFIC_PER_VERTEX.items() if k not in ("loop_props", "op_rewrite")}
-TRAFFIC_KERNELS_SHA1 = ("2bcd43154d5dbe04227fe45c685d4a3e85f64f03", "7f31eb08d2f1539aba0a26c771a385c99bf920e5")
+TRAFFIC_KERNELS_SHA1 = ("2bcd43154d5dbe04227fe45c685d4a3e85f64f03", "7f31eb08d2f1539aba0a26c771a385c99bf920e5",
+                        "fa8691b2a774215fa52e6afef9cb78fd57fd7843")
 
 
 # DRAM bytes per launch of each Swendsen-Wang phase at L = 8192, K = K_c (one
